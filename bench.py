@@ -1,0 +1,546 @@
+"""Benchmark of the batched hash-table hot path on one GB300 (or N replicas).
+
+One step is one pass of the whole path over the 2^28-cell workload
+(4 GiB table, 16-byte cells):
+  create the table (zeroed) | insert 2^27 uniform keys (load 0.5) |
+  find 2^27 hits + 2^27 misses | insert up to load 0.9 (241,591,910 keys) |
+  find 2^27 hits + 2^27 misses | for s in {0.5, 1.0, 1.25, 1.5}: a fresh
+  2^28-cell table and 2^28 insertOrUpdate(add 1) ops drawn Zipf(s) over 2^26
+  keys (word count) | erase 2^27 keys | migrate the load-0.9 table to 2^29
+  cells (gamma = 2) | destroy.
+value = operations (inserts + finds + insertOrUpdates + erases) per second of
+the whole step, migration and table creation included.  Inputs are resident
+in HBM before the timed region; every input is far larger than the 129 MB L2.
+`e2e` repeats the same steps through the same C ABI with pinned HOST arrays
+(the library stages them to the device and copies the results back).
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload: the same recipe at 2^22 cells.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+LOG2C = 28
+ZIPF_S = (0.5, 1.0, 1.25, 1.5)
+ZIPF_RANKS = 1 << 26
+METRIC = "Mops/s for insert/find/insertOrUpdate at 1 GB300 vs random-access roofline; p50/p99"
+UNIT = "Mops/s"
+
+
+# ----------------------------------------------------------------------------
+# roofline arithmetic (algorithmic bytes per operation)
+# ----------------------------------------------------------------------------
+def sectors(cells: float) -> float:
+    """Expected 32-byte sectors a probe of `cells` cells from a random home touches."""
+    return 1.0 + (cells - 1.0) / 2.0
+
+
+def knuth_hit(a: float) -> float:
+    return 0.5 * (1.0 + 1.0 / (1.0 - a))
+
+
+def knuth_miss(a: float) -> float:
+    return 0.5 * (1.0 + 1.0 / (1.0 - a) ** 2)
+
+
+def insert_probe_cells(a0: float, a1: float) -> float:
+    """Mean probe length of inserts that fill the table from load a0 to a1:
+    the unsuccessful-search length averaged over the fill (Knuth)."""
+    if a0 == 0.0:
+        return knuth_hit(a1)
+    return 0.5 * (1.0 + (1.0 / (1.0 - a1) - 1.0 / (1.0 - a0)) / (a1 - a0))
+
+
+def algorithmic_bytes(kind: str, **kw) -> float:
+    """Bytes one operation must move to or from HBM (SURVEY-style formula):
+    its input/output streams plus the 32-byte sectors its probe touches
+    (plus one dirty sector written back for an insert)."""
+    if kind == "find_hit":
+        return 8 + 8 + 1 + 32 * sectors(knuth_hit(kw["load"]))
+    if kind == "find_miss":
+        return 8 + 8 + 1 + 32 * sectors(knuth_miss(kw["load"]))
+    if kind == "insert":
+        return 16 + 1 + 32 * sectors(insert_probe_cells(kw["a0"], kw["a1"])) + 32
+    if kind == "iou":
+        # streams + each distinct key's cell read and written once, amortised
+        return 16 + 1 + 64.0 * kw["distinct"] / kw["ops"]
+    if kind == "erase":
+        return 8 + 1 + 32 * sectors(knuth_hit(kw["load"])) + 32
+    if kind == "migrate":
+        return 16 + 16 * kw["gamma"]  # per source cell
+    raise ValueError(kind)
+
+
+# ----------------------------------------------------------------------------
+# clocks sampling during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = sorted(sm)[len(sm) // 2:]  # upper half: samples under load
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# the GPU arm
+# ----------------------------------------------------------------------------
+def make_inputs(device: str):
+    """All step inputs, generated on the device (same recipe as the tests)."""
+    import torch
+
+    c = 1 << LOG2C
+    wl = W.bounded_workload(LOG2C, loads=(0.5, 0.9), n_find=1 << 27, backend=device)
+    zipf = {s: W.zipf_keys(1 << 28, s, ZIPF_RANKS, W.SEED_ZIPF, backend=device) for s in ZIPF_S}
+    distinct = {s: int(torch.unique(z).numel()) for s, z in zipf.items()}
+    ones = torch.ones(1 << 28, dtype=torch.int64, device=device)
+    torch.cuda.synchronize()
+    return {"c": c, "wl": wl, "zipf": zipf, "distinct": distinct, "ones": ones}
+
+
+class StepRunner:
+    """Runs one step; records per-call CUDA events when asked."""
+
+    def __init__(self, cht, inp, host: bool = False):
+        import torch
+
+        self.cht, self.inp, self.host = cht, inp, host
+        self.torch = torch
+        wl = inp["wl"]
+        n05, n09 = wl["counts"][0.5], wl["counts"][0.9]
+        self.n05, self.n09 = n05, n09
+        nf = 1 << 27
+        self.calls = []  # (name, fn, ops)
+        dev = "cuda"
+        if host:
+            pin = lambda t: t.cpu().pin_memory()  # noqa: E731
+            self.keys = pin(wl["keys"])
+            self.vals = pin(wl["vals"])
+            self.h05, self.h09, self.miss = pin(wl["hits"][0.5]), pin(wl["hits"][0.9]), pin(wl["misses"])
+            self.zipf = {s: pin(z) for s, z in inp["zipf"].items()}
+            self.ones = pin(inp["ones"])
+            mk = lambda n, dt: torch.empty(n, dtype=dt).pin_memory()  # noqa: E731
+        else:
+            self.keys, self.vals = wl["keys"], wl["vals"]
+            self.h05, self.h09, self.miss = wl["hits"][0.5], wl["hits"][0.9], wl["misses"]
+            self.zipf, self.ones = inp["zipf"], inp["ones"]
+            mk = lambda n, dt: torch.empty(n, dtype=dt, device=dev)  # noqa: E731
+        self.codes = mk(1 << 28, torch.uint8)
+        self.vout = mk(nf, torch.int64)
+        self.ops_per_step = n09 + 4 * nf + 4 * (1 << 28) + nf
+        self.h2d = 8 * (2 * n09 + 4 * nf + 4 * 2 * (1 << 28) + nf) if host else 0
+        self.d2h = (n09 + 4 * (9 * nf) + 4 * (1 << 28) + nf) if host else 0
+
+    def step(self, events: dict | None = None):
+        cht, torch = self.cht, self.torch
+        s = torch.cuda.current_stream()
+        n05, n09, nf = self.n05, self.n09, 1 << 27
+
+        def timed(name, fn):
+            if events is None:
+                fn()
+                return
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            events.setdefault(name, []).append((a, b))
+
+        t = cht.Table(1 << LOG2C)
+        timed("insert_0.5", lambda: t.insert(self.keys[:n05], self.vals[:n05], self.codes[:n05]))
+        timed("find_hit_0.5", lambda: t.find(self.h05, self.vout, self.codes[:nf]))
+        timed("find_miss_0.5", lambda: t.find(self.miss, self.vout, self.codes[:nf]))
+        timed("insert_0.9", lambda: t.insert(self.keys[n05:n09], self.vals[n05:n09], self.codes[: n09 - n05]))
+        timed("find_hit_0.9", lambda: t.find(self.h09, self.vout, self.codes[:nf]))
+        timed("find_miss_0.9", lambda: t.find(self.miss, self.vout, self.codes[:nf]))
+        for sv in ZIPF_S:
+            t2 = cht.Table(1 << LOG2C)
+            timed(f"iou_add_s{sv}", lambda: t2.insert_or_update(self.zipf[sv], self.ones, cht.ADD, self.codes))
+            t2.destroy()
+        timed("erase", lambda: t.erase(self.keys[:nf], self.codes[:nf]))
+        timed("migrate_x2", lambda: t.migrate(2 << LOG2C))
+        t.destroy()
+
+
+def per_op_bytes(inp):
+    b = {
+        "insert_0.5": algorithmic_bytes("insert", a0=0.0, a1=0.5),
+        "insert_0.9": algorithmic_bytes("insert", a0=0.5, a1=0.9),
+        "find_hit_0.5": algorithmic_bytes("find_hit", load=0.5),
+        "find_miss_0.5": algorithmic_bytes("find_miss", load=0.5),
+        "find_hit_0.9": algorithmic_bytes("find_hit", load=0.9),
+        "find_miss_0.9": algorithmic_bytes("find_miss", load=0.9),
+        "erase": algorithmic_bytes("erase", load=0.9),
+    }
+    for sv in ZIPF_S:
+        b[f"iou_add_s{sv}"] = algorithmic_bytes("iou", distinct=inp["distinct"][sv], ops=1 << 28)
+    return b
+
+
+def op_counts(inp):
+    wl = inp["wl"]
+    n05, n09 = wl["counts"][0.5], wl["counts"][0.9]
+    nf = 1 << 27
+    d = {"insert_0.5": n05, "insert_0.9": n09 - n05, "find_hit_0.5": nf, "find_miss_0.5": nf,
+         "find_hit_0.9": nf, "find_miss_0.9": nf, "erase": nf, "migrate_x2": 1 << LOG2C}
+    for sv in ZIPF_S:
+        d[f"iou_add_s{sv}"] = 1 << 28
+    return d
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float, device=None) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def latency_percentiles(cht, inp, reps: int):
+    """p50/p99 of single calls at the small (2^20-cell) workload, 2^19 ops each."""
+    import torch
+
+    wl = W.bounded_workload(20, loads=(0.5,), n_find=1 << 19, backend="cuda")
+    n = wl["counts"][0.5]
+    codes = torch.empty(n, dtype=torch.uint8, device="cuda")
+    vout = torch.empty(n, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream()
+    out = {}
+    t = cht.Table(1 << 20)
+    samples = {"insert": [], "find_hit": [], "find_miss": []}
+    for _ in range(reps):
+        t.clear()
+        for name, fn in (("insert", lambda: t.insert(wl["keys"], wl["vals"], codes)),
+                         ("find_hit", lambda: t.find(wl["hits"][0.5], vout, codes)),
+                         ("find_miss", lambda: t.find(wl["misses"], vout, codes))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            b.synchronize()
+            samples[name].append(a.elapsed_time(b))
+    t.destroy()
+    for k, v in samples.items():
+        v = sorted(v)
+        p50 = v[len(v) // 2]
+        p99 = v[min(len(v) - 1, int(math.ceil(0.99 * len(v))) - 1)]
+        out[k] = {"p50_ms": round(p50, 5), "p99_ms": round(p99, 5),
+                  "mops_at_p50": round(n / (p50 * 1e-3) / 1e6, 1)}
+    return out
+
+
+def run_gpu(args):
+    import torch
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    import paper_1601_04017_gb300 as cht
+
+    cht.load_library()
+    inp = make_inputs("cuda")
+    runner = StepRunner(cht, inp)
+    for _ in range(args.warmup):
+        runner.step()
+    torch.cuda.synchronize()
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = cht.launch_count()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    events: dict = {}
+    e0.record(s)
+    for _ in range(args.steps):
+        runner.step(events)
+    e1.record(s)
+    torch.cuda.synchronize()
+    launches = cht.launch_count() - l0
+    barrier(pg)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(pg, ms, device="cuda")
+    ms_step = ms_max / args.steps
+    ops = runner.ops_per_step * args.steps * world
+    value = ops / (ms_max * 1e-3) / 1e6
+
+    # per-call breakdown and the dominant kernel's roofline
+    counts = op_counts(inp)
+    bpo = per_op_bytes(inp)
+    peak, peak_kind = load_peaks()
+    breakdown = {}
+    for name, evs in events.items():
+        t_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        row = {"ms": round(t_ms, 4), "mops": round(counts[name] / (t_ms * 1e-3) / 1e6, 1)}
+        if name in bpo:
+            gbs = bpo[name] * counts[name] / (t_ms * 1e-3) / 1e9
+            row.update({"bytes_per_op": round(bpo[name], 2), "gbs": round(gbs, 1),
+                        "frac_of_" + peak_kind: round(gbs / peak, 4)})
+        elif name == "migrate_x2":
+            gbs = algorithmic_bytes("migrate", gamma=2) * counts[name] / (t_ms * 1e-3) / 1e9
+            row.update({"bytes_per_src_cell": 48, "gbs": round(gbs, 1),
+                        "frac_of_" + peak_kind: round(gbs / peak, 4)})
+        breakdown[name] = row
+    probe_rows = {k: v for k, v in breakdown.items() if k != "migrate_x2"}
+    dom = max(probe_rows, key=lambda k: probe_rows[k]["ms"])
+    dom_t = probe_rows[dom]["ms"]
+    achieved = bpo[dom] * counts[dom] / (dom_t * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            with open(tr_path) as f:
+                traffic = json.load(f).get(dom)
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": traffic}
+
+    # end-to-end through the same API with pinned host arrays
+    e2e = None
+    if not args.no_e2e:
+        hrunner = StepRunner(cht, inp, host=True)
+        hrunner.step()
+        torch.cuda.synchronize()
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.e2e_steps)):
+            hrunner.step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        el = max_over_ranks(pg, el, device="cuda")
+        e2e = {"value": round(hrunner.ops_per_step * max(1, args.e2e_steps) * world / el / 1e6, 1),
+               "unit": UNIT, "h2d_bytes_per_step": hrunner.h2d, "d2h_bytes_per_step": hrunner.d2h}
+        del hrunner
+
+    lat = latency_percentiles(cht, inp, args.latency_reps) if args.latency_reps > 0 else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_once()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (SplitMix64 uniform keys, Zipf rejection-inversion; generated on device)",
+            "config": {"workload": "bounded table 2^28 cells: insert to load 0.5/0.9, find 2^27 hits + "
+                                   "2^27 misses at each load, insertOrUpdate(add 1) 2^28 Zipf ops over "
+                                   "2^26 keys for s in {0.5,1.0,1.25,1.5}, erase 2^27, migrate x2",
+                       "capacity_cells": 1 << LOG2C, "ops_per_step": runner.ops_per_step,
+                       "l2": "inputs and table far larger than L2 (no flush needed)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "group_width": 1},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "breakdown": breakdown, "latency_config1": lat,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and the reference arm)
+# ----------------------------------------------------------------------------
+CPU_LOG2C = 22
+
+
+def cpu_sample_step(oracle, inp) -> tuple[int, float]:
+    """The bench step's recipe on a 2^22-cell oracle table; (ops, seconds)."""
+    wl = inp["wl"]
+    n05, n09 = wl["counts"][0.5], wl["counts"][0.9]
+    ops = 0
+    t0 = time.perf_counter()
+    t = oracle.OracleTable(1 << CPU_LOG2C)
+    t.insert(wl["keys"][:n05], wl["vals"][:n05])
+    t.find(wl["hits"][0.5])
+    t.find(wl["misses"])
+    t.insert(wl["keys"][n05:n09], wl["vals"][n05:n09])
+    t.find(wl["hits"][0.9])
+    t.find(wl["misses"])
+    nf = wl["misses"].size
+    ops += n09 + 4 * nf
+    for sv in ZIPF_S:
+        t2 = oracle.OracleTable(1 << CPU_LOG2C)
+        z = inp["zipf"][sv]
+        t2.insert_or_update(z, np.ones(z.size, np.uint64), oracle.ADD)
+        ops += z.size
+        t2.close()
+    t.erase(wl["keys"][:nf])
+    ops += nf
+    t.migrate(2 << CPU_LOG2C)
+    t.close()
+    return ops, time.perf_counter() - t0
+
+
+def cpu_inputs():
+    wl = W.bounded_workload(CPU_LOG2C, loads=(0.5, 0.9), n_find=1 << (CPU_LOG2C - 1))
+    zipf = {s: W.zipf_keys(1 << CPU_LOG2C, s, ZIPF_RANKS >> 6, W.SEED_ZIPF) for s in ZIPF_S}
+    return {"wl": wl, "zipf": zipf}
+
+
+SAMPLE_DESC = ("the same step recipe at 2^22 cells: insert to load 0.5/0.9, 2^21 find hits + misses at "
+               "each load, 2^22 Zipf insertOrUpdate(add) per s over 2^20 keys, erase 2^21, migrate x2")
+
+
+def cpu_baseline_once():
+    import oracle
+
+    oracle.build()
+    inp = cpu_inputs()
+    ops, sec = cpu_sample_step(oracle, inp)
+    return {"value": round(ops / sec / 1e6, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": SAMPLE_DESC, "seconds": round(sec, 2)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    inp = cpu_inputs()
+    for _ in range(args.warmup):
+        cpu_sample_step(oracle, inp)
+    tot_ops, tot_s, per = 0, 0.0, []
+    for _ in range(args.steps):
+        ops, sec = cpu_sample_step(oracle, inp)
+        tot_ops += ops
+        tot_s += sec
+        per.append(sec)
+    value = tot_ops / tot_s / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot_s / args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": SAMPLE_DESC, "capacity_cells": 1 << CPU_LOG2C},
+        "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": SAMPLE_DESC},
+        "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--latency-reps", type=int, default=100)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

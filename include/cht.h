@@ -1,0 +1,196 @@
+/*
+ * libcht -- a GB300 (sm_103a) concurrent hash table: the folklore
+ * linear-probing table of Maier, Sanders & Dementiev, "Concurrent Hash
+ * Tables: Fast and General(?)!" (arXiv 1601.04017), with batched operations
+ * and cluster-wise migration for growth.
+ *
+ * Data model
+ *   A table is an array of c cells of 16 bytes, <key u64, value u64>, c a
+ *   power of two >= 64 (Sec. 6 "Bounded Hash Tables").  Key 0 marks an empty
+ *   cell and key ~0 a tombstone (Sec. 3 "Deletions", Sec. 4.4); neither can be
+ *   stored.  The home cell of key x is the top log2(c) bits of fmix64(x)
+ *   (MurmurHash3's 64-bit finalizer), i.e. the scaling map
+ *   h_c(x) = floor(h(x) * c / 2^64) of Sec. 4.3.1, so doubling c keeps the
+ *   order of clusters and lets migration run cluster by cluster (Lemma 1).
+ *
+ * Calls, streams and phase semantics
+ *   Every operation call is one batch of ONE operation type.  Calls are
+ *   asynchronous and ordered on the CUDA stream passed in; a batch behaves as
+ *   if its operations ran in some sequential order (linearizability, Sec. 3),
+ *   and consecutive calls on one stream see each other's effects.  Calls on
+ *   one table must be issued on one stream, or ordered by the caller; calls
+ *   that overlap on the device on the same table are not supported.
+ *
+ * Pointers
+ *   Every array argument may be device memory or host memory.  Host arrays
+ *   (pageable or pinned) are staged through library-owned device buffers:
+ *   inputs are copied in on the stream before the kernel, outputs are copied
+ *   back on the stream after it; results in a host output array are valid
+ *   once the stream has been synchronized.  The caller owns every array and
+ *   keeps it alive until the work on the stream has completed.  The library
+ *   owns the table memory.  `stream` may be NULL (the legacy default stream).
+ *
+ * Per-operation result codes (optional uint8 output arrays; NULL = not wanted)
+ *   0  no   (key already present / not found / not erased)
+ *   1  yes  (inserted / found / erased)
+ *   2  table full: every cell was probed without success (bounded table)
+ *   3  reserved key (0 or ~0); the operation did not touch the table
+ *   Codes 2 and 3 also set bits in the table's sticky device status, which
+ *   cht_size() and cht_get_status() report.
+ *
+ * Errors
+ *   Argument errors return at once with no side effect.  Device-side
+ *   conditions (full table, reserved keys) are reported per operation and in
+ *   the sticky status.  CUDA errors return CHT_ERR_CUDA.
+ */
+#ifndef CHT_H
+#define CHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-compatible with cudaStream_t; no CUDA header is needed to include this. */
+struct CUstream_st;
+typedef struct CUstream_st *cht_stream_t;
+
+typedef struct cht_table *cht_handle;
+
+typedef enum {
+    CHT_OK = 0,
+    CHT_ERR_INVALID_ARG = 1,  /* NULL handle/pointer, bad size, bad op */
+    CHT_ERR_OOM = 2,          /* device allocation failed; table unchanged */
+    CHT_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
+    CHT_ERR_TABLE_FULL = 4,   /* some operation found no free cell */
+    CHT_ERR_RESERVED_KEY = 5, /* some operation used key 0 or ~0 */
+    CHT_ERR_TIMEOUT = 6       /* a bounded device wait gave up */
+} cht_status;
+
+typedef enum {
+    CHT_OVERWRITE = 0, /* value <- d (Sec. 3, single-word store specialisation) */
+    CHT_ADD = 1        /* value <- value + d mod 2^64 (fetch-and-add specialisation) */
+} cht_update_op;
+
+/* Sticky device status bits (cht_get_status). */
+#define CHT_STATUS_FULL 0x1u
+#define CHT_STATUS_RESERVED 0x2u
+
+/* Tunables.  group_width G: lanes that probe one key together, each loading
+ * 16 bytes (G in {1,2,4,8,16,32}); G = 1 uses one 32-byte load (two cells,
+ * one DRAM sector) per lane and probe step.  ctas_per_sm: resident CTAs per
+ * SM for the operation kernels (0 = occupancy maximum).  migrate_tile:
+ * source cells per migration CTA (power of two, 256..8192, 0 = default).
+ * alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5). */
+typedef struct {
+    int group_width;
+    int ctas_per_sm;
+    int migrate_tile;
+    double alpha;
+} cht_config;
+
+/* Create a table of at least `capacity` cells (rounded up to a power of two,
+ * minimum 64, maximum 2^40), all empty (Sec. 3 "Initialization").  growable
+ * != 0: insert and insert_or_update migrate the table to a larger (gamma = 2)
+ * or same-size (gamma = 1, tombstone purge) one before the number of
+ * non-empty cells could exceed alpha * c (Sec. 4.3.2, Sec. 4.4).  The table
+ * memory is zeroed on `stream`.  CHT_ERR_OOM if the memory is not there. */
+cht_status cht_create(uint64_t capacity, int growable, cht_stream_t stream, cht_handle *out);
+
+/* Free the table (stream-ordered on its last stream) and the handle. */
+cht_status cht_destroy(cht_handle h);
+
+/* Replace the tunables (NULL restores defaults).  Takes effect on the next call. */
+cht_status cht_set_config(cht_handle h, const cht_config *cfg);
+cht_status cht_get_config(cht_handle h, cht_config *cfg);
+
+/* insert (Sec. 3, Algorithm 1 with the insert return rule): for each i <
+ * n, store <keys[i], vals[i]> unless the key is present.  If several
+ * operations of the batch carry the same absent key, exactly one of them
+ * inserts (code 1; the stored value is that operation's) and the others
+ * report 0.  keys/vals: n u64 each; inserted: n u8 result codes or NULL. */
+cht_status cht_insert(cht_handle h, const uint64_t *keys, const uint64_t *vals, uint64_t n,
+                      uint8_t *inserted, cht_stream_t stream);
+
+/* find (Sec. 3 "Lookup", copy semantics): vals_out[i] = the value stored
+ * with keys[i], or 0 if absent; found[i] = 1 / 0 (3 for a reserved key).
+ * Writes nothing to the table.  vals_out: n u64 (required); found: n u8 or NULL. */
+cht_status cht_find(cht_handle h, const uint64_t *keys, uint64_t n, uint64_t *vals_out,
+                    uint8_t *found, cht_stream_t stream);
+
+/* insertOrUpdate (Sec. 3, Algorithm 1): insert <k, d> if k is absent, else
+ * update its value by `op` (CHT_ADD: fetch-and-add; CHT_OVERWRITE: store).
+ * Code 1 iff this operation inserted: for an absent key exactly one of the
+ * batch's operations on it reports 1.  With CHT_ADD the final value is the
+ * previous value (0 if absent) plus the sum of the batch's d for that key,
+ * mod 2^64, independent of order; with CHT_OVERWRITE it is one of those d. */
+cht_status cht_insert_or_update(cht_handle h, const uint64_t *keys, const uint64_t *vals,
+                                uint64_t n, cht_update_op op, uint8_t *inserted,
+                                cht_stream_t stream);
+
+/* erase (Sec. 4.4): replace the key of the cell holding keys[i] by the
+ * tombstone (value kept).  For a present key exactly one of the batch's
+ * operations on it reports 1.  Tombstones keep occupying their cells until
+ * the next migration purges them. */
+cht_status cht_erase(cht_handle h, const uint64_t *keys, uint64_t n, uint8_t *erased,
+                     cht_stream_t stream);
+
+/* Migrate into a new table of new_capacity cells (rounded up to a power of
+ * two; must be a power-of-two multiple gamma >= 1 of the current capacity and
+ * hold every live element), dropping tombstones (Sec. 4.3.1, Sec. 4.4).
+ * new_capacity = 0 applies the growth policy: double if more than alpha*c/2
+ * elements are live, else keep the size.  The resulting cell layout equals the
+ * sequential migration that visits the old cells in index order from a
+ * cluster start (Lemma 1).  The new table is allocated before the old one is
+ * released: on CHT_ERR_OOM the table is unchanged.  Reads the live count
+ * back from the device (synchronizes `stream`). */
+cht_status cht_migrate(cht_handle h, uint64_t new_capacity, cht_stream_t stream);
+
+/* Synchronize `stream` and report: live elements (I - D), non-empty cells
+ * I (tombstones included), capacity c.  Any out-pointer may be NULL.
+ * Returns CHT_ERR_TABLE_FULL / CHT_ERR_RESERVED_KEY if the sticky status has
+ * the bit set (the status is not cleared), else CHT_OK. */
+cht_status cht_size(cht_handle h, uint64_t *live, uint64_t *nonempty, uint64_t *capacity,
+                    cht_stream_t stream);
+
+/* Synchronize `stream`, return the sticky status bits in *bits and clear them. */
+cht_status cht_get_status(cht_handle h, uint32_t *bits, cht_stream_t stream);
+
+/* forall (Sec. 3 "Bulk Operations"): write the live elements to keys_out /
+ * vals_out (max_n entries each, in no particular order) and their number to
+ * *n_out; fails with CHT_ERR_INVALID_ARG, writing the number to *n_out, if it
+ * exceeds max_n.  vals_out may be NULL.  Synchronizes `stream`. */
+cht_status cht_export(cht_handle h, uint64_t *keys_out, uint64_t *vals_out, uint64_t max_n,
+                      uint64_t *n_out, cht_stream_t stream);
+
+/* Copy the raw cell array (2*c u64: key, value, key, value, ...) to
+ * cells_out, which holds max_cells cells; *n_cells receives c.  Used to check
+ * layouts.  Asynchronous for device memory. */
+cht_status cht_copy_cells(cht_handle h, uint64_t *cells_out, uint64_t max_cells,
+                          uint64_t *n_cells, cht_stream_t stream);
+
+/* Make every cell empty again and reset the counters (capacity unchanged). */
+cht_status cht_clear(cht_handle h, cht_stream_t stream);
+
+/* Cap, in bytes, on the device memory this library allocates at any time for
+ * tables and staging (0 = no cap).  An allocation that would exceed it fails
+ * with CHT_ERR_OOM exactly like a failed cudaMalloc. */
+cht_status cht_set_memory_limit(uint64_t bytes);
+uint64_t cht_memory_in_use(void);
+
+/* Number of kernel launches this library has issued (process-wide). */
+uint64_t cht_launch_count(void);
+
+/* Static string for a status code. */
+const char *cht_status_string(cht_status s);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int cht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHT_H */

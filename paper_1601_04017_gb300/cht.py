@@ -1,0 +1,265 @@
+"""ctypes binding of libcht (include/cht.h): argument marshalling only.
+
+Every array argument is a torch tensor (CUDA or CPU) or a numpy array with
+8-byte elements for keys and values (int64 or uint64: the same bits) and
+uint8 for result codes.  CPU arrays go through the library's host staging.
+The stream defaults to torch's current CUDA stream.  There is no fallback:
+if libcht.so cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+CHT_OK = 0
+CHT_ERR_INVALID_ARG = 1
+CHT_ERR_OOM = 2
+CHT_ERR_CUDA = 3
+CHT_ERR_TABLE_FULL = 4
+CHT_ERR_RESERVED_KEY = 5
+CHT_ERR_TIMEOUT = 6
+
+OVERWRITE = 0
+ADD = 1
+STATUS_FULL = 0x1
+STATUS_RESERVED = 0x2
+
+CODE_NO, CODE_YES, CODE_FULL, CODE_RESERVED = 0, 1, 2, 3
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ChtError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = _lib.cht_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} (status {status})")
+
+
+class ChtConfig(ctypes.Structure):
+    _fields_ = [("group_width", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("migrate_tile", ctypes.c_int), ("alpha", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build: bool = True):
+    """Load libcht.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcht.so not found at {path}")
+        lib = ctypes.CDLL(path)
+        p, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+        sigs = {
+            "cht_create": (i32, [u64, i32, p, ctypes.POINTER(p)]),
+            "cht_destroy": (i32, [p]),
+            "cht_set_config": (i32, [p, ctypes.POINTER(ChtConfig)]),
+            "cht_get_config": (i32, [p, ctypes.POINTER(ChtConfig)]),
+            "cht_insert": (i32, [p, p, p, u64, p, p]),
+            "cht_find": (i32, [p, p, u64, p, p, p]),
+            "cht_insert_or_update": (i32, [p, p, p, u64, i32, p, p]),
+            "cht_erase": (i32, [p, p, u64, p, p]),
+            "cht_migrate": (i32, [p, u64, p]),
+            "cht_size": (i32, [p, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64), p]),
+            "cht_get_status": (i32, [p, ctypes.POINTER(ctypes.c_uint32), p]),
+            "cht_export": (i32, [p, p, p, u64, ctypes.POINTER(u64), p]),
+            "cht_copy_cells": (i32, [p, p, u64, ctypes.POINTER(u64), p]),
+            "cht_clear": (i32, [p, p]),
+            "cht_set_memory_limit": (i32, [u64]),
+            "cht_memory_in_use": (u64, []),
+            "cht_launch_count": (u64, []),
+            "cht_status_string": (ctypes.c_char_p, [i32]),
+            "cht_version": (i32, []),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, what: str):
+    if status != CHT_OK:
+        raise ChtError(status, what)
+
+
+def _ptr(x, elem_size: int, n: int | None = None, what: str = "array"):
+    """(pointer, element count, is_cuda) of a tensor / numpy array."""
+    if x is None:
+        return None, 0, False
+    if isinstance(x, np.ndarray):
+        if x.dtype.itemsize != elem_size or not x.flags.c_contiguous:
+            raise TypeError(f"{what}: need a contiguous array of {elem_size}-byte elements")
+        cnt = x.size
+        ptr = x.ctypes.data if cnt else None
+        cuda = False
+    else:
+        if x.element_size() != elem_size or not x.is_contiguous():
+            raise TypeError(f"{what}: need a contiguous tensor of {elem_size}-byte elements")
+        cnt = x.numel()
+        ptr = x.data_ptr() if cnt else None
+        cuda = x.is_cuda
+    if n is not None and cnt < n:
+        raise ValueError(f"{what}: holds {cnt} elements, need {n}")
+    return ptr, cnt, cuda
+
+
+def _stream(stream, device=None):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def memory_in_use() -> int:
+    return int(load_library().cht_memory_in_use())
+
+
+def set_memory_limit(nbytes: int) -> None:
+    _check(load_library().cht_set_memory_limit(int(nbytes)), "cht_set_memory_limit")
+
+
+def launch_count() -> int:
+    return int(load_library().cht_launch_count())
+
+
+def version() -> int:
+    return int(load_library().cht_version())
+
+
+class Table:
+    """A libcht table.  Methods mirror the C ABI (cht_insert, cht_find, ...)."""
+
+    def __init__(self, capacity: int, growable: bool = False, stream=None, config: dict | None = None):
+        import torch
+
+        self._lib = load_library()
+        self.device = torch.cuda.current_device()
+        h = ctypes.c_void_p()
+        _check(self._lib.cht_create(int(capacity), int(bool(growable)), _stream(stream), ctypes.byref(h)),
+               "cht_create")
+        self._h = h
+        if config:
+            self.set_config(**config)
+
+    # -- lifetime ------------------------------------------------------------
+    def destroy(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _check(self._lib.cht_destroy(self._h), "cht_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    # -- configuration -------------------------------------------------------
+    def config(self) -> dict:
+        c = ChtConfig()
+        _check(self._lib.cht_get_config(self._h, ctypes.byref(c)), "cht_get_config")
+        return {f: getattr(c, f) for f, _ in ChtConfig._fields_}
+
+    def set_config(self, **kw):
+        cur = self.config()
+        cur.update(kw)
+        c = ChtConfig(int(cur["group_width"]), int(cur["ctas_per_sm"]), int(cur["migrate_tile"]),
+                      float(cur["alpha"]))
+        _check(self._lib.cht_set_config(self._h, ctypes.byref(c)), "cht_set_config")
+
+    # -- operations ----------------------------------------------------------
+    def insert(self, keys, vals, inserted=None, stream=None):
+        kp, n, _ = _ptr(keys, 8, what="keys")
+        vp, _, _ = _ptr(vals, 8, n, "vals")
+        cp, _, _ = _ptr(inserted, 1, n, "inserted")
+        _check(self._lib.cht_insert(self._h, kp, vp, n, cp, _stream(stream)), "cht_insert")
+        return inserted
+
+    def find(self, keys, vals_out, found=None, stream=None):
+        kp, n, _ = _ptr(keys, 8, what="keys")
+        vp, _, _ = _ptr(vals_out, 8, n, "vals_out")
+        cp, _, _ = _ptr(found, 1, n, "found")
+        _check(self._lib.cht_find(self._h, kp, n, vp, cp, _stream(stream)), "cht_find")
+        return vals_out, found
+
+    def insert_or_update(self, keys, vals, op: int = ADD, inserted=None, stream=None):
+        kp, n, _ = _ptr(keys, 8, what="keys")
+        vp, _, _ = _ptr(vals, 8, n, "vals")
+        cp, _, _ = _ptr(inserted, 1, n, "inserted")
+        _check(self._lib.cht_insert_or_update(self._h, kp, vp, n, int(op), cp, _stream(stream)),
+               "cht_insert_or_update")
+        return inserted
+
+    def erase(self, keys, erased=None, stream=None):
+        kp, n, _ = _ptr(keys, 8, what="keys")
+        cp, _, _ = _ptr(erased, 1, n, "erased")
+        _check(self._lib.cht_erase(self._h, kp, n, cp, _stream(stream)), "cht_erase")
+        return erased
+
+    def migrate(self, new_capacity: int = 0, stream=None):
+        _check(self._lib.cht_migrate(self._h, int(new_capacity), _stream(stream)), "cht_migrate")
+
+    def clear(self, stream=None):
+        _check(self._lib.cht_clear(self._h, _stream(stream)), "cht_clear")
+
+    # -- state ---------------------------------------------------------------
+    def size(self, stream=None, check: bool = False):
+        """(live, nonempty, capacity); raises on a set status bit if check."""
+        live, ne, cap = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        r = self._lib.cht_size(self._h, ctypes.byref(live), ctypes.byref(ne), ctypes.byref(cap),
+                               _stream(stream))
+        if r not in (CHT_OK, CHT_ERR_TABLE_FULL, CHT_ERR_RESERVED_KEY) or (check and r != CHT_OK):
+            _check(r, "cht_size")
+        return int(live.value), int(ne.value), int(cap.value)
+
+    @property
+    def capacity(self) -> int:
+        return self.size()[2]
+
+    def status(self, stream=None) -> int:
+        bits = ctypes.c_uint32()
+        _check(self._lib.cht_get_status(self._h, ctypes.byref(bits), _stream(stream)), "cht_get_status")
+        return int(bits.value)
+
+    def export(self, stream=None):
+        """Live (keys, values) as CUDA int64 tensors, in no particular order."""
+        import torch
+
+        live = self.size(stream)[0]
+        k = torch.empty(max(live, 1), dtype=torch.int64, device=f"cuda:{self.device}")
+        v = torch.empty_like(k)
+        n = ctypes.c_uint64()
+        _check(self._lib.cht_export(self._h, k.data_ptr(), v.data_ptr(), live, ctypes.byref(n),
+                                    _stream(stream)), "cht_export")
+        return k[: n.value], v[: n.value]
+
+    def cells(self, stream=None):
+        """Raw cells as a (c, 2) CUDA int64 tensor of (key, value)."""
+        import torch
+
+        cap = self.size(stream)[2]
+        out = torch.empty((cap, 2), dtype=torch.int64, device=f"cuda:{self.device}")
+        n = ctypes.c_uint64()
+        _check(self._lib.cht_copy_cells(self._h, out.data_ptr(), cap, ctypes.byref(n), _stream(stream)),
+               "cht_copy_cells")
+        return out

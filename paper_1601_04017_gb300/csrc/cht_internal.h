@@ -1,0 +1,49 @@
+// Internal host-side interface between the C-ABI runtime (cht_runtime.cu)
+// and the kernel translation units (cht_ops.cu, cht_migrate.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cht_device.cuh"
+
+namespace cht {
+
+enum Mode : int { kFind = 0, kInsert = 1, kIouAdd = 2, kIouOverwrite = 3, kErase = 4 };
+
+// One batched operation over a table of 2^log2c cells.
+struct OpArgs {
+    Cell* cells;
+    u32 log2c;
+    const u64* keys;
+    const u64* vals;      // insert / insert_or_update input values (else NULL)
+    u64* vals_out;        // find output values (else NULL)
+    unsigned char* codes; // per-op result codes (nullable)
+    u64 n;
+    DevState* st;
+};
+
+// Launch one batched operation. group_width in {1,2,4,8,16,32}; ctas_per_sm
+// 0 = occupancy maximum.  Returns the launch error (cudaSuccess if none).
+cudaError_t launch_op(Mode mode, const OpArgs& a, int group_width, int ctas_per_sm,
+                      cudaStream_t s);
+
+// Cluster-wise migration of `src` (2^src_log2 cells) into `dst`
+// (2^dst_log2 cells, dst_log2 >= src_log2).  dst needs no initialisation:
+// every target cell is written.  `st` receives the new I (it must be zero
+// on entry) and mig_fail.  tile: source cells per CTA (power of two).
+cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log2, DevState* st,
+                           int tile, cudaStream_t s);
+
+// Compact the live cells into keys_out / vals_out (max_n entries); the count
+// lands in st->export_pos, which must be zero on entry.
+cudaError_t launch_export(const Cell* cells, u32 log2c, u64* keys_out, u64* vals_out, u64 max_n,
+                          DevState* st, cudaStream_t s);
+
+// Kernel launches issued so far (process-wide).
+void count_launch();
+
+// SM count of the current device (cached).
+int sm_count();
+
+}  // namespace cht

@@ -1,0 +1,58 @@
+// Launchers of the batched probe kernels (see cht_ops.cuh).
+#include <atomic>
+
+#include "cht_ops.cuh"
+
+namespace cht {
+namespace {
+
+template <int G, int MODE>
+cudaError_t launch_one(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
+    static std::atomic<int> occ{0};
+    int per_sm = occ.load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, op_kernel<G, MODE>, kOpBlock, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        occ.store(per_sm, std::memory_order_relaxed);
+    }
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    u64 grid = u64(sm_count()) * u64(per_sm);
+    const u64 need = (a.n + kOpBlock - 1) / kOpBlock;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    op_kernel<G, MODE><<<unsigned(grid), kOpBlock, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_mode(const OpArgs& a, int g, int ctas_per_sm, cudaStream_t s) {
+    switch (g) {
+        case 1: return launch_one<1, MODE>(a, ctas_per_sm, s);
+        case 2: return launch_one<2, MODE>(a, ctas_per_sm, s);
+        case 4: return launch_one<4, MODE>(a, ctas_per_sm, s);
+        case 8: return launch_one<8, MODE>(a, ctas_per_sm, s);
+        case 16: return launch_one<16, MODE>(a, ctas_per_sm, s);
+        case 32: return launch_one<32, MODE>(a, ctas_per_sm, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_op(Mode mode, const OpArgs& a, int group_width, int ctas_per_sm,
+                      cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    switch (mode) {
+        case kFind: return launch_mode<kFind>(a, group_width, ctas_per_sm, s);
+        case kInsert: return launch_mode<kInsert>(a, group_width, ctas_per_sm, s);
+        case kIouAdd: return launch_mode<kIouAdd>(a, group_width, ctas_per_sm, s);
+        case kIouOverwrite: return launch_mode<kIouOverwrite>(a, group_width, ctas_per_sm, s);
+        case kErase: return launch_mode<kErase>(a, group_width, ctas_per_sm, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cht

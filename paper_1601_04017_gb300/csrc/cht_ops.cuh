@@ -1,0 +1,276 @@
+// Batched probe kernels of libcht: find, insert, insertOrUpdate (add /
+// overwrite) and erase over the folklore linear-probing table (Sec. 3,
+// Algorithm 1; tombstone erase, Sec. 4.4).
+//
+// Work layout.  Each warp owns a contiguous slice of the operation batch.
+// Its lanes form 32/G groups of G lanes; a group probes one key at a time
+// over an aligned window of W = G*V cells (V = 2 cells per lane for G = 1,
+// fetched with one 256-bit load = one 32-byte DRAM sector; V = 1 otherwise).
+// A group that finishes its key immediately takes the next key of the warp's
+// slice ("refill"), so every probe step of the warp issues loads for all of
+// its groups instead of idling while the slowest probe of a fixed set of 32
+// keys finishes.  Keys loaded in the same refill step are pre-reduced with
+// __match_any_sync: one leader per distinct key performs the table operation
+// (with the summed value for insertOrUpdate(add)); the others resolve at once
+// as "not inserted / updated / not erased", which is a valid linearization
+// (they are ordered right after the leader).
+//
+// Probe step (Algorithm 1).  The first cell in probe order that holds the key
+// or is empty decides: find reads it; erase CASes its key to the tombstone;
+// insert / insertOrUpdate CAS <0,0> -> <k,d> into an empty cell and, if the
+// CAS reveals the same key, apply the update (fetch-and-add or store, the
+// specialised atomicUpdate of Sec. 3); a CAS that reveals another key moves
+// on to the next cell (Algorithm 1 re-reads the cell; the CAS already
+// returned its content).  Keys only ever change empty -> key -> tombstone,
+// so a stale window can only show "empty" too early, which the CAS corrects.
+// Every probe is bounded by c cells; an insert that sees all c cells reports
+// "table full".
+#pragma once
+
+#include "cht_internal.h"
+
+namespace cht {
+
+constexpr int kOpBlock = 256;
+
+template <int G>
+struct GroupConsts {
+    static constexpr u32 leaders = G == 1 ? 0xffffffffu
+                                 : G == 2 ? 0x55555555u
+                                 : G == 4 ? 0x11111111u
+                                 : G == 8 ? 0x01010101u
+                                 : G == 16 ? 0x00010001u
+                                           : 0x00000001u;
+};
+
+// Outcome of a leader's atomic step.
+enum : int { kStepDoneNo = 0, kStepDoneYes = 1, kStepContinue = 2 };
+
+template <int MODE>
+__device__ __forceinline__ int modify_at(Cell* cp, bool is_key, u64 key, u64 d) {
+    if (is_key) {
+        if (MODE == kInsert) return kStepDoneNo;
+        if (MODE == kIouAdd) { atomicAdd(&cp->val, d); return kStepDoneNo; }
+        if (MODE == kIouOverwrite) { atomicExch(&cp->val, d); return kStepDoneNo; }
+        // kErase: 1-word CAS of the key to the tombstone, value untouched.
+        const u64 old = atomicCAS(&cp->key, key, kTomb);
+        return old == key ? kStepDoneYes : kStepDoneNo;
+    }
+    // empty cell
+    if (MODE == kErase) return kStepDoneNo;
+    Cell expect;
+    expect.key = kEmpty;
+    expect.val = 0;
+    Cell desired;
+    desired.key = key;
+    desired.val = d;
+    const Cell old = cas_cell(cp, expect, desired);
+    if (old.key == kEmpty && old.val == 0) return kStepDoneYes;
+    if (old.key == key) {
+        if (MODE == kIouAdd) atomicAdd(&cp->val, d);
+        if (MODE == kIouOverwrite) atomicExch(&cp->val, d);
+        return kStepDoneNo;
+    }
+    return kStepContinue;
+}
+
+template <int G, int MODE>
+__global__ void __launch_bounds__(kOpBlock) op_kernel(OpArgs a) {
+    constexpr int V = (G == 1) ? 2 : 1;
+    constexpr u32 W = G * V;
+    constexpr u32 FULL = 0xffffffffu;
+    constexpr bool kModify = MODE != kFind;
+    constexpr bool kHasVals = MODE == kInsert || MODE == kIouAdd || MODE == kIouOverwrite;
+
+    const u64 cap = 1ull << a.log2c;
+    const u64 cmask = cap - 1;
+    const u32 shift = 64u - a.log2c;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int g0 = lane & ~(G - 1);
+    const u32 group_lanes = (G == 32) ? FULL : (((1u << G) - 1u) << g0);
+    const u32 below_group = (1u << g0) - 1u;
+
+    const u64 warp = (u64(blockIdx.x) * kOpBlock + threadIdx.x) >> 5;
+    const u64 nwarps = (u64(gridDim.x) * kOpBlock) >> 5;
+    const u64 per = (a.n + nwarps - 1) / nwarps;
+    u64 next = warp * per;
+    const u64 end = next + per < a.n ? next + per : a.n;
+
+    bool active = false;
+    u64 idx = 0, key = 0, d = 0, pos = 0, probed = 0;
+    u64 n_ins = 0, n_del = 0;
+    u32 sbits = 0;
+
+    for (;;) {
+        // ---- refill idle groups from this warp's slice
+        bool fresh = false;
+        const u32 idle = __ballot_sync(FULL, !active) & GroupConsts<G>::leaders;
+        if (idle != 0 && next < end) {
+            if (!active) {
+                const u64 my = next + __popc(idle & below_group);
+                if (my < end) {
+                    idx = my;
+                    key = ld_stream(a.keys + idx);
+                    if (kHasVals) d = ld_stream(a.vals + idx);
+                    if (is_reserved(key)) {
+                        if (gl == 0) {
+                            if (a.codes) a.codes[idx] = kCodeReserved;
+                            if (MODE == kFind) a.vals_out[idx] = 0;
+                        }
+                        sbits |= kReserved;
+                    } else {
+                        fresh = true;
+                        active = true;
+                        pos = home_of(key, shift);
+                        probed = 0;
+                    }
+                }
+            }
+            next += __popc(idle);
+        }
+
+        // ---- pre-reduce equal keys loaded in this step (modifying modes)
+        if (kModify) {
+            const u32 fm = __ballot_sync(FULL, fresh && gl == 0);
+            if (fm & (fm - 1u)) {
+                bool dup = false;
+                if (fresh && gl == 0) {
+                    const u32 same = __match_any_sync(fm, key);
+                    const int lead = __ffs(same) - 1;
+                    if (MODE == kIouAdd) {
+                        u32 rem = same;
+                        u64 total = 0;
+                        while (__any_sync(fm, rem != 0)) {
+                            const int src = rem ? __ffs(rem) - 1 : lane;
+                            const u64 x = __shfl_sync(fm, d, src);
+                            if (rem) {
+                                total += x;
+                                rem &= rem - 1u;
+                            }
+                        }
+                        d = total;
+                    }
+                    dup = lane != lead;
+                }
+                if (G > 1) {
+                    dup = __shfl_sync(FULL, dup, g0);
+                    if (MODE == kIouAdd) d = __shfl_sync(FULL, d, g0);
+                }
+                if (dup) {
+                    if (gl == 0 && a.codes) a.codes[idx] = kNo;
+                    active = false;
+                }
+            }
+        }
+
+        if (!__any_sync(FULL, active)) {
+            if (next >= end) break;
+            continue;
+        }
+
+        // ---- one probe step: load the window holding `pos`
+        const u64 base = pos & ~u64(W - 1);
+        const u32 first = u32(pos - base);
+        u64 k0 = 0, v0 = 0, k1 = 0, v1 = 0;
+        int hit = -1;
+        bool match = false;
+        u64 hv = 0;
+        if (active) {
+            const Cell* p = a.cells + base + u32(gl) * V;
+            if (V == 2) {
+                if (kModify) ld_pair_cg(p, k0, v0, k1, v1);
+                else ld_pair_nc(p, k0, v0, k1, v1);
+            } else {
+                if (kModify) ld_cell_cg(p, k0, v0);
+                else ld_cell_nc(p, k0, v0);
+            }
+            const u32 o0 = u32(gl) * V;
+            if (o0 >= first && (k0 == key || k0 == kEmpty)) {
+                hit = int(o0);
+                match = k0 == key;
+                hv = v0;
+            } else if (V == 2 && o0 + 1 >= first && (k1 == key || k1 == kEmpty)) {
+                hit = int(o0 + 1);
+                match = k1 == key;
+                hv = v1;
+            }
+        }
+        int ghit = hit;
+        bool gmatch = match;
+        u64 gval = hv;
+        if (G > 1) {
+            const u32 b = __ballot_sync(FULL, hit >= 0) & group_lanes;
+            const int src = b ? __ffs(b) - 1 : lane;
+            ghit = __shfl_sync(FULL, hit, src);
+            gmatch = __shfl_sync(FULL, int(match), src) != 0;
+            if (MODE == kFind) gval = __shfl_sync(FULL, hv, src);
+        }
+
+        int outcome = kStepContinue;
+        if (active && ghit >= 0) {
+            if (MODE == kFind) {
+                if (gl == 0) {
+                    a.vals_out[idx] = gmatch ? gval : 0;
+                    if (a.codes) a.codes[idx] = gmatch ? kYes : kNo;
+                }
+                active = false;
+            } else if (gl == 0) {
+                outcome = modify_at<MODE>(a.cells + base + u32(ghit), gmatch, key, d);
+            }
+        }
+        if (kModify && G > 1) outcome = __shfl_sync(FULL, outcome, g0);
+
+        if (active) {
+            if (ghit < 0) {
+                probed += W - first;
+                pos = (base + W) & cmask;
+            } else if (kModify) {
+                if (outcome == kStepContinue) {
+                    probed += u32(ghit) - first + 1;
+                    pos = (base + u32(ghit) + 1) & cmask;
+                } else {
+                    if (gl == 0) {
+                        if (a.codes) a.codes[idx] = (unsigned char)outcome;
+                        if (outcome == kStepDoneYes) {
+                            if (MODE == kErase) ++n_del;
+                            else ++n_ins;
+                        }
+                    }
+                    active = false;
+                }
+            }
+            if (active && probed >= cap) {
+                // every cell was examined without a decision
+                if (gl == 0) {
+                    if (MODE == kFind) {
+                        a.vals_out[idx] = 0;
+                        if (a.codes) a.codes[idx] = kNo;
+                    } else if (MODE == kErase) {
+                        if (a.codes) a.codes[idx] = kNo;
+                    } else {
+                        if (a.codes) a.codes[idx] = kCodeFull;
+                    }
+                }
+                if (MODE != kFind && MODE != kErase) sbits |= kFull;
+                active = false;
+            }
+        }
+    }
+
+    // ---- per-warp aggregation of the counters and status bits
+    if (kModify) {
+        for (int o = 16; o > 0; o >>= 1) {
+            n_ins += __shfl_xor_sync(FULL, n_ins, o);
+            n_del += __shfl_xor_sync(FULL, n_del, o);
+        }
+    }
+    const u32 any_status = __reduce_or_sync(FULL, sbits);
+    if (lane == 0) {
+        if (n_ins) atomicAdd(&a.st->I, n_ins);
+        if (n_del) atomicAdd(&a.st->D, n_del);
+        if (any_status) atomicOr(&a.st->status, any_status);
+    }
+}
+
+}  // namespace cht

@@ -1,0 +1,605 @@
+// Host runtime and C ABI of libcht (declared in include/cht.h).
+//
+// The runtime owns the table memory, validates arguments, stages host
+// arrays through device buffers, and applies the growth policy of growable
+// tables: before a batch that could push the number of non-empty cells I
+// past alpha*c it reads I back, inserts a chunk that fits, and migrates the
+// table -- doubling it when more than alpha*c/2 elements are live, otherwise
+// migrating at the same size to purge tombstones (Sec. 4.3.2 trigger and
+// growth factor; Sec. 4.4 size choice by the live count I - D).  Migration
+// and operations are ordered on the caller's stream, which gives the
+// "synchronized" growing protocol of Sec. 4.3.2: no operation runs while a
+// migration does, so fetch-and-add updates stay legal.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/cht.h"
+#include "cht_internal.h"
+
+using cht::Cell;
+using cht::DevState;
+using cht::u32;
+using cht::u64;
+
+namespace {
+
+constexpr u64 kMinCap = 64;
+constexpr u32 kMaxLog2 = 40;
+
+std::atomic<u64> g_launches{0};
+std::atomic<u64> g_mem_in_use{0};
+std::atomic<u64> g_mem_limit{0};
+std::mutex g_pool_mu;
+bool g_pool_ready[64] = {};
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+// Keep freed stream-ordered memory in the pool so repeated staging and
+// migrations do not go back to the driver.
+void prepare_pool(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= 64 || g_pool_ready[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        u64 thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    g_pool_ready[dev] = true;
+}
+
+// Stream-ordered allocation with the library-wide memory cap.
+cht_status lib_alloc(void** p, u64 bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    const u64 lim = g_mem_limit.load();
+    const u64 now = g_mem_in_use.fetch_add(bytes) + bytes;
+    if (lim != 0 && now > lim) {
+        g_mem_in_use.fetch_sub(bytes);
+        return CHT_ERR_OOM;
+    }
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_mem_in_use.fetch_sub(bytes);
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? CHT_ERR_OOM : CHT_ERR_CUDA;
+    }
+    if ((reinterpret_cast<uintptr_t>(*p) & 255u) != 0) {  // cells need 32-byte alignment
+        cudaFreeAsync(*p, s);
+        g_mem_in_use.fetch_sub(bytes);
+        *p = nullptr;
+        return CHT_ERR_CUDA;
+    }
+    return CHT_OK;
+}
+
+void lib_free(void* p, u64 bytes, cudaStream_t s) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    cudaFreeAsync(p, s);
+    g_mem_in_use.fetch_sub(bytes);
+}
+
+bool is_host_pointer(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+// Stages host arrays of one call through device buffers on the stream.
+class Staging {
+  public:
+    explicit Staging(cudaStream_t s) : s_(s) {}
+    ~Staging() { release(); }
+
+    // Device view of an input array (copied in when it lives on the host).
+    cht_status in(const void* p, u64 bytes, const void** out) {
+        *out = p;
+        if (!p || bytes == 0 || !is_host_pointer(p)) return CHT_OK;
+        void* d = nullptr;
+        cht_status st = lib_alloc(&d, bytes, s_);
+        if (st != CHT_OK) return st;
+        bufs_.push_back({d, bytes});
+        if (cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s_) != cudaSuccess) return CHT_ERR_CUDA;
+        *out = d;
+        return CHT_OK;
+    }
+
+    // Device view of an output array (copied back by finish()).
+    cht_status out(void* p, u64 bytes, void** out) {
+        *out = p;
+        if (!p || bytes == 0 || !is_host_pointer(p)) return CHT_OK;
+        void* d = nullptr;
+        cht_status st = lib_alloc(&d, bytes, s_);
+        if (st != CHT_OK) return st;
+        bufs_.push_back({d, bytes});
+        backs_.push_back({p, d, bytes});
+        *out = d;
+        return CHT_OK;
+    }
+
+    cht_status finish() {
+        cht_status r = CHT_OK;
+        for (const Back& b : backs_)
+            if (cudaMemcpyAsync(b.host, b.dev, b.bytes, cudaMemcpyDeviceToHost, s_) != cudaSuccess)
+                r = CHT_ERR_CUDA;
+        backs_.clear();
+        release();
+        return r;
+    }
+
+  private:
+    struct Buf {
+        void* p;
+        u64 bytes;
+    };
+    struct Back {
+        void* host;
+        void* dev;
+        u64 bytes;
+    };
+    void release() {
+        for (const Buf& b : bufs_) lib_free(b.p, b.bytes, s_);
+        bufs_.clear();
+    }
+    cudaStream_t s_;
+    std::vector<Buf> bufs_;
+    std::vector<Back> backs_;
+};
+
+cht_config default_config() {
+    cht_config c;
+    c.group_width = 1;
+    c.ctas_per_sm = 0;
+    c.migrate_tile = 2048;
+    c.alpha = 0.5;
+    return c;
+}
+
+bool valid_config(const cht_config& c) {
+    const int g = c.group_width;
+    if (!(g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32)) return false;
+    if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64) return false;
+    const int t = c.migrate_tile;
+    if (t != 0 && (t < 256 || t > 8192 || (t & (t - 1)) != 0)) return false;
+    if (!(c.alpha > 0.0 && c.alpha < 1.0)) return false;
+    return true;
+}
+
+u32 log2_ceil_cap(u64 capacity) {
+    u32 l = 6;
+    while (l < kMaxLog2 && (1ull << l) < capacity) ++l;
+    return l;
+}
+
+}  // namespace
+
+struct cht_table {
+    Cell* cells = nullptr;
+    u32 log2c = 0;
+    DevState* st = nullptr;
+    int growable = 0;
+    int device = 0;
+    cht_config cfg = default_config();
+    u64 i_bound = 0;      // upper bound on the device's I
+    bool i_exact = true;  // i_bound equals the device's I
+    cudaStream_t last = nullptr;
+
+    u64 cap() const { return 1ull << log2c; }
+};
+
+namespace {
+
+cht_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return CHT_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? CHT_ERR_OOM : CHT_ERR_CUDA;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+cht_status read_state(cht_table* h, DevState* out, cudaStream_t s) {
+    if (cudaMemcpyAsync(out, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CHT_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
+// Migrate h into 2^new_log2 cells (new_log2 >= log2c).  `live` is the exact
+// live count if known (else ~0).  Allocates first: on failure h is unchanged.
+cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
+    Cell* dst = nullptr;
+    const u64 bytes = (1ull << new_log2) * sizeof(Cell);
+    cht_status r = lib_alloc(reinterpret_cast<void**>(&dst), bytes, s);
+    if (r != CHT_OK) return r;
+    // I and D restart (the kernel accumulates the moved count into I)
+    if (cudaMemsetAsync(&h->st->I, 0, 2 * sizeof(u64), s) != cudaSuccess ||
+        cudaMemsetAsync(&h->st->mig_fail, 0, sizeof(u32), s) != cudaSuccess) {
+        lib_free(dst, bytes, s);
+        return CHT_ERR_CUDA;
+    }
+    cudaError_t e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, h->cfg.migrate_tile, s);
+    if (e != cudaSuccess) {
+        lib_free(dst, bytes, s);
+        return cuda_status(e);
+    }
+    lib_free(h->cells, h->cap() * sizeof(Cell), s);
+    h->cells = dst;
+    h->log2c = new_log2;
+    if (live != ~0ull) {
+        h->i_bound = live;
+        h->i_exact = true;
+    } else {
+        h->i_exact = false;  // new I <= old I, so i_bound stays an upper bound
+    }
+    return CHT_OK;
+}
+
+cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals, u64* vals_out,
+                  unsigned char* codes, u64 n, cudaStream_t s) {
+    cht::OpArgs a;
+    a.cells = h->cells;
+    a.log2c = h->log2c;
+    a.keys = keys;
+    a.vals = vals;
+    a.vals_out = vals_out;
+    a.codes = codes;
+    a.n = n;
+    a.st = h->st;
+    return cuda_status(cht::launch_op(mode, a, h->cfg.group_width, h->cfg.ctas_per_sm, s));
+}
+
+// insert / insert_or_update with the growth policy of growable tables.
+cht_status run_modify(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals,
+                      unsigned char* codes, u64 n, cudaStream_t s) {
+    if (!h->growable) {
+        h->i_bound += n;
+        h->i_exact = false;
+        return launch(h, mode, keys, vals, nullptr, codes, n, s);
+    }
+    u64 done = 0;
+    while (done < n) {
+        const u64 limit = u64(std::floor(h->cfg.alpha * double(h->cap())));
+        const u64 rest = n - done;
+        if (h->i_bound + rest <= limit) {
+            cht_status r = launch(h, mode, keys + done, vals + done, nullptr, codes ? codes + done : nullptr,
+                                  rest, s);
+            if (r != CHT_OK) return r;
+            h->i_bound += rest;
+            h->i_exact = false;
+            break;
+        }
+        u64 I = h->i_bound, D = 0;
+        bool have_d = false;
+        if (!h->i_exact) {
+            DevState ds;
+            cht_status r = read_state(h, &ds, s);
+            if (r != CHT_OK) return r;
+            I = ds.I;
+            D = ds.D;
+            have_d = true;
+            h->i_bound = I;
+            h->i_exact = true;
+        }
+        if (I >= limit) {
+            if (!have_d) {
+                DevState ds;
+                cht_status r = read_state(h, &ds, s);
+                if (r != CHT_OK) return r;
+                D = ds.D;
+            }
+            const u64 live = I - D;
+            const u64 half = u64(std::floor(h->cfg.alpha * double(h->cap()) / 2.0));
+            u32 nl = h->log2c + (live > half ? 1u : 0u);
+            if (nl > kMaxLog2) return CHT_ERR_OOM;
+            cht_status r = do_migrate(h, nl, live, s);
+            if (r != CHT_OK) return r;
+            continue;
+        }
+        const u64 chunk = (limit - I) < rest ? (limit - I) : rest;
+        cht_status r = launch(h, mode, keys + done, vals + done, nullptr, codes ? codes + done : nullptr,
+                              chunk, s);
+        if (r != CHT_OK) return r;
+        h->i_bound += chunk;
+        h->i_exact = false;
+        done += chunk;
+    }
+    return CHT_OK;
+}
+
+}  // namespace
+
+namespace cht {
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int sm_count() {
+    static std::atomic<int> cached[64];
+    const int dev = current_device();
+    if (dev < 0 || dev >= 64) return 1;
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (v < 1) v = 1;
+        cached[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+}  // namespace cht
+
+extern "C" {
+
+cht_status cht_create(uint64_t capacity, int growable, cht_stream_t stream, cht_handle* out) {
+    if (!out) return CHT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (capacity > (1ull << kMaxLog2)) return CHT_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cht_table* h = new (std::nothrow) cht_table();
+    if (!h) return CHT_ERR_OOM;
+    h->device = current_device();
+    prepare_pool(h->device);
+    h->log2c = log2_ceil_cap(capacity < kMinCap ? kMinCap : capacity);
+    h->growable = growable ? 1 : 0;
+    cht_status r = lib_alloc(reinterpret_cast<void**>(&h->cells), h->cap() * sizeof(Cell), s);
+    if (r != CHT_OK) {
+        delete h;
+        return r;
+    }
+    r = lib_alloc(reinterpret_cast<void**>(&h->st), sizeof(DevState), s);
+    if (r != CHT_OK) {
+        lib_free(h->cells, h->cap() * sizeof(Cell), s);
+        delete h;
+        return r;
+    }
+    if (cudaMemsetAsync(h->cells, 0, h->cap() * sizeof(Cell), s) != cudaSuccess ||
+        cudaMemsetAsync(h->st, 0, sizeof(DevState), s) != cudaSuccess) {
+        lib_free(h->cells, h->cap() * sizeof(Cell), s);
+        lib_free(h->st, sizeof(DevState), s);
+        delete h;
+        return CHT_ERR_CUDA;
+    }
+    h->last = s;
+    *out = h;
+    return CHT_OK;
+}
+
+cht_status cht_destroy(cht_handle h) {
+    if (!h) return CHT_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    lib_free(h->cells, h->cap() * sizeof(Cell), h->last);
+    lib_free(h->st, sizeof(DevState), h->last);
+    cudaError_t e = cudaStreamSynchronize(h->last);
+    delete h;
+    return cuda_status(e);
+}
+
+cht_status cht_set_config(cht_handle h, const cht_config* cfg) {
+    if (!h) return CHT_ERR_INVALID_ARG;
+    cht_config c = cfg ? *cfg : default_config();
+    if (c.migrate_tile == 0) c.migrate_tile = 2048;
+    if (!valid_config(c)) return CHT_ERR_INVALID_ARG;
+    h->cfg = c;
+    return CHT_OK;
+}
+
+cht_status cht_get_config(cht_handle h, cht_config* cfg) {
+    if (!h || !cfg) return CHT_ERR_INVALID_ARG;
+    *cfg = h->cfg;
+    return CHT_OK;
+}
+
+static cht_status modify_call(cht_handle h, cht::Mode mode, const uint64_t* keys, const uint64_t* vals,
+                              uint64_t n, uint8_t* codes, cht_stream_t stream) {
+    if (!h || (n > 0 && (!keys || !vals))) return CHT_ERR_INVALID_ARG;
+    if (n == 0) return CHT_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last = s;
+    Staging stg(s);
+    const void *dk, *dv;
+    void* dc;
+    cht_status r = stg.in(keys, n * 8, &dk);
+    if (r == CHT_OK) r = stg.in(vals, n * 8, &dv);
+    if (r == CHT_OK) r = stg.out(codes, n, &dc);
+    if (r != CHT_OK) return r;
+    r = run_modify(h, mode, static_cast<const u64*>(dk), static_cast<const u64*>(dv),
+                   static_cast<unsigned char*>(dc), n, s);
+    cht_status f = stg.finish();
+    return r != CHT_OK ? r : f;
+}
+
+cht_status cht_insert(cht_handle h, const uint64_t* keys, const uint64_t* vals, uint64_t n,
+                      uint8_t* inserted, cht_stream_t stream) {
+    return modify_call(h, cht::kInsert, keys, vals, n, inserted, stream);
+}
+
+cht_status cht_insert_or_update(cht_handle h, const uint64_t* keys, const uint64_t* vals, uint64_t n,
+                                cht_update_op op, uint8_t* inserted, cht_stream_t stream) {
+    if (op != CHT_ADD && op != CHT_OVERWRITE) return CHT_ERR_INVALID_ARG;
+    return modify_call(h, op == CHT_ADD ? cht::kIouAdd : cht::kIouOverwrite, keys, vals, n, inserted,
+                       stream);
+}
+
+cht_status cht_find(cht_handle h, const uint64_t* keys, uint64_t n, uint64_t* vals_out, uint8_t* found,
+                    cht_stream_t stream) {
+    if (!h || (n > 0 && (!keys || !vals_out))) return CHT_ERR_INVALID_ARG;
+    if (n == 0) return CHT_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last = s;
+    Staging stg(s);
+    const void* dk;
+    void *dv, *dc;
+    cht_status r = stg.in(keys, n * 8, &dk);
+    if (r == CHT_OK) r = stg.out(vals_out, n * 8, &dv);
+    if (r == CHT_OK) r = stg.out(found, n, &dc);
+    if (r != CHT_OK) return r;
+    r = launch(h, cht::kFind, static_cast<const u64*>(dk), nullptr, static_cast<u64*>(dv),
+               static_cast<unsigned char*>(dc), n, s);
+    cht_status f = stg.finish();
+    return r != CHT_OK ? r : f;
+}
+
+cht_status cht_erase(cht_handle h, const uint64_t* keys, uint64_t n, uint8_t* erased, cht_stream_t stream) {
+    if (!h || (n > 0 && !keys)) return CHT_ERR_INVALID_ARG;
+    if (n == 0) return CHT_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last = s;
+    Staging stg(s);
+    const void* dk;
+    void* dc;
+    cht_status r = stg.in(keys, n * 8, &dk);
+    if (r == CHT_OK) r = stg.out(erased, n, &dc);
+    if (r != CHT_OK) return r;
+    r = launch(h, cht::kErase, static_cast<const u64*>(dk), nullptr, nullptr, static_cast<unsigned char*>(dc),
+               n, s);
+    cht_status f = stg.finish();
+    return r != CHT_OK ? r : f;
+}
+
+cht_status cht_migrate(cht_handle h, uint64_t new_capacity, cht_stream_t stream) {
+    if (!h) return CHT_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last = s;
+    u32 nl;
+    u64 live = ~0ull;
+    if (new_capacity == 0) {
+        DevState ds;
+        cht_status r = read_state(h, &ds, s);
+        if (r != CHT_OK) return r;
+        live = ds.I - ds.D;
+        const u64 half = u64(std::floor(h->cfg.alpha * double(h->cap()) / 2.0));
+        nl = h->log2c + (live > half ? 1u : 0u);
+    } else {
+        if (new_capacity > (1ull << kMaxLog2)) return CHT_ERR_INVALID_ARG;
+        nl = log2_ceil_cap(new_capacity);
+    }
+    if (nl < h->log2c || nl > kMaxLog2) return CHT_ERR_INVALID_ARG;
+    return do_migrate(h, nl, live, s);
+}
+
+cht_status cht_size(cht_handle h, uint64_t* live, uint64_t* nonempty, uint64_t* capacity,
+                    cht_stream_t stream) {
+    if (!h) return CHT_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DevState ds;
+    cht_status r = read_state(h, &ds, s);
+    if (r != CHT_OK) return r;
+    h->i_bound = ds.I;
+    h->i_exact = true;
+    if (live) *live = ds.I - ds.D;
+    if (nonempty) *nonempty = ds.I;
+    if (capacity) *capacity = h->cap();
+    if (ds.status & CHT_STATUS_FULL) return CHT_ERR_TABLE_FULL;
+    if (ds.status & CHT_STATUS_RESERVED) return CHT_ERR_RESERVED_KEY;
+    return CHT_OK;
+}
+
+cht_status cht_get_status(cht_handle h, uint32_t* bits, cht_stream_t stream) {
+    if (!h || !bits) return CHT_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DevState ds;
+    cht_status r = read_state(h, &ds, s);
+    if (r != CHT_OK) return r;
+    *bits = ds.status;
+    if (cudaMemsetAsync(&h->st->status, 0, sizeof(u32), s) != cudaSuccess) return CHT_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
+cht_status cht_export(cht_handle h, uint64_t* keys_out, uint64_t* vals_out, uint64_t max_n, uint64_t* n_out,
+                      cht_stream_t stream) {
+    if (!h || !n_out || (max_n > 0 && !keys_out)) return CHT_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last = s;
+    Staging stg(s);
+    void *dk = nullptr, *dv = nullptr;
+    cht_status r = stg.out(keys_out, max_n * 8, &dk);
+    if (r == CHT_OK && vals_out) r = stg.out(vals_out, max_n * 8, &dv);
+    if (r != CHT_OK) return r;
+    if (cudaMemsetAsync(&h->st->export_pos, 0, sizeof(u64), s) != cudaSuccess) return CHT_ERR_CUDA;
+    r = cuda_status(cht::launch_export(h->cells, h->log2c, static_cast<u64*>(dk), static_cast<u64*>(dv), max_n,
+                                       h->st, s));
+    cht_status f = stg.finish();
+    if (r != CHT_OK) return r;
+    if (f != CHT_OK) return f;
+    DevState ds;
+    r = read_state(h, &ds, s);
+    if (r != CHT_OK) return r;
+    *n_out = ds.export_pos;
+    return ds.export_pos > max_n ? CHT_ERR_INVALID_ARG : CHT_OK;
+}
+
+cht_status cht_copy_cells(cht_handle h, uint64_t* cells_out, uint64_t max_cells, uint64_t* n_cells,
+                          cht_stream_t stream) {
+    if (!h || !cells_out) return CHT_ERR_INVALID_ARG;
+    if (n_cells) *n_cells = h->cap();
+    if (max_cells < h->cap()) return CHT_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return cuda_status(cudaMemcpyAsync(cells_out, h->cells, h->cap() * sizeof(Cell), cudaMemcpyDefault, s));
+}
+
+cht_status cht_clear(cht_handle h, cht_stream_t stream) {
+    if (!h) return CHT_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last = s;
+    if (cudaMemsetAsync(h->cells, 0, h->cap() * sizeof(Cell), s) != cudaSuccess) return CHT_ERR_CUDA;
+    if (cudaMemsetAsync(h->st, 0, sizeof(DevState), s) != cudaSuccess) return CHT_ERR_CUDA;
+    h->i_bound = 0;
+    h->i_exact = true;
+    return CHT_OK;
+}
+
+cht_status cht_set_memory_limit(uint64_t bytes) {
+    g_mem_limit.store(bytes);
+    return CHT_OK;
+}
+
+uint64_t cht_memory_in_use(void) { return g_mem_in_use.load(); }
+
+uint64_t cht_launch_count(void) { return g_launches.load(); }
+
+const char* cht_status_string(cht_status s) {
+    switch (s) {
+        case CHT_OK: return "ok";
+        case CHT_ERR_INVALID_ARG: return "invalid argument";
+        case CHT_ERR_OOM: return "out of device memory";
+        case CHT_ERR_CUDA: return "CUDA error";
+        case CHT_ERR_TABLE_FULL: return "table full";
+        case CHT_ERR_RESERVED_KEY: return "reserved key (0 or ~0)";
+        case CHT_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+int cht_version(void) { return 100; }
+
+}  // extern "C"

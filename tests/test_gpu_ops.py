@@ -1,0 +1,237 @@
+"""GPU parity of the batched operations against the CPU oracle (through the C ABI).
+
+Bit-exact where the result is unique (find values and codes, aggregated
+sums, final key sets, occupied cells); set-valued where duplicates inside one
+batch allow several correct outcomes (which op inserted / erased, which value
+an overwrite kept).  Sizes span many CTAs and warps and leave ragged tails.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import (assert_one_winner, assert_same_live_set, codes_buf, ops_by_key, to_dev,
+                         to_np_u8, to_np_u64, vals_buf)
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = [1, 2, 4, 8, 16, 32]
+
+
+def _table(cht, cap, g=1, growable=False, **cfg):
+    t = cht.Table(cap, growable=growable)
+    t.set_config(group_width=g, **cfg)
+    return t
+
+
+@pytest.mark.parametrize("g", GROUPS)
+@pytest.mark.parametrize("load", [0.5, 0.9])
+def test_insert_find_uniform(cuda_lib, oracle_mod, g, load):
+    log2c = 16
+    c = 1 << log2c
+    wl = W.bounded_workload(log2c, loads=(load,), n_find=(c // 3) + 17)
+    n = wl["counts"][load]
+    keys, vals = wl["keys"][:n], wl["vals"][:n]
+    t = _table(cuda_lib, c, g)
+    o = oracle_mod.OracleTable(c)
+    codes = codes_buf(n)
+    t.insert(to_dev(keys), to_dev(vals), codes)
+    assert (to_np_u8(codes) == 1).all()
+    assert (o.insert(keys, vals) == 1).all()
+    live, ne, cap = t.size(check=True)
+    assert (live, ne, cap) == (n, n, c)
+    # occupied cells depend only on the multiset of homes: equal to the oracle
+    gcells = to_np_u64(t.cells())
+    assert np.array_equal(gcells.reshape(-1, 2)[:, 0] != 0, o.cells()[:, 0] != 0)
+    for q in (wl["hits"][load], wl["misses"]):
+        vo, fo = vals_buf(q.size), codes_buf(q.size)
+        t.find(to_dev(q), vo, fo)
+        ev, ef = o.find(q)
+        assert np.array_equal(to_np_u8(fo), ef)
+        assert np.array_equal(to_np_u64(vo), ev)
+    assert_same_live_set(t, o)
+
+
+@pytest.mark.parametrize("g", [1, 8])
+def test_insert_duplicates_one_winner(cuda_lib, oracle_mod, g):
+    c = 1 << 14
+    base = W.uniform_keys(3000, seed=51)
+    rng = np.random.default_rng(1)
+    pre = base[:500]
+    keys = base[rng.integers(0, base.size, 9001)]
+    vals = rng.integers(1, 1 << 62, keys.size).astype(np.uint64)
+    t = _table(cuda_lib, c, g)
+    t.insert(to_dev(pre), to_dev(pre))
+    codes = codes_buf(keys.size)
+    t.insert(to_dev(keys), to_dev(vals), codes)
+    cs = to_np_u8(codes)
+    pre_set = set(pre.tolist())
+    assert_one_winner(keys, cs, lambda k: k not in pre_set)
+    # stored value: untouched for pre-existing keys; else one of the key's values
+    uk = np.unique(keys)
+    vo = vals_buf(uk.size)
+    t.find(to_dev(uk), vo)
+    got = dict(zip(uk.tolist(), to_np_u64(vo).tolist()))
+    by = ops_by_key(keys, vals, cs)
+    for k, rows in by.items():
+        if k in pre_set:
+            assert got[k] == k
+        else:
+            winner = [v for v, code in rows if code == 1]
+            assert got[k] == winner[0]
+    live, _, _ = t.size()
+    assert live == len(pre_set | set(keys.tolist()))
+
+
+@pytest.mark.parametrize("g", GROUPS)
+@pytest.mark.parametrize("s", [0.5, 1.25, 1.5])
+def test_insert_or_update_add_exact(cuda_lib, oracle_mod, g, s):
+    c = 1 << 17
+    keys = W.zipf_keys(150_001, s, n_ranks=1 << 15, seed=52)
+    vals = (np.arange(keys.size, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)) | np.uint64(1)
+    pre = np.unique(keys)[::5]
+    t = _table(cuda_lib, c, g)
+    o = oracle_mod.OracleTable(c)
+    t.insert(to_dev(pre), to_dev(pre))
+    o.insert(pre, pre)
+    codes = codes_buf(keys.size)
+    t.insert_or_update(to_dev(keys), to_dev(vals), cuda_lib.ADD, codes)
+    o.insert_or_update(keys, vals, oracle_mod.ADD)
+    pre_set = set(pre.tolist())
+    assert_one_winner(keys, to_np_u8(codes), lambda k: k not in pre_set)
+    assert_same_live_set(t, o)  # sums are order-free: bit-exact
+    live, ne, _ = t.size(check=True)
+    assert live == o.live and ne == o.nonempty
+
+
+@pytest.mark.parametrize("g", [1, 4])
+def test_insert_or_update_overwrite(cuda_lib, oracle_mod, g):
+    c = 1 << 15
+    keys = W.zipf_keys(40_000, 1.0, n_ranks=1 << 12, seed=53)
+    vals = np.arange(1, keys.size + 1, dtype=np.uint64)
+    pre = np.unique(keys)[::3]
+    t = _table(cuda_lib, c, g)
+    t.insert(to_dev(pre), to_dev(pre))
+    codes = codes_buf(keys.size)
+    t.insert_or_update(to_dev(keys), to_dev(vals), cuda_lib.OVERWRITE, codes)
+    pre_set = set(pre.tolist())
+    assert_one_winner(keys, to_np_u8(codes), lambda k: k not in pre_set)
+    uk = np.unique(keys)
+    vo = vals_buf(uk.size)
+    t.find(to_dev(uk), vo)
+    by = ops_by_key(keys, vals)
+    for k, v in zip(uk.tolist(), to_np_u64(vo).tolist()):
+        assert v in {r[0] for r in by[k]}
+
+
+@pytest.mark.parametrize("g", [1, 2, 8, 32])
+def test_erase_and_tombstones(cuda_lib, oracle_mod, g):
+    c = 1 << 15
+    keys = W.uniform_keys(20_000, seed=54)
+    t = _table(cuda_lib, c, g)
+    o = oracle_mod.OracleTable(c)
+    t.insert(to_dev(keys), to_dev(keys))
+    o.insert(keys, keys)
+    rng = np.random.default_rng(2)
+    victims = np.concatenate([keys[rng.integers(0, keys.size, 12_000)],
+                              W.uniform_keys(777, start=10**6, seed=54)])  # absent ones too
+    codes = codes_buf(victims.size)
+    t.erase(to_dev(victims), codes)
+    o.erase(victims)
+    present = set(keys.tolist())
+    assert_one_winner(victims, to_np_u8(codes), lambda k: k in present)
+    live, ne, _ = t.size()
+    assert live == o.live and ne == o.nonempty == keys.size
+    # finds pass over tombstones
+    vo, fo = vals_buf(keys.size), codes_buf(keys.size)
+    t.find(to_dev(keys), vo, fo)
+    ev, ef = o.find(keys)
+    assert np.array_equal(to_np_u8(fo), ef) and np.array_equal(to_np_u64(vo), ev)
+    # inserting again after erase uses fresh cells (tombstones are not reused)
+    again = victims[: 100]
+    t.insert(to_dev(again), to_dev(again))
+    o.insert(again, again)
+    assert_same_live_set(t, o)
+    assert t.size()[1] == o.nonempty
+
+
+def test_reserved_keys(cuda_lib):
+    import torch
+
+    t = _table(cuda_lib, 1024)
+    keys = np.array([5, 0, (1 << 64) - 1, 9], dtype=np.uint64)
+    codes = codes_buf(4)
+    t.insert(to_dev(keys), to_dev(keys), codes)
+    assert to_np_u8(codes).tolist() == [1, 3, 3, 1]
+    vo, fo = vals_buf(4), codes_buf(4)
+    t.find(to_dev(keys), vo, fo)
+    assert to_np_u8(fo).tolist() == [1, 3, 3, 1]
+    assert to_np_u64(vo).tolist() == [5, 0, 0, 9]
+    with pytest.raises(cuda_lib.ChtError) as e:
+        t.size(check=True)
+    assert e.value.status == cuda_lib.CHT_ERR_RESERVED_KEY
+    assert t.status() & cuda_lib.STATUS_RESERVED
+    assert t.status() == 0  # cleared by the previous read
+    assert t.size()[:2] == (2, 2)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("g", [1, 8, 32])
+def test_full_bounded_table(cuda_lib, g):
+    t = _table(cuda_lib, 64, g)
+    keys = W.uniform_keys(100, seed=55)
+    codes = codes_buf(100)
+    t.insert(to_dev(keys), to_dev(keys), codes)
+    cs = to_np_u8(codes)
+    assert (cs == 1).sum() == 64 and (cs == 2).sum() == 36
+    assert t.status() & cuda_lib.STATUS_FULL
+    vo, fo = vals_buf(100), codes_buf(100)
+    t.find(to_dev(keys), vo, fo)
+    assert np.array_equal(to_np_u8(fo) == 1, cs == 1)
+    miss = W.uniform_keys(10, start=5000, seed=55)
+    vo, fo = vals_buf(10), codes_buf(10)
+    t.find(to_dev(miss), vo, fo)  # terminates after c cells
+    assert (to_np_u8(fo) == 0).all()
+
+
+def test_empty_batches_and_bad_args(cuda_lib):
+    import torch
+
+    t = _table(cuda_lib, 1000)
+    e = torch.empty(0, dtype=torch.int64, device="cuda")
+    t.insert(e, e)
+    t.find(e, e)
+    t.erase(e)
+    t.insert_or_update(e, e)
+    assert t.size() == (0, 0, 1024)
+    with pytest.raises(cuda_lib.ChtError):
+        t.set_config(group_width=3)
+    with pytest.raises(cuda_lib.ChtError):
+        t.insert_or_update(to_dev(np.array([1], np.uint64)), to_dev(np.array([1], np.uint64)), op=7)
+
+
+def test_host_arrays_match_device(cuda_lib, oracle_mod):
+    c = 1 << 14
+    keys = W.uniform_keys(5000, seed=56)
+    vals = W.values_for(keys)
+    t = _table(cuda_lib, c)
+    codes = np.full(keys.size, 255, np.uint8)
+    t.insert(keys, vals, codes)  # numpy in, numpy out: staged by the library
+    import torch
+
+    torch.cuda.synchronize()
+    assert (codes == 1).all()
+    q = np.concatenate([keys[::3], W.uniform_keys(100, start=9000, seed=56)])
+    vo = np.zeros(q.size, np.uint64)
+    fo = np.zeros(q.size, np.uint8)
+    t.find(q, vo, fo)
+    torch.cuda.synchronize()
+    o = oracle_mod.OracleTable(c)
+    o.insert(keys, vals)
+    ev, ef = o.find(q)
+    assert np.array_equal(vo, ev) and np.array_equal(fo, ef)
+    # pinned host memory goes through the same staging
+    pk = torch.from_numpy(q.view(np.int64)).pin_memory()
+    pv = torch.zeros(q.size, dtype=torch.int64).pin_memory()
+    t.find(pk, pv)
+    torch.cuda.synchronize()
+    assert np.array_equal(pv.numpy().view(np.uint64), ev)
