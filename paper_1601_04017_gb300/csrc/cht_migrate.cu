@@ -98,6 +98,23 @@ __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
                 m0 = 0;
             }
             int fail = 0;
+            if (!own) {
+                // The tile lies inside a cluster that starts before it; the
+                // owner of that cluster is an earlier tile, whose forward
+                // border scan fails if the cluster outruns it.  If no empty
+                // cell precedes the tile within the scan bound, no tile may
+                // own the cluster (a full table): report it.
+                bool found = false;
+                for (u32 off = 0; off < kMaxScan && off < c; off += 32) {
+                    const u64 i = d - 1 - off - lane;
+                    const bool e = a.src[i & cmask].key == kEmpty;
+                    if (__ballot_sync(0xffffffffu, e)) {
+                        found = true;
+                        break;
+                    }
+                }
+                if (!found) fail = 1;
+            }
             if (own) {
                 if (s_src[T - 1].key == kEmpty) {
                     m1 = d + T;
