@@ -183,6 +183,27 @@ uint64_t cht_memory_in_use(void);
 /* Number of kernel launches this library has issued (process-wide). */
 uint64_t cht_launch_count(void);
 
+/* find without any device allocation.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc where they look keys up -- a process
+ * whose device memory another allocator already owns (a framework's caching
+ * pool, a serving system's fixed arena), a latency-critical path that must not
+ * block or synchronize on an allocation, or an embedding with a fixed memory
+ * budget.  Same arguments and results as cht_find; keys, vals_out and found
+ * may be host or device arrays.  Keys and results pass through one fixed
+ * scratch array in device memory that the library holds on every GPU that
+ * loads it until the process exits (CHT_NOALLOC_MAX_KEYS * 17 bytes, about
+ * 1.1 MiB); batches larger than CHT_NOALLOC_MAX_KEYS return
+ * CHT_ERR_INVALID_ARG.  The first call on a device looks up the scratch's
+ * device address there; make that first call before any stream capture.
+ * Every call shares the one scratch array: calls whose work overlaps on the
+ * GPU (different streams or threads, not ordered) race and may return each
+ * other's results, so order them.  Results in host arrays are valid once the
+ * stream has been synchronized.  Allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine). */
+#define CHT_NOALLOC_MAX_KEYS 65536u
+cht_status cht_find_noalloc(cht_handle h, const uint64_t *keys, uint64_t n, uint64_t *vals_out,
+                            uint8_t *found, cht_stream_t stream);
+
 /* Static string for a status code. */
 const char *cht_status_string(cht_status s);
 

@@ -1,6 +1,6 @@
 """Build libcht.so in-tree with nvcc for sm_103a (GB300).
 
-The three CUDA translation units compile in parallel; the shared library is
+The CUDA translation units compile in parallel; the shared library is
 linked next to this file.  No PyTorch extension machinery is involved: the
 library has a plain C ABI (include/cht.h) and is loaded with ctypes.
 """
@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libcht.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["cht_ops.cu", "cht_migrate.cu", "cht_runtime.cu"]
+SOURCES = ["cht_ops.cu", "cht_migrate.cu", "cht_runtime.cu", "cht_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -263,3 +263,29 @@ class Table:
         _check(self._lib.cht_copy_cells(self._h, out.data_ptr(), cap, ctypes.byref(n), _stream(stream)),
                "cht_copy_cells")
         return out
+
+
+NOALLOC_MAX_KEYS = 65536
+
+
+def find_noalloc(table: Table, keys, vals_out, found=None, stream=None):
+    """cht_find_noalloc: find that allocates no device memory.
+
+    For callers that cannot allocate device memory where they look keys up
+    (memory owned by another allocator, allocation-free request paths, fixed
+    budgets).  Keys and results pass through the library's fixed scratch
+    array, so at most NOALLOC_MAX_KEYS keys per call; calls that overlap on
+    the GPU share that array and race, so keep them ordered.  Host results are
+    valid after the stream is synchronized.
+    """
+    lib = load_library()
+    f = lib.cht_find_noalloc
+    if f.argtypes is None:
+        p = ctypes.c_void_p
+        f.restype = ctypes.c_int
+        f.argtypes = [p, p, ctypes.c_uint64, p, p, p]
+    kp, n, _ = _ptr(keys, 8, what="keys")
+    vp, _, _ = _ptr(vals_out, 8, n, "vals_out")
+    cp, _, _ = _ptr(found, 1, n, "found")
+    _check(f(table._h, kp, n, vp, cp, _stream(stream)), "cht_find_noalloc")
+    return vals_out, found

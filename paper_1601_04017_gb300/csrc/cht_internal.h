@@ -47,3 +47,14 @@ void count_launch();
 int sm_count();
 
 }  // namespace cht
+
+struct cht_table;
+
+namespace cht {
+
+// Read-only view of a table's device state and tunables (for entry points
+// that live outside the runtime translation unit).
+void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int* device,
+                int* group_width, int* ctas_per_sm);
+
+}  // namespace cht

@@ -347,6 +347,16 @@ int sm_count() {
     return v;
 }
 
+void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int* device, int* group_width,
+                int* ctas_per_sm) {
+    *cells = h->cells;
+    *log2c = h->log2c;
+    *st = h->st;
+    *device = h->device;
+    *group_width = h->cfg.group_width;
+    *ctas_per_sm = h->cfg.ctas_per_sm;
+}
+
 }  // namespace cht
 
 extern "C" {
