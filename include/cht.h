@@ -77,18 +77,27 @@ typedef enum {
 /* Sticky device status bits (cht_get_status). */
 #define CHT_STATUS_FULL 0x1u
 #define CHT_STATUS_RESERVED 0x2u
+#define CHT_STATUS_TIMEOUT 0x4u /* a bounded device wait gave up (the work was redone) */
 
 /* Tunables.  group_width G: lanes that probe one key together, each loading
  * 16 bytes (G in {1,2,4,8,16,32}); G = 1 uses one 32-byte load (two cells,
- * one DRAM sector) per lane and probe step.  ctas_per_sm: resident CTAs per
+ * one DRAM sector) per lane and probe step; 0 (default) picks G per batch
+ * from the table's load: 1 below 0.6, 4 below 0.75, else 8.  ctas_per_sm: resident CTAs per
  * SM for the operation kernels (0 = occupancy maximum).  migrate_tile:
  * source cells per migration CTA (power of two, 256..8192, 0 = default).
- * alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5). */
+ * alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).
+ * wait_limit_us: bound of every device-side wait on an asynchronous copy
+ * (0 = default, about one second); a wait that runs out sets
+ * CHT_STATUS_TIMEOUT and the work is redone by a slower path.
+ * fault_inject: testing only; bit 0 makes each migration CTA first wait on a
+ * barrier that nothing completes, so that wait runs out (0 = off). */
 typedef struct {
     int group_width;
     int ctas_per_sm;
     int migrate_tile;
     double alpha;
+    int wait_limit_us;
+    int fault_inject;
 } cht_config;
 
 /* Create a table of at least `capacity` cells (rounded up to a power of two,
@@ -150,8 +159,8 @@ cht_status cht_migrate(cht_handle h, uint64_t new_capacity, cht_stream_t stream)
 
 /* Synchronize `stream` and report: live elements (I - D), non-empty cells
  * I (tombstones included), capacity c.  Any out-pointer may be NULL.
- * Returns CHT_ERR_TABLE_FULL / CHT_ERR_RESERVED_KEY if the sticky status has
- * the bit set (the status is not cleared), else CHT_OK. */
+ * Returns CHT_ERR_TABLE_FULL / CHT_ERR_RESERVED_KEY / CHT_ERR_TIMEOUT if the
+ * sticky status has that bit set (the status is not cleared), else CHT_OK. */
 cht_status cht_size(cht_handle h, uint64_t *live, uint64_t *nonempty, uint64_t *capacity,
                     cht_stream_t stream);
 

@@ -31,9 +31,12 @@ cudaError_t launch_op(Mode mode, const OpArgs& a, int group_width, int ctas_per_
 // Cluster-wise migration of `src` (2^src_log2 cells) into `dst`
 // (2^dst_log2 cells, dst_log2 >= src_log2).  dst needs no initialisation:
 // every target cell is written.  `st` receives the new I (it must be zero
-// on entry) and mig_fail.  tile: source cells per CTA (power of two).
+// on entry) and mig_fail.  tile: source cells per CTA (power of two);
+// wait_limit: bound of one bulk-copy wait in clock cycles (0 = default);
+// inject_stall != 0 makes each CTA first wait on a barrier nothing arrives
+// on (testing the timeout path).
 cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log2, DevState* st,
-                           int tile, cudaStream_t s);
+                           int tile, long long wait_limit, int inject_stall, cudaStream_t s);
 
 // Compact the live cells into keys_out / vals_out (max_n entries); the count
 // lands in st->export_pos, which must be zero on entry.
@@ -53,7 +56,8 @@ struct cht_table;
 namespace cht {
 
 // Read-only view of a table's device state and tunables (for entry points
-// that live outside the runtime translation unit).
+// that live outside the runtime translation unit); group_width is the
+// effective width a find would use now.
 void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int* device,
                 int* group_width, int* ctas_per_sm);
 

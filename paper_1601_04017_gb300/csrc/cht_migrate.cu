@@ -2,33 +2,41 @@
 // Sec. 4.4) and the forall/export compaction (Sec. 3 "Bulk Operations").
 //
 // Migration into a table gamma = 2^g times larger (g >= 0).  The source is
-// cut into tiles of T cells, one CTA per tile (grid-stride).  Tile [d, d+T)
-// moves its borders to just after the next empty cell: m(d) = d if cell d-1
-// is empty, else (first empty cell >= d) + 1.  The CTA migrates the source
-// range [m(d), m(d+T)), which consists of whole clusters, and owns the target
-// range [gamma*m(d), gamma*m(d+T)).  By Lemma 1 a cluster a..b lands inside
-// gamma*a .. gamma*(b+1)-1 (the integer-gamma form of the lemma's bound), so
-// the owned target ranges of different tiles are disjoint and together cover
-// the target table: no atomics and no separate initialisation are needed --
-// each CTA writes every cell of its range, empties included (the paper's
-// "each thread is responsible for initializing all cells in its region").
-// Inside the CTA each cluster is re-inserted by one thread in source index
-// order, so the layout equals the sequential migration (Lemma 1).
+// cut into tiles of T cells.  Tile [d, d+T) moves its borders to just after
+// the next empty cell: m(d) = d if cell d-1 is empty, else (first empty cell
+// >= d) + 1.  It migrates the source range [m(d), m(d+T)), which consists of
+// whole clusters, and owns the target range [gamma*m(d), gamma*m(d+T)).  By
+// Lemma 1 a cluster a..b lands inside gamma*a .. gamma*(b+1)-1 (the
+// integer-gamma form of the lemma's bound), so the owned target ranges of
+// different tiles are disjoint and together cover the target table: no
+// atomics and no separate initialisation -- each tile writes every cell of
+// its range, empties included (the paper's "each thread is responsible for
+// initializing all cells in its region").  Each cluster is re-inserted by one
+// thread in source index order, so the layout equals the sequential
+// migration (Lemma 1).
 //
-// The target range is staged in shared memory when it fits (the common case:
-// about gamma*T cells) and written out with coalesced stores; otherwise the
-// CTA zero-fills it in global memory and inserts there directly.  A border
-// scan that finds no empty cell within kMaxScan cells sets mig_fail; a
-// single-CTA fallback kernel, always launched after the tile kernel, then
-// redoes the whole migration sequentially (only for pathological tables:
-// full, or with a cluster longer than kMaxScan cells).
+// GB300 mapping.  Persistent CTAs walk the tiles.  The copy engine (TMA,
+// untiled bulk copies) brings the window [d-1, d+T+H) -- the tile, its
+// predecessor cell and a halo of H cells -- into one of two shared buffers
+// while the CTA works on the previous tile (mbarrier completion, bounded
+// waits).  Cluster starts are compacted into a list so every thread inserts.
+// The owned target range is staged in shared memory (the part beyond the
+// staging capacity goes straight to global memory) and written back by a
+// bulk store.  A border scan that finds no empty cell within kMaxScan cells,
+// or a bulk-copy wait that runs out, sets mig_fail; a single-CTA fallback
+// kernel, always launched after the tile kernel, then redoes the whole
+// migration sequentially (only for pathological tables: full, or with a
+// cluster longer than kMaxScan cells).
 #include "cht_internal.h"
+#include "cht_tma.cuh"
 
 namespace cht {
 namespace {
 
 constexpr int kMigBlock = 256;
 constexpr u32 kMaxScan = 1u << 16;  // longest cluster overhang a tile CTA handles
+constexpr u32 kMigTimeoutBit = 16u;
+constexpr long long kDrainLimit = 4000000000ll;  // cycles to wait for copies in flight
 
 struct MigArgs {
     const Cell* src;
@@ -36,9 +44,12 @@ struct MigArgs {
     Cell* dst;
     u32 dlog2;
     DevState* st;
-    u32 tile;       // T, power of two, <= source capacity
-    u32 tgt_cap;    // cells of shared-memory target staging (0 = global only)
-    u32 bm_words;   // 32-bit words of the cluster-start bitmask
+    u32 tile;        // T, power of two, <= c/2
+    u32 halo;        // H cells after the tile brought in with it
+    u32 lw_pad;      // cells per window buffer (T + H + 1 rounded up to 8)
+    u32 tgt_cap;     // cells of shared-memory target staging
+    long long wait_limit;  // bound of one bulk-copy wait, in clock cycles
+    int inject_stall;      // testing: wait once on a barrier nothing arrives on
 };
 
 __device__ __forceinline__ u64 warp_sum(u64 x) {
@@ -47,92 +58,137 @@ __device__ __forceinline__ u64 warp_sum(u64 x) {
 }
 
 __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
-    extern __shared__ uint4 smem[];
-    Cell* s_src = reinterpret_cast<Cell*>(smem);
-    Cell* s_tgt = s_src + a.tile;
-    u32* s_bm = reinterpret_cast<u32*>(s_tgt + a.tgt_cap);
+    extern __shared__ __align__(128) unsigned char smem[];
+    Cell* const buf0 = reinterpret_cast<Cell*>(smem);
+    Cell* const buf1 = buf0 + a.lw_pad;
+    Cell* const tgt = buf1 + a.lw_pad;
+    u32* const starts = reinterpret_cast<u32*>(tgt + a.tgt_cap);
+    __shared__ unsigned long long bars[3];
     __shared__ u64 s_m0, s_m1;
-    __shared__ u32 s_first_empty;
-    __shared__ int s_fail;
-    __shared__ u64 s_part[kMigBlock / 32];
+    __shared__ u32 s_first_tile, s_first_halo, s_nstarts;
+    __shared__ int s_fail, s_timeout;
 
     const u64 c = 1ull << a.slog2, cmask = c - 1;
     const u64 nc = 1ull << a.dlog2, nmask = nc - 1;
     const u32 g = a.dlog2 - a.slog2;
     const u32 dshift = 64u - a.dlog2;
-    const u32 T = a.tile;
+    const u32 T = a.tile, H = a.halo, Lw = T + H + 1;
     const u64 ntiles = c / T;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    u64 moved = 0;
+    int bad = 0;
 
-    for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // thread 0: bring the window [d-1, d+T+H) of tile `t` into buffer `b`
+    auto issue = [&](u64 t, int b) {
+        Cell* dstb = b ? buf1 : buf0;
+        const u64 s0 = (t * T - 1) & cmask;
+        u64 first = c - s0;
+        if (first > Lw) first = Lw;
+        mbar_arrive_expect_tx(&bars[b], Lw * 16u);
+        bulk_g2s(dstb, a.src + s0, u32(first * 16), &bars[b]);
+        if (first < Lw) bulk_g2s(dstb + first, a.src, u32((Lw - first) * 16), &bars[b]);
+    };
+
+    u32 parity = 0;  // bit b: parity of the next completion of bars[b]
+    u64 tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) issue(tile, 0);
+    int b = 0;
+    for (; tile < ntiles; tile += gridDim.x, b ^= 1) {
         const u64 d = tile * T;
+        const u64 nt = tile + gridDim.x;
         if (tid == 0) {
-            s_first_empty = 0xffffffffu;
+            s_first_tile = 0xffffffffu;
+            s_first_halo = 0xffffffffu;
+            s_nstarts = 0;
             s_fail = 0;
-        }
-        // ---- stage the source tile (two cells per 256-bit load)
-        for (u32 i = tid; i < T / 2; i += kMigBlock) {
-            u64 k0, v0, k1, v1;
-            ld_pair_nc(a.src + d + 2 * i, k0, v0, k1, v1);
-            s_src[2 * i].key = k0;
-            s_src[2 * i].val = v0;
-            s_src[2 * i + 1].key = k1;
-            s_src[2 * i + 1].val = v1;
+            s_timeout = 0;
+            if (nt < ntiles) {
+                fence_proxy_async_smem();
+                issue(nt, b ^ 1);
+            }
         }
         __syncthreads();
-        for (u32 i = tid; i < T; i += kMigBlock)
-            if (s_src[i].key == kEmpty) atomicMin(&s_first_empty, i);
+        bool ok = true;
+        if (a.inject_stall && tile == blockIdx.x) ok = mbar_wait_bounded(&bars[2], 0, a.wait_limit);
+        if (ok) ok = mbar_wait_bounded(&bars[b], (parity >> b) & 1u, a.wait_limit);
+        parity ^= 1u << b;
+        if (!ok) s_timeout = 1;
+        __syncthreads();
+        if (s_timeout) {
+            // give up: let the copies in flight land, then leave it to the fallback
+            if (tid == 0) {
+                atomicOr(&a.st->mig_fail, kMigTimeoutBit);
+                atomicOr(&a.st->status, 4u);
+                mbar_wait_bounded(&bars[b], ((parity >> b) & 1u) ^ 1u, kDrainLimit);
+                if (nt < ntiles) mbar_wait_bounded(&bars[b ^ 1], (parity >> (b ^ 1)) & 1u, kDrainLimit);
+                bulk_wait_all();
+            }
+            __syncthreads();
+            return;
+        }
+        const Cell* w = b ? buf1 : buf0;  // w[k] = cell d - 1 + k
+        auto key_at = [&](u64 i) -> u64 {  // unwrapped index i >= d - 1
+            const u64 k = i - (d - 1);
+            return k < Lw ? w[k].key : a.src[i & cmask].key;
+        };
+        auto cell_at = [&](u64 i) -> Cell {
+            const u64 k = i - (d - 1);
+            return k < Lw ? w[k] : a.src[i & cmask];
+        };
+        for (u32 k = 1 + tid; k < Lw; k += kMigBlock) {
+            if (w[k].key == kEmpty) {
+                if (k <= T) atomicMin(&s_first_tile, k - 1);
+                else atomicMin(&s_first_halo, k - 1 - T);
+            }
+        }
         __syncthreads();
 
-        // ---- moved borders m(d) and m(d+T)
+        // ---- moved borders m(d) and m(d+T) (warp 0)
         if (wid == 0) {
-            const bool prev_empty = a.src[(d - 1) & cmask].key == kEmpty;
-            u64 m0, m1 = 0;
+            u64 m0 = 0, m1 = 0;
             bool own = true;
-            if (prev_empty) {
-                m0 = d;
-            } else if (s_first_empty != 0xffffffffu) {
-                m0 = d + s_first_empty + 1;
-            } else {
-                own = false;  // the whole tile lies inside a cluster begun earlier
-                m0 = 0;
-            }
             int fail = 0;
+            if (w[0].key == kEmpty) m0 = d;
+            else if (s_first_tile != 0xffffffffu) m0 = d + s_first_tile + 1;
+            else own = false;  // the whole tile lies inside a cluster begun earlier
             if (!own) {
-                // The tile lies inside a cluster that starts before it; the
-                // owner of that cluster is an earlier tile, whose forward
+                // The owner of that cluster is an earlier tile, whose forward
                 // border scan fails if the cluster outruns it.  If no empty
-                // cell precedes the tile within the scan bound, no tile may
-                // own the cluster (a full table): report it.
+                // cell precedes the tile within the bound, no tile owns the
+                // cluster (a full table): report it.
                 bool found = false;
                 for (u32 off = 0; off < kMaxScan && off < c; off += 32) {
-                    const u64 i = d - 1 - off - lane;
-                    const bool e = a.src[i & cmask].key == kEmpty;
+                    const bool e = a.src[(d - 1 - off - lane) & cmask].key == kEmpty;
                     if (__ballot_sync(0xffffffffu, e)) {
                         found = true;
                         break;
                     }
                 }
                 if (!found) fail = 1;
-            }
-            if (own) {
-                if (s_src[T - 1].key == kEmpty) {
-                    m1 = d + T;
-                } else {
-                    bool found = false;
-                    for (u32 off = 0; off < kMaxScan && off < c; off += 32) {
-                        const u64 i = d + T + off + lane;
-                        const bool e = a.src[i & cmask].key == kEmpty;
-                        const u32 b = __ballot_sync(0xffffffffu, e);
-                        if (b) {
-                            m1 = d + T + off + (__ffs(b) - 1) + 1;
-                            found = true;
-                            break;
-                        }
+            } else if (w[T].key == kEmpty) {
+                m1 = d + T;
+            } else if (s_first_halo != 0xffffffffu) {
+                m1 = d + T + s_first_halo + 1;
+            } else {
+                bool found = false;
+                for (u32 off = 0; off < kMaxScan && off < c; off += 32) {
+                    const u64 i = d + T + H + off + lane;
+                    const u32 bb = __ballot_sync(0xffffffffu, a.src[i & cmask].key == kEmpty);
+                    if (bb) {
+                        m1 = d + T + H + off + (__ffs(bb) - 1) + 1;
+                        found = true;
+                        break;
                     }
-                    if (!found) fail = 1;
                 }
-                if (!fail && m1 < m0) m1 = m0;
+                if (!found) fail = 1;
             }
             if (lane == 0) {
                 s_m0 = own ? m0 : 0;
@@ -140,111 +196,89 @@ __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
                 s_fail = fail;
             }
         }
+        // the previous tile's bulk store must have read the staging area
+        if (tid == 0) bulk_wait_read_all();
         __syncthreads();
         if (s_fail) {
             if (tid == 0) atomicOr(&a.st->mig_fail, 1u);
-            __syncthreads();
+            __syncthreads();  // everyone has read s_fail before thread 0 resets it
             continue;
         }
         const u64 m0 = s_m0, m1 = s_m1;
-        const u64 L = m1 - m0;          // source cells of this CTA's clusters
-        const u64 tl = L << g;          // owned target cells
-        const u64 tbase = m0 << g;      // first owned target cell (unwrapped)
-        u64 moved = 0;
+        const u64 L = m1 - m0;      // source cells of this tile's clusters
+        const u64 tl = L << g;      // owned target cells
+        const u64 tbase = m0 << g;  // first owned target cell (unwrapped)
+        const u64 staged = tl < a.tgt_cap ? tl : a.tgt_cap;
         if (L > 0) {
-            const bool staged = tl <= a.tgt_cap;
-            // source cell i (unwrapped index >= d - 1)
-            auto src_key = [&](u64 i) -> u64 {
-                return (i >= d && i < d + T) ? s_src[i - d].key : a.src[i & cmask].key;
-            };
-            auto src_cell = [&](u64 i) -> Cell {
-                return (i >= d && i < d + T) ? s_src[i - d] : a.src[i & cmask];
-            };
-            int bad = 0;
-            if (staged) {
-                // zero the staged target range and the cluster-start bitmask
-                const u32 words = u32((L + 31) / 32);
-                for (u32 w = tid; w < words; w += kMigBlock) s_bm[w] = 0;
-                for (u64 i = tid; i < tl; i += kMigBlock) {
-                    s_tgt[i].key = 0;
-                    s_tgt[i].val = 0;
-                }
-                __syncthreads();
-                // cluster starts: a non-empty cell whose predecessor is empty
-                for (u64 j = tid; j < L; j += kMigBlock) {
-                    const u64 i = m0 + j;
-                    if (src_key(i) != kEmpty && src_key(i - 1) == kEmpty)
-                        atomicOr(&s_bm[j >> 5], 1u << (j & 31));
-                }
-                __syncthreads();
-                // each thread takes 32-cell words of the bitmask and re-inserts
-                // the clusters that start there, in source index order
-                for (u32 w = tid; w < words; w += kMigBlock) {
-                    u32 bits = s_bm[w];
-                    while (bits) {
-                        const u32 b = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        for (u64 j = u64(w) * 32 + b; j < L; ++j) {
-                            const Cell cl = src_cell(m0 + j);
-                            if (cl.key == kEmpty) break;
-                            if (cl.key == kTomb) continue;
-                            u64 loc = (home_of(cl.key, dshift) - tbase) & nmask;
-                            while (loc < tl && s_tgt[loc].key != kEmpty) ++loc;
-                            if (loc >= tl) {
-                                bad = 1;
-                                break;
-                            }
-                            s_tgt[loc] = cl;
-                            ++moved;
-                        }
-                    }
-                }
-                __syncthreads();
-                for (u64 i = tid; i < tl; i += kMigBlock) a.dst[(tbase + i) & nmask] = s_tgt[i];
-            } else {
-                // long range or large gamma: zero-fill the owned target range
-                // in global memory, then each thread re-inserts the clusters
-                // that start in its own contiguous chunk of the source range
-                for (u64 i = tid; i < tl; i += kMigBlock) {
-                    Cell z;
-                    z.key = 0;
-                    z.val = 0;
-                    a.dst[(tbase + i) & nmask] = z;
-                }
-                __syncthreads();
-                const u64 ch = (L + kMigBlock - 1) / kMigBlock;
-                const u64 lo = u64(tid) * ch;
-                const u64 hi = lo + ch < L ? lo + ch : L;
-                for (u64 s0 = lo; s0 < hi; ++s0) {
-                    if (!(src_key(m0 + s0) != kEmpty && src_key(m0 + s0 - 1) == kEmpty)) continue;
-                    for (u64 j = s0; j < L; ++j) {
-                        const Cell cl = src_cell(m0 + j);
-                        if (cl.key == kEmpty) break;
-                        if (cl.key == kTomb) continue;
-                        u64 loc = (home_of(cl.key, dshift) - tbase) & nmask;
-                        while (loc < tl && a.dst[(tbase + loc) & nmask].key != kEmpty) ++loc;
+            for (u64 k = tid; k < staged; k += kMigBlock) {
+                tgt[k].key = 0;
+                tgt[k].val = 0;
+            }
+            for (u64 k = staged + tid; k < tl; k += kMigBlock) {
+                Cell z;
+                z.key = 0;
+                z.val = 0;
+                a.dst[(tbase + k) & nmask] = z;
+            }
+            // cluster starts in [m0, min(m1, d+T)): non-empty after an empty
+            const u64 sl = (m1 < d + T ? m1 : d + T) - m0;
+            for (u64 j0 = u64(wid) * 32; j0 < sl; j0 += kMigBlock) {
+                const u64 j = j0 + lane;
+                const bool is_start = j < sl && key_at(m0 + j) != kEmpty && key_at(m0 + j - 1) == kEmpty;
+                const u32 bb = __ballot_sync(0xffffffffu, is_start);
+                u32 base = 0;
+                if (lane == 0 && bb) base = atomicAdd(&s_nstarts, u32(__popc(bb)));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (is_start) starts[base + __popc(bb & ((1u << lane) - 1u))] = u32(j);
+            }
+            __syncthreads();
+            // one thread per cluster: re-insert its live cells in index order
+            const u32 ns = s_nstarts;
+            for (u32 q = tid; q < ns && !bad; q += kMigBlock) {
+                for (u64 i = m0 + starts[q];; ++i) {
+                    const Cell cl = cell_at(i);
+                    if (cl.key == kEmpty) break;
+                    if (cl.key == kTomb) continue;
+                    u64 loc = (home_of(cl.key, dshift) - tbase) & nmask;
+                    for (;; ++loc) {
                         if (loc >= tl) {
                             bad = 1;
                             break;
                         }
-                        a.dst[(tbase + loc) & nmask] = cl;
-                        ++moved;
+                        if (loc < staged) {
+                            if (tgt[loc].key == kEmpty) {
+                                tgt[loc] = cl;
+                                break;
+                            }
+                        } else {
+                            Cell* gp = a.dst + ((tbase + loc) & nmask);
+                            if (gp->key == kEmpty) {
+                                *gp = cl;
+                                break;
+                            }
+                        }
                     }
+                    if (bad) break;
+                    ++moved;
                 }
             }
-            if (bad) atomicOr(&a.st->mig_fail, 2u);
         }
-        // ---- moved-element count -> new I
-        moved = warp_sum(moved);
-        if (lane == 0) s_part[wid] = moved;
+        // write the staged target range back with a bulk store
+        fence_proxy_async_smem();
         __syncthreads();
-        if (tid == 0) {
-            u64 tot = 0;
-            for (int w = 0; w < kMigBlock / 32; ++w) tot += s_part[w];
-            if (tot) atomicAdd(&a.st->I, tot);
+        if (tid == 0 && staged > 0) {
+            const u64 s0 = tbase & nmask;
+            u64 first = nc - s0;
+            if (first > staged) first = staged;
+            bulk_s2g(a.dst + s0, tgt, u32(first * 16));
+            if (first < staged) bulk_s2g(a.dst, tgt + first, u32((staged - first) * 16));
+            bulk_commit();
         }
-        __syncthreads();
     }
+    if (tid == 0) bulk_wait_all();
+    if (bad) atomicOr(&a.st->mig_fail, 2u);
+    moved = warp_sum(moved);
+    if (lane == 0 && moved) atomicAdd(&a.st->I, moved);
 }
 
 // Sequential migration of the whole table by one thread (after a block-wide
@@ -321,21 +355,23 @@ __global__ void __launch_bounds__(256) export_kernel(const Cell* __restrict__ ce
 }  // namespace
 
 cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log2, DevState* st,
-                           int tile, cudaStream_t s) {
+                           int tile, long long wait_limit, int inject_stall, cudaStream_t s) {
     const u64 c = 1ull << src_log2;
-    u32 T = tile > 0 ? u32(tile) : 2048u;
-    if (T > c) T = u32(c);
-    if (T < 64) T = 64;
+    u32 T = tile > 0 ? u32(tile) : 1024u;
+    if (T > 4096) T = 4096;  // two window buffers must fit in shared memory
+    if (T > c / 2) T = u32(c / 2);
+    u32 H = T / 4 < 64 ? 64 : T / 4;
+    if (H > 256) H = 256;
+    if (H > c / 4) H = u32(c / 4);
     const u32 g = dst_log2 - src_log2;
-    // shared memory: source tile + target staging + start bitmask
-    // staged target: the tile plus a margin for clusters running past its
-    // end, times gamma; the bitmask covers the staged source range
-    const u32 span = T + T / 8 + 64;
-    const u32 bm_words = span / 32 + 1;
-    const size_t fixed = size_t(T) * sizeof(Cell) + size_t(bm_words) * 4;
-    const size_t budget = 200 * 1024;
-    u64 want = (g <= 3) ? (u64(span) << g) : 0;
-    if (fixed + want * sizeof(Cell) > budget) want = 0;
+    const u32 lw_pad = (T + H + 1 + 7) & ~7u;
+    const u32 start_cap = T / 2 + 32;
+    // shared memory: two window buffers, the start list, the target staging
+    const size_t fixed = 2 * size_t(lw_pad) * sizeof(Cell) + size_t(start_cap) * 4;
+    const size_t budget = 100 * 1024;
+    u64 want = g <= 4 ? (u64(T + H) << g) : 0;
+    const u64 room = fixed < budget ? (budget - fixed) / sizeof(Cell) : 0;
+    if (want > room) want = room;
     MigArgs a;
     a.src = src;
     a.slog2 = src_log2;
@@ -343,8 +379,11 @@ cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log
     a.dlog2 = dst_log2;
     a.st = st;
     a.tile = T;
+    a.halo = H;
+    a.lw_pad = lw_pad;
     a.tgt_cap = u32(want);
-    a.bm_words = bm_words;
+    a.wait_limit = wait_limit > 0 ? wait_limit : 2000000000ll;
+    a.inject_stall = inject_stall;
     const size_t smem = fixed + size_t(a.tgt_cap) * sizeof(Cell);
     cudaError_t e = cudaFuncSetAttribute(migrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));

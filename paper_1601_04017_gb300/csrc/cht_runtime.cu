@@ -160,20 +160,24 @@ class Staging {
 
 cht_config default_config() {
     cht_config c;
-    c.group_width = 1;
+    c.group_width = 0;
     c.ctas_per_sm = 0;
-    c.migrate_tile = 2048;
+    c.migrate_tile = 1024;
     c.alpha = 0.5;
+    c.wait_limit_us = 0;
+    c.fault_inject = 0;
     return c;
 }
 
 bool valid_config(const cht_config& c) {
     const int g = c.group_width;
-    if (!(g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32)) return false;
+    if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32)) return false;
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64) return false;
     const int t = c.migrate_tile;
     if (t != 0 && (t < 256 || t > 8192 || (t & (t - 1)) != 0)) return false;
     if (!(c.alpha > 0.0 && c.alpha < 1.0)) return false;
+    if (c.wait_limit_us < 0 || c.wait_limit_us > 60000000) return false;
+    if (c.fault_inject < 0 || c.fault_inject > 1) return false;
     return true;
 }
 
@@ -239,7 +243,9 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
         lib_free(dst, bytes, s);
         return CHT_ERR_CUDA;
     }
-    cudaError_t e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, h->cfg.migrate_tile, s);
+    const long long wait_cycles = (long long)h->cfg.wait_limit_us * 2000;  // ~2 GHz SM clock
+    cudaError_t e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, h->cfg.migrate_tile,
+                                        wait_cycles, h->cfg.fault_inject & 1, s);
     if (e != cudaSuccess) {
         lib_free(dst, bytes, s);
         return cuda_status(e);
@@ -256,6 +262,19 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
     return CHT_OK;
 }
 
+// Group width for a batch: the configured one, or (auto) by the load the
+// probes will see -- short probes want one sector per lane (G = 1), long
+// probes at high load want wider windows so fewer dependent steps are needed.
+int pick_group_width(const cht_table* h, cht::Mode mode, u64 n) {
+    if (h->cfg.group_width > 0) return h->cfg.group_width;
+    u64 filled = h->i_bound;
+    if (mode == cht::kInsert || mode == cht::kIouAdd || mode == cht::kIouOverwrite) filled += n;
+    const double load = double(filled) / double(h->cap());
+    if (load < 0.6) return 1;
+    if (load < 0.75) return 4;
+    return 8;
+}
+
 cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals, u64* vals_out,
                   unsigned char* codes, u64 n, cudaStream_t s) {
     cht::OpArgs a;
@@ -267,7 +286,7 @@ cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals
     a.codes = codes;
     a.n = n;
     a.st = h->st;
-    return cuda_status(cht::launch_op(mode, a, h->cfg.group_width, h->cfg.ctas_per_sm, s));
+    return cuda_status(cht::launch_op(mode, a, pick_group_width(h, mode, n), h->cfg.ctas_per_sm, s));
 }
 
 // insert / insert_or_update with the growth policy of growable tables.
@@ -353,7 +372,7 @@ void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int
     *log2c = h->log2c;
     *st = h->st;
     *device = h->device;
-    *group_width = h->cfg.group_width;
+    *group_width = pick_group_width(h, kFind, 0);  // the width a find would use now
     *ctas_per_sm = h->cfg.ctas_per_sm;
 }
 
@@ -408,7 +427,7 @@ cht_status cht_destroy(cht_handle h) {
 cht_status cht_set_config(cht_handle h, const cht_config* cfg) {
     if (!h) return CHT_ERR_INVALID_ARG;
     cht_config c = cfg ? *cfg : default_config();
-    if (c.migrate_tile == 0) c.migrate_tile = 2048;
+    if (c.migrate_tile == 0) c.migrate_tile = 1024;
     if (!valid_config(c)) return CHT_ERR_INVALID_ARG;
     h->cfg = c;
     return CHT_OK;
@@ -527,6 +546,7 @@ cht_status cht_size(cht_handle h, uint64_t* live, uint64_t* nonempty, uint64_t* 
     if (capacity) *capacity = h->cap();
     if (ds.status & CHT_STATUS_FULL) return CHT_ERR_TABLE_FULL;
     if (ds.status & CHT_STATUS_RESERVED) return CHT_ERR_RESERVED_KEY;
+    if (ds.status & CHT_STATUS_TIMEOUT) return CHT_ERR_TIMEOUT;
     return CHT_OK;
 }
 

@@ -183,3 +183,25 @@ def test_sliding_window_purges_tombstones(cuda_lib, oracle_mod):
     assert live == window == o.live
     assert cap <= 1 << 16  # the table does not keep doubling: tombstones are purged
     assert_same_live_set(t, o)
+
+
+def test_migration_wait_timeout_is_reported_and_recovered(cuda_lib, oracle_mod):
+    """A bulk-copy wait that runs out (here: a barrier nothing arrives on, via
+    fault_inject) ends the tile kernel with a status bit instead of a hang; the
+    fallback redoes the migration, so the result is still exact."""
+    log2c = 12
+    t, _ = _fill(cuda_lib, oracle_mod, log2c, 0.5, 0.1, seed=9)
+    t.set_config(fault_inject=1, wait_limit_us=20)
+    snap = to_np_u64(t.cells())
+    o = oracle_mod.OracleTable(64)
+    o.load_cells(snap)
+    o.migrate(2 << log2c)
+    t.migrate(2 << log2c)
+    assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), o.cells())
+    with pytest.raises(cuda_lib.ChtError) as e:
+        t.size(check=True)
+    assert e.value.status == cuda_lib.CHT_ERR_TIMEOUT
+    assert t.status() & cuda_lib.STATUS_TIMEOUT
+    t.set_config(fault_inject=0, wait_limit_us=0)
+    t.migrate(4 << log2c)
+    assert t.size(check=True)[0] == o.live
