@@ -82,7 +82,8 @@ typedef enum {
 /* Tunables.  group_width G: lanes that probe one key together, each loading
  * 16 bytes (G in {1,2,4,8,16,32}); G = 1 uses one 32-byte load (two cells,
  * one DRAM sector) per lane and probe step; 0 (default) picks G per batch
- * from the table's load: 1 below 0.6, 4 below 0.75, else 8.  ctas_per_sm: resident CTAs per
+ * from the table's load (for insert: the load after the batch): 1 below 0.6,
+ * 4 below 0.75 (and for erase above it), else 8.  ctas_per_sm: resident CTAs per
  * SM for the operation kernels (0 = occupancy maximum).  migrate_tile:
  * source cells per migration CTA (power of two, 256..8192, 0 = default).
  * alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).

@@ -267,11 +267,14 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
 // probes at high load want wider windows so fewer dependent steps are needed.
 int pick_group_width(const cht_table* h, cht::Mode mode, u64 n) {
     if (h->cfg.group_width > 0) return h->cfg.group_width;
+    // Only a plain insert batch is assumed to add n new cells; insertOrUpdate
+    // batches are mostly updates of few hot keys, which want G = 1.
     u64 filled = h->i_bound;
-    if (mode == cht::kInsert || mode == cht::kIouAdd || mode == cht::kIouOverwrite) filled += n;
+    if (mode == cht::kInsert) filled += n;
+    if (filled > h->cap()) filled = h->cap();
     const double load = double(filled) / double(h->cap());
     if (load < 0.6) return 1;
-    if (load < 0.75) return 4;
+    if (load < 0.75 || mode == cht::kErase) return 4;  // erase ends in an atomic: narrower groups
     return 8;
 }
 
