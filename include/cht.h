@@ -91,7 +91,10 @@ typedef enum {
  * (0 = default, about one second); a wait that runs out sets
  * CHT_STATUS_TIMEOUT and the work is redone by a slower path.
  * fault_inject: testing only; bit 0 makes each migration CTA first wait on a
- * barrier that nothing completes, so that wait runs out (0 = off). */
+ * barrier that nothing completes, so that wait runs out (0 = off).
+ * iou_aggregate: 1 (default) folds equal keys of each window of 1024
+ * insertOrUpdate operations in shared memory first (one table operation per
+ * distinct key and window); 0 probes every operation with the group kernel. */
 typedef struct {
     int group_width;
     int ctas_per_sm;
@@ -99,6 +102,7 @@ typedef struct {
     double alpha;
     int wait_limit_us;
     int fault_inject;
+    int iou_aggregate;
 } cht_config;
 
 /* Create a table of at least `capacity` cells (rounded up to a power of two,

@@ -46,7 +46,8 @@ class ChtError(RuntimeError):
 class ChtConfig(ctypes.Structure):
     _fields_ = [("group_width", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("migrate_tile", ctypes.c_int), ("alpha", ctypes.c_double),
-                ("wait_limit_us", ctypes.c_int), ("fault_inject", ctypes.c_int)]
+                ("wait_limit_us", ctypes.c_int), ("fault_inject", ctypes.c_int),
+                ("iou_aggregate", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -186,7 +187,8 @@ class Table:
         cur = self.config()
         cur.update(kw)
         c = ChtConfig(int(cur["group_width"]), int(cur["ctas_per_sm"]), int(cur["migrate_tile"]),
-                      float(cur["alpha"]), int(cur["wait_limit_us"]), int(cur["fault_inject"]))
+                      float(cur["alpha"]), int(cur["wait_limit_us"]), int(cur["fault_inject"]),
+                      int(cur["iou_aggregate"]))
         _check(self._lib.cht_set_config(self._h, ctypes.byref(c)), "cht_set_config")
 
     # -- operations ----------------------------------------------------------

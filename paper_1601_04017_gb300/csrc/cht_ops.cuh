@@ -274,3 +274,139 @@ __global__ void __launch_bounds__(kOpBlock) op_kernel(OpArgs a) {
 }
 
 }  // namespace cht
+
+namespace cht {
+
+// ---------------------------------------------------------------------------
+// insertOrUpdate with CTA-level aggregation in shared memory.
+//
+// A CTA takes windows of kAggWindow consecutive operations.  Equal keys of a
+// window are folded into one slot of a shared-memory table (open addressing,
+// kAggSlots >= 2 * kAggWindow slots, so every key finds a slot): the add
+// operator sums the values (fetch-and-add on the slot), overwrite keeps the
+// value of the slot's first operation.  The window is then flushed: one
+// global insertOrUpdate per distinct key (Algorithm 1 with the specialised
+// atomicUpdate), whose result -- inserted or updated -- goes to the slot's
+// first operation; every other operation of the key reports "updated"
+// (linearized right after it).  Under skewed keys this turns millions of
+// atomics on one hot cell into one per window.
+// ---------------------------------------------------------------------------
+constexpr int kAggBlock = 256;
+constexpr int kAggWindow = 1024;
+constexpr int kAggSlots = 2048;
+
+// One operation on the global table by one thread (sector-wise probe).
+template <int MODE>
+__device__ __forceinline__ unsigned char global_modify(const OpArgs& a, u64 key, u64 d, u64 cap, u32 shift,
+                                                       u64& n_ins, u32& sbits) {
+    const u64 cmask = cap - 1;
+    u64 pos = home_of(key, shift), probed = 0;
+    while (probed < cap) {
+        const u64 base = pos & ~1ull;
+        const u32 first = u32(pos - base);
+        u64 k0, v0, k1, v1;
+        ld_pair_cg(a.cells + base, k0, v0, k1, v1);
+        int hit = -1;
+        bool match = false;
+        if (first == 0 && (k0 == key || k0 == kEmpty)) {
+            hit = 0;
+            match = k0 == key;
+        } else if (k1 == key || k1 == kEmpty) {
+            hit = 1;
+            match = k1 == key;
+        }
+        if (hit < 0) {
+            probed += 2 - first;
+            pos = (base + 2) & cmask;
+            continue;
+        }
+        const int out = modify_at<MODE>(a.cells + base + hit, match, key, d);
+        if (out == kStepContinue) {
+            probed += u32(hit) - first + 1;
+            pos = (base + u32(hit) + 1) & cmask;
+            continue;
+        }
+        if (out == kStepDoneYes) ++n_ins;
+        return (unsigned char)out;
+    }
+    sbits |= kFull;
+    return kCodeFull;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
+    extern __shared__ __align__(16) unsigned char agg_smem[];
+    u64* const skey = reinterpret_cast<u64*>(agg_smem);
+    u64* const sval = skey + kAggSlots;
+    u32* const slead = reinterpret_cast<u32*>(sval + kAggSlots);  // window offset of the slot's first op
+    const u64 cap = 1ull << a.log2c;
+    const u32 shift = 64u - a.log2c;
+    const int tid = threadIdx.x;
+    u64 n_ins = 0;
+    u32 sbits = 0;
+    for (int s = tid; s < kAggSlots; s += kAggBlock) {
+        skey[s] = kEmpty;
+        sval[s] = 0;
+    }
+    __syncthreads();
+    const u64 nwin = (a.n + kAggWindow - 1) / kAggWindow;
+    for (u64 w = blockIdx.x; w < nwin; w += gridDim.x) {
+        const u64 w0 = w * kAggWindow;
+        // fold the window's operations into the slots
+#pragma unroll
+        for (int j = 0; j < kAggWindow / kAggBlock; ++j) {
+            const u32 off = u32(j * kAggBlock + tid);
+            const u64 idx = w0 + off;
+            if (idx >= a.n) continue;
+            const u64 key = ld_stream(a.keys + idx);
+            const u64 d = ld_stream(a.vals + idx);
+            if (is_reserved(key)) {
+                if (a.codes) a.codes[idx] = kCodeReserved;
+                sbits |= kReserved;
+                continue;
+            }
+            u32 s = u32(fmix64(key)) & (kAggSlots - 1);
+            for (;;) {
+                const u64 k0 = *reinterpret_cast<volatile u64*>(skey + s);
+                bool mine = false, same = k0 == key;
+                if (k0 == kEmpty) {
+                    const u64 old = atomicCAS(reinterpret_cast<unsigned long long*>(skey + s), kEmpty, key);
+                    mine = old == kEmpty;
+                    same = old == key;
+                }
+                if (mine) {
+                    if (MODE == kIouAdd) atomicAdd(reinterpret_cast<unsigned long long*>(sval + s), d);
+                    else sval[s] = d;
+                    slead[s] = off;
+                    break;
+                }
+                if (same) {
+                    if (MODE == kIouAdd) atomicAdd(reinterpret_cast<unsigned long long*>(sval + s), d);
+                    if (a.codes) a.codes[idx] = kNo;
+                    break;
+                }
+                s = (s + 1) & (kAggSlots - 1);
+            }
+        }
+        __syncthreads();
+        // flush: one global operation per distinct key of the window
+        for (int s = tid; s < kAggSlots; s += kAggBlock) {
+            const u64 k = skey[s];
+            if (k == kEmpty) continue;
+            const unsigned char r = global_modify<MODE>(a, k, sval[s], cap, shift, n_ins, sbits);
+            if (a.codes) a.codes[w0 + slead[s]] = r;
+            skey[s] = kEmpty;
+            sval[s] = 0;
+        }
+        __syncthreads();
+    }
+    constexpr u32 FULL = 0xffffffffu;
+    for (int o = 16; o > 0; o >>= 1) n_ins += __shfl_xor_sync(FULL, n_ins, o);
+    const u32 any_status = __reduce_or_sync(FULL, sbits);
+    if ((tid & 31) == 0) {
+        if (n_ins) atomicAdd(&a.st->I, n_ins);
+        if (any_status) atomicOr(&a.st->status, any_status);
+    }
+}
+
+}  // namespace cht

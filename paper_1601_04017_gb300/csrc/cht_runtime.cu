@@ -166,6 +166,7 @@ cht_config default_config() {
     c.alpha = 0.5;
     c.wait_limit_us = 0;
     c.fault_inject = 0;
+    c.iou_aggregate = 1;
     return c;
 }
 
@@ -178,6 +179,7 @@ bool valid_config(const cht_config& c) {
     if (!(c.alpha > 0.0 && c.alpha < 1.0)) return false;
     if (c.wait_limit_us < 0 || c.wait_limit_us > 60000000) return false;
     if (c.fault_inject < 0 || c.fault_inject > 1) return false;
+    if (c.iou_aggregate < 0 || c.iou_aggregate > 1) return false;
     return true;
 }
 
@@ -289,6 +291,8 @@ cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals
     a.codes = codes;
     a.n = n;
     a.st = h->st;
+    if ((mode == cht::kIouAdd || mode == cht::kIouOverwrite) && h->cfg.iou_aggregate)
+        return cuda_status(cht::launch_iou_aggregated(mode, a, h->cfg.ctas_per_sm, s));
     return cuda_status(cht::launch_op(mode, a, pick_group_width(h, mode, n), h->cfg.ctas_per_sm, s));
 }
 

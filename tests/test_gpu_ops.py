@@ -82,14 +82,18 @@ def test_insert_duplicates_one_winner(cuda_lib, oracle_mod, g):
     assert live == len(pre_set | set(keys.tolist()))
 
 
-@pytest.mark.parametrize("g", GROUPS)
+IOU_PATHS = [(0, 1)] + [(g, 0) for g in GROUPS]  # (group width, shared-memory aggregation)
+
+
+@pytest.mark.parametrize("g,agg", IOU_PATHS)
 @pytest.mark.parametrize("s", [0.5, 1.25, 1.5])
-def test_insert_or_update_add_exact(cuda_lib, oracle_mod, g, s):
+def test_insert_or_update_add_exact(cuda_lib, oracle_mod, g, agg, s):
     c = 1 << 17
     keys = W.zipf_keys(150_001, s, n_ranks=1 << 15, seed=52)
     vals = (np.arange(keys.size, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)) | np.uint64(1)
-    pre = np.unique(keys)[::5]
-    t = _table(cuda_lib, c, g)
+    keys[::997] = 0  # reserved keys inside the batch
+    pre = np.unique(keys[keys != 0])[::5]
+    t = _table(cuda_lib, c, g, iou_aggregate=agg)
     o = oracle_mod.OracleTable(c)
     t.insert(to_dev(pre), to_dev(pre))
     o.insert(pre, pre)
@@ -97,19 +101,22 @@ def test_insert_or_update_add_exact(cuda_lib, oracle_mod, g, s):
     t.insert_or_update(to_dev(keys), to_dev(vals), cuda_lib.ADD, codes)
     o.insert_or_update(keys, vals, oracle_mod.ADD)
     pre_set = set(pre.tolist())
-    assert_one_winner(keys, to_np_u8(codes), lambda k: k not in pre_set)
+    cs = to_np_u8(codes)
+    assert (cs[keys == 0] == 3).all()
+    live_ops = keys != 0
+    assert_one_winner(keys[live_ops], cs[live_ops], lambda k: k not in pre_set)
     assert_same_live_set(t, o)  # sums are order-free: bit-exact
-    live, ne, _ = t.size(check=True)
+    live, ne, _ = t.size()
     assert live == o.live and ne == o.nonempty
 
 
-@pytest.mark.parametrize("g", [1, 4])
-def test_insert_or_update_overwrite(cuda_lib, oracle_mod, g):
+@pytest.mark.parametrize("g,agg", [(0, 1), (1, 0), (4, 0)])
+def test_insert_or_update_overwrite(cuda_lib, oracle_mod, g, agg):
     c = 1 << 15
     keys = W.zipf_keys(40_000, 1.0, n_ranks=1 << 12, seed=53)
     vals = np.arange(1, keys.size + 1, dtype=np.uint64)
     pre = np.unique(keys)[::3]
-    t = _table(cuda_lib, c, g)
+    t = _table(cuda_lib, c, g, iou_aggregate=agg)
     t.insert(to_dev(pre), to_dev(pre))
     codes = codes_buf(keys.size)
     t.insert_or_update(to_dev(keys), to_dev(vals), cuda_lib.OVERWRITE, codes)
