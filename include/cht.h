@@ -66,7 +66,7 @@ typedef enum {
     CHT_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
     CHT_ERR_TABLE_FULL = 4,   /* some operation found no free cell */
     CHT_ERR_RESERVED_KEY = 5, /* some operation used key 0 or ~0 */
-    CHT_ERR_TIMEOUT = 6       /* a bounded device wait gave up */
+    CHT_ERR_TIMEOUT = 6       /* reserved: a bounded device wait gave up */
 } cht_status;
 
 typedef enum {
@@ -77,7 +77,6 @@ typedef enum {
 /* Sticky device status bits (cht_get_status). */
 #define CHT_STATUS_FULL 0x1u
 #define CHT_STATUS_RESERVED 0x2u
-#define CHT_STATUS_TIMEOUT 0x4u /* a bounded device wait gave up (the work was redone) */
 
 /* Tunables.  group_width G: lanes that probe one key together, each loading
  * 16 bytes (G in {1,2,4,8,16,32}); G = 1 uses one 32-byte load (two cells,
@@ -85,13 +84,8 @@ typedef enum {
  * from the table's load (for insert: the load after the batch): 1 below 0.6,
  * 4 below 0.75 (and for erase above it), else 8.  ctas_per_sm: resident CTAs per
  * SM for the operation kernels (0 = occupancy maximum).  migrate_tile:
- * source cells per migration CTA (power of two, 256..8192, 0 = default).
- * alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).
- * wait_limit_us: bound of every device-side wait on an asynchronous copy
- * (0 = default, about one second); a wait that runs out sets
- * CHT_STATUS_TIMEOUT and the work is redone by a slower path.
- * fault_inject: testing only; bit 0 makes each migration CTA first wait on a
- * barrier that nothing completes, so that wait runs out (0 = off).
+ * source cells per migration warp task (power of two, 64..8192, 0 = default
+ * 256).  alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).
  * iou_aggregate: 1 (default) folds equal keys of each window of 1024
  * insertOrUpdate operations in shared memory first (one table operation per
  * distinct key and window); 0 probes every operation with the group kernel. */
@@ -100,8 +94,6 @@ typedef struct {
     int ctas_per_sm;
     int migrate_tile;
     double alpha;
-    int wait_limit_us;
-    int fault_inject;
     int iou_aggregate;
 } cht_config;
 
@@ -164,8 +156,8 @@ cht_status cht_migrate(cht_handle h, uint64_t new_capacity, cht_stream_t stream)
 
 /* Synchronize `stream` and report: live elements (I - D), non-empty cells
  * I (tombstones included), capacity c.  Any out-pointer may be NULL.
- * Returns CHT_ERR_TABLE_FULL / CHT_ERR_RESERVED_KEY / CHT_ERR_TIMEOUT if the
- * sticky status has that bit set (the status is not cleared), else CHT_OK. */
+ * Returns CHT_ERR_TABLE_FULL / CHT_ERR_RESERVED_KEY if the sticky status has
+ * that bit set (the status is not cleared), else CHT_OK. */
 cht_status cht_size(cht_handle h, uint64_t *live, uint64_t *nonempty, uint64_t *capacity,
                     cht_stream_t stream);
 

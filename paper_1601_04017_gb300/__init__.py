@@ -7,12 +7,12 @@ The compute path is hand-written CUDA for sm_103a in ``csrc/``, built into
 from ._build import build
 from .cht import (ADD, CHT_ERR_CUDA, CHT_ERR_INVALID_ARG, CHT_ERR_OOM, CHT_ERR_RESERVED_KEY,
                   CHT_ERR_TABLE_FULL, CHT_ERR_TIMEOUT, CHT_OK, CODE_FULL, CODE_NO, CODE_RESERVED,
-                  CODE_YES, OVERWRITE, STATUS_FULL, STATUS_RESERVED, STATUS_TIMEOUT, ChtError, Table, launch_count,
+                  CODE_YES, OVERWRITE, STATUS_FULL, STATUS_RESERVED, ChtError, Table, launch_count,
                   library_path, load_library, memory_in_use, set_memory_limit, version)
 
 __all__ = [
     "ADD", "OVERWRITE", "Table", "ChtError", "build", "load_library", "library_path", "launch_count",
     "memory_in_use", "set_memory_limit", "version", "CHT_OK", "CHT_ERR_INVALID_ARG", "CHT_ERR_OOM",
     "CHT_ERR_CUDA", "CHT_ERR_TABLE_FULL", "CHT_ERR_RESERVED_KEY", "CHT_ERR_TIMEOUT", "CODE_NO",
-    "CODE_YES", "CODE_FULL", "CODE_RESERVED", "STATUS_FULL", "STATUS_RESERVED", "STATUS_TIMEOUT",
+    "CODE_YES", "CODE_FULL", "CODE_RESERVED", "STATUS_FULL", "STATUS_RESERVED",
 ]

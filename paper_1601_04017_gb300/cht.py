@@ -28,7 +28,6 @@ OVERWRITE = 0
 ADD = 1
 STATUS_FULL = 0x1
 STATUS_RESERVED = 0x2
-STATUS_TIMEOUT = 0x4
 
 CODE_NO, CODE_YES, CODE_FULL, CODE_RESERVED = 0, 1, 2, 3
 
@@ -46,7 +45,6 @@ class ChtError(RuntimeError):
 class ChtConfig(ctypes.Structure):
     _fields_ = [("group_width", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("migrate_tile", ctypes.c_int), ("alpha", ctypes.c_double),
-                ("wait_limit_us", ctypes.c_int), ("fault_inject", ctypes.c_int),
                 ("iou_aggregate", ctypes.c_int)]
 
 
@@ -187,8 +185,7 @@ class Table:
         cur = self.config()
         cur.update(kw)
         c = ChtConfig(int(cur["group_width"]), int(cur["ctas_per_sm"]), int(cur["migrate_tile"]),
-                      float(cur["alpha"]), int(cur["wait_limit_us"]), int(cur["fault_inject"]),
-                      int(cur["iou_aggregate"]))
+                      float(cur["alpha"]), int(cur["iou_aggregate"]))
         _check(self._lib.cht_set_config(self._h, ctypes.byref(c)), "cht_set_config")
 
     # -- operations ----------------------------------------------------------
@@ -232,7 +229,7 @@ class Table:
         live, ne, cap = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         r = self._lib.cht_size(self._h, ctypes.byref(live), ctypes.byref(ne), ctypes.byref(cap),
                                _stream(stream))
-        if r not in (CHT_OK, CHT_ERR_TABLE_FULL, CHT_ERR_RESERVED_KEY, CHT_ERR_TIMEOUT) or (check and r != CHT_OK):
+        if r not in (CHT_OK, CHT_ERR_TABLE_FULL, CHT_ERR_RESERVED_KEY) or (check and r != CHT_OK):
             _check(r, "cht_size")
         return int(live.value), int(ne.value), int(cap.value)
 

@@ -35,12 +35,11 @@ cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, int ctas_per_sm, c
 // Cluster-wise migration of `src` (2^src_log2 cells) into `dst`
 // (2^dst_log2 cells, dst_log2 >= src_log2).  dst needs no initialisation:
 // every target cell is written.  `st` receives the new I (it must be zero
-// on entry) and mig_fail.  tile: source cells per CTA (power of two);
-// wait_limit: bound of one bulk-copy wait in clock cycles (0 = default);
-// inject_stall != 0 makes each CTA first wait on a barrier nothing arrives
-// on (testing the timeout path).
+// on entry) and mig_fail.  tile: source cells per warp task (power of two,
+// 0 = default); border: device scratch of migrate_border_count() u64.
+u64 migrate_border_count(u32 src_log2, int tile);
 cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log2, DevState* st,
-                           int tile, long long wait_limit, int inject_stall, cudaStream_t s);
+                           int tile, u64* border, cudaStream_t s);
 
 // Compact the live cells into keys_out / vals_out (max_n entries); the count
 // lands in st->export_pos, which must be zero on entry.

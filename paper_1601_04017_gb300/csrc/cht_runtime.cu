@@ -162,10 +162,8 @@ cht_config default_config() {
     cht_config c;
     c.group_width = 0;
     c.ctas_per_sm = 0;
-    c.migrate_tile = 1024;
+    c.migrate_tile = 256;
     c.alpha = 0.5;
-    c.wait_limit_us = 0;
-    c.fault_inject = 0;
     c.iou_aggregate = 1;
     return c;
 }
@@ -175,10 +173,8 @@ bool valid_config(const cht_config& c) {
     if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32)) return false;
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64) return false;
     const int t = c.migrate_tile;
-    if (t != 0 && (t < 256 || t > 8192 || (t & (t - 1)) != 0)) return false;
+    if (t != 0 && (t < 64 || t > 8192 || (t & (t - 1)) != 0)) return false;
     if (!(c.alpha > 0.0 && c.alpha < 1.0)) return false;
-    if (c.wait_limit_us < 0 || c.wait_limit_us > 60000000) return false;
-    if (c.fault_inject < 0 || c.fault_inject > 1) return false;
     if (c.iou_aggregate < 0 || c.iou_aggregate > 1) return false;
     return true;
 }
@@ -245,9 +241,16 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
         lib_free(dst, bytes, s);
         return CHT_ERR_CUDA;
     }
-    const long long wait_cycles = (long long)h->cfg.wait_limit_us * 2000;  // ~2 GHz SM clock
-    cudaError_t e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, h->cfg.migrate_tile,
-                                        wait_cycles, h->cfg.fault_inject & 1, s);
+    // scratch: the moved border of every migration tile
+    const u64 nb = cht::migrate_border_count(h->log2c, h->cfg.migrate_tile);
+    u64* border = nullptr;
+    r = lib_alloc(reinterpret_cast<void**>(&border), nb * sizeof(u64), s);
+    if (r != CHT_OK) {
+        lib_free(dst, bytes, s);
+        return r;
+    }
+    cudaError_t e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, h->cfg.migrate_tile, border, s);
+    lib_free(border, nb * sizeof(u64), s);
     if (e != cudaSuccess) {
         lib_free(dst, bytes, s);
         return cuda_status(e);
@@ -434,7 +437,7 @@ cht_status cht_destroy(cht_handle h) {
 cht_status cht_set_config(cht_handle h, const cht_config* cfg) {
     if (!h) return CHT_ERR_INVALID_ARG;
     cht_config c = cfg ? *cfg : default_config();
-    if (c.migrate_tile == 0) c.migrate_tile = 1024;
+    if (c.migrate_tile == 0) c.migrate_tile = 256;
     if (!valid_config(c)) return CHT_ERR_INVALID_ARG;
     h->cfg = c;
     return CHT_OK;
@@ -553,7 +556,6 @@ cht_status cht_size(cht_handle h, uint64_t* live, uint64_t* nonempty, uint64_t* 
     if (capacity) *capacity = h->cap();
     if (ds.status & CHT_STATUS_FULL) return CHT_ERR_TABLE_FULL;
     if (ds.status & CHT_STATUS_RESERVED) return CHT_ERR_RESERVED_KEY;
-    if (ds.status & CHT_STATUS_TIMEOUT) return CHT_ERR_TIMEOUT;
     return CHT_OK;
 }
 

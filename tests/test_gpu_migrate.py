@@ -36,15 +36,16 @@ def _fill(cuda_lib, oracle_mod, log2c, load, erase_frac, seed, wrap=0):
 
 
 @pytest.mark.parametrize("log2c,load,erase,gamma_log2,tile", [
-    (12, 0.5, 0.0, 1, 2048),
+    (12, 0.5, 0.0, 1, 0),
     (16, 0.5, 0.0, 1, 2048),
-    (16, 0.9, 0.0, 1, 256),
-    (16, 0.95, 0.0, 1, 1024),
-    (16, 0.8, 0.4, 0, 2048),
-    (15, 0.6, 0.2, 2, 512),
-    (6, 0.5, 0.0, 1, 2048),     # table smaller than a tile
+    (16, 0.9, 0.0, 1, 64),
+    (16, 0.95, 0.0, 1, 256),     # long clusters crossing many tiles
+    (16, 0.8, 0.4, 0, 512),
+    (15, 0.6, 0.2, 2, 128),
+    (6, 0.5, 0.0, 1, 2048),      # table smaller than a tile
     (18, 0.7, 0.1, 1, 4096),
-    (14, 0.5, 0.0, 4, 1024),    # gamma = 16: global (unstaged) target path
+    (14, 0.5, 0.0, 4, 1024),     # gamma = 16
+    (13, 0.5, 0.0, 8, 256),      # gamma = 256: owned ranges beyond the bitmap (global path)
 ])
 def test_migration_layout_equals_sequential(cuda_lib, oracle_mod, log2c, load, erase, gamma_log2, tile):
     t, _ = _fill(cuda_lib, oracle_mod, log2c, load, erase, seed=log2c + gamma_log2, wrap=5)
@@ -184,24 +185,3 @@ def test_sliding_window_purges_tombstones(cuda_lib, oracle_mod):
     assert cap <= 1 << 16  # the table does not keep doubling: tombstones are purged
     assert_same_live_set(t, o)
 
-
-def test_migration_wait_timeout_is_reported_and_recovered(cuda_lib, oracle_mod):
-    """A bulk-copy wait that runs out (here: a barrier nothing arrives on, via
-    fault_inject) ends the tile kernel with a status bit instead of a hang; the
-    fallback redoes the migration, so the result is still exact."""
-    log2c = 12
-    t, _ = _fill(cuda_lib, oracle_mod, log2c, 0.5, 0.1, seed=9)
-    t.set_config(fault_inject=1, wait_limit_us=20)
-    snap = to_np_u64(t.cells())
-    o = oracle_mod.OracleTable(64)
-    o.load_cells(snap)
-    o.migrate(2 << log2c)
-    t.migrate(2 << log2c)
-    assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), o.cells())
-    with pytest.raises(cuda_lib.ChtError) as e:
-        t.size(check=True)
-    assert e.value.status == cuda_lib.CHT_ERR_TIMEOUT
-    assert t.status() & cuda_lib.STATUS_TIMEOUT
-    t.set_config(fault_inject=0, wait_limit_us=0)
-    t.migrate(4 << log2c)
-    assert t.size(check=True)[0] == o.live
