@@ -43,7 +43,7 @@ class ChtError(RuntimeError):
 
 
 class ChtConfig(ctypes.Structure):
-    _fields_ = [("group_width", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+    _fields_ = [("group_width", ctypes.c_int), ("lane_cells", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("migrate_tile", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("iou_aggregate", ctypes.c_int)]
 
@@ -184,8 +184,8 @@ class Table:
     def set_config(self, **kw):
         cur = self.config()
         cur.update(kw)
-        c = ChtConfig(int(cur["group_width"]), int(cur["ctas_per_sm"]), int(cur["migrate_tile"]),
-                      float(cur["alpha"]), int(cur["iou_aggregate"]))
+        c = ChtConfig(int(cur["group_width"]), int(cur["lane_cells"]), int(cur["ctas_per_sm"]),
+                      int(cur["migrate_tile"]), float(cur["alpha"]), int(cur["iou_aggregate"]))
         _check(self._lib.cht_set_config(self._h, ctypes.byref(c)), "cht_set_config")
 
     # -- operations ----------------------------------------------------------

@@ -23,9 +23,10 @@ struct OpArgs {
     DevState* st;
 };
 
-// Launch one batched operation. group_width in {1,2,4,8,16,32}; ctas_per_sm
-// 0 = occupancy maximum.  Returns the launch error (cudaSuccess if none).
-cudaError_t launch_op(Mode mode, const OpArgs& a, int group_width, int ctas_per_sm,
+// Launch one batched operation. group_width in {1,2,4,8,16,32}; lane_cells
+// 1 or 2 (G = 1 always uses 2; G = 32 only 1); ctas_per_sm 0 = occupancy
+// maximum.  Returns the launch error (cudaSuccess if none).
+cudaError_t launch_op(Mode mode, const OpArgs& a, int group_width, int lane_cells, int ctas_per_sm,
                       cudaStream_t s);
 
 // insertOrUpdate (mode kIouAdd or kIouOverwrite) with CTA-level
@@ -62,6 +63,6 @@ namespace cht {
 // that live outside the runtime translation unit); group_width is the
 // effective width a find would use now.
 void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int* device,
-                int* group_width, int* ctas_per_sm);
+                int* group_width, int* lane_cells, int* ctas_per_sm);
 
 }  // namespace cht

@@ -60,8 +60,8 @@ extern "C" cht_status cht_find_noalloc(cht_handle h, const uint64_t* keys, uint6
     cht::Cell* cells = nullptr;
     cht::u32 log2c = 0;
     cht::DevState* st = nullptr;
-    int device = 0, group_width = 1, ctas_per_sm = 0;
-    cht::table_view(h, &cells, &log2c, &st, &device, &group_width, &ctas_per_sm);
+    int device = 0, group_width = 1, lane_cells = 2, ctas_per_sm = 0;
+    cht::table_view(h, &cells, &log2c, &st, &device, &group_width, &lane_cells, &ctas_per_sm);
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != device && cudaSetDevice(device) != cudaSuccess) return CHT_ERR_CUDA;
@@ -86,7 +86,7 @@ extern "C" cht_status cht_find_noalloc(cht_handle h, const uint64_t* keys, uint6
             a.codes = found ? s_codes : nullptr;
             a.n = n;
             a.st = st;
-            if (cht::launch_op(cht::kFind, a, group_width, ctas_per_sm, s) != cudaSuccess ||
+            if (cht::launch_op(cht::kFind, a, group_width, lane_cells, ctas_per_sm, s) != cudaSuccess ||
                 cudaMemcpyAsync(vals_out, s_vals, n * 8, cudaMemcpyDefault, s) != cudaSuccess ||
                 (found && cudaMemcpyAsync(found, s_codes, n, cudaMemcpyDefault, s) != cudaSuccess))
                 r = CHT_ERR_CUDA;

@@ -6,13 +6,13 @@
 namespace cht {
 namespace {
 
-template <int G, int MODE>
+template <int G, int V, int MODE>
 cudaError_t launch_one(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     static std::atomic<int> occ{0};
     int per_sm = occ.load(std::memory_order_relaxed);
     if (per_sm == 0) {
         cudaError_t e =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, op_kernel<G, MODE>, kOpBlock, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, op_kernel<G, V, MODE>, kOpBlock, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         occ.store(per_sm, std::memory_order_relaxed);
@@ -22,20 +22,31 @@ cudaError_t launch_one(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     const u64 need = (a.n + kOpBlock - 1) / kOpBlock;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    op_kernel<G, MODE><<<unsigned(grid), kOpBlock, 0, s>>>(a);
+    op_kernel<G, V, MODE><<<unsigned(grid), kOpBlock, 0, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
 
+// (group width G, cells per lane V): G = 1 always loads a whole sector.
 template <int MODE>
-cudaError_t launch_mode(const OpArgs& a, int g, int ctas_per_sm, cudaStream_t s) {
+cudaError_t launch_mode(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStream_t s) {
+    if (v == 2) {
+        switch (g) {
+            case 1: return launch_one<1, 2, MODE>(a, ctas_per_sm, s);
+            case 2: return launch_one<2, 2, MODE>(a, ctas_per_sm, s);
+            case 4: return launch_one<4, 2, MODE>(a, ctas_per_sm, s);
+            case 8: return launch_one<8, 2, MODE>(a, ctas_per_sm, s);
+            case 16: return launch_one<16, 2, MODE>(a, ctas_per_sm, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (g) {
-        case 1: return launch_one<1, MODE>(a, ctas_per_sm, s);
-        case 2: return launch_one<2, MODE>(a, ctas_per_sm, s);
-        case 4: return launch_one<4, MODE>(a, ctas_per_sm, s);
-        case 8: return launch_one<8, MODE>(a, ctas_per_sm, s);
-        case 16: return launch_one<16, MODE>(a, ctas_per_sm, s);
-        case 32: return launch_one<32, MODE>(a, ctas_per_sm, s);
+        case 1: return launch_one<1, 2, MODE>(a, ctas_per_sm, s);
+        case 2: return launch_one<2, 1, MODE>(a, ctas_per_sm, s);
+        case 4: return launch_one<4, 1, MODE>(a, ctas_per_sm, s);
+        case 8: return launch_one<8, 1, MODE>(a, ctas_per_sm, s);
+        case 16: return launch_one<16, 1, MODE>(a, ctas_per_sm, s);
+        case 32: return launch_one<32, 1, MODE>(a, ctas_per_sm, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -73,15 +84,16 @@ cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, int ctas_per_sm, c
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_op(Mode mode, const OpArgs& a, int group_width, int ctas_per_sm,
+cudaError_t launch_op(Mode mode, const OpArgs& a, int group_width, int lane_cells, int ctas_per_sm,
                       cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
+    const int v = lane_cells;
     switch (mode) {
-        case kFind: return launch_mode<kFind>(a, group_width, ctas_per_sm, s);
-        case kInsert: return launch_mode<kInsert>(a, group_width, ctas_per_sm, s);
-        case kIouAdd: return launch_mode<kIouAdd>(a, group_width, ctas_per_sm, s);
-        case kIouOverwrite: return launch_mode<kIouOverwrite>(a, group_width, ctas_per_sm, s);
-        case kErase: return launch_mode<kErase>(a, group_width, ctas_per_sm, s);
+        case kFind: return launch_mode<kFind>(a, group_width, v, ctas_per_sm, s);
+        case kInsert: return launch_mode<kInsert>(a, group_width, v, ctas_per_sm, s);
+        case kIouAdd: return launch_mode<kIouAdd>(a, group_width, v, ctas_per_sm, s);
+        case kIouOverwrite: return launch_mode<kIouOverwrite>(a, group_width, v, ctas_per_sm, s);
+        case kErase: return launch_mode<kErase>(a, group_width, v, ctas_per_sm, s);
     }
     return cudaErrorInvalidValue;
 }

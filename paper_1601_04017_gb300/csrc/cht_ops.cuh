@@ -4,8 +4,8 @@
 //
 // Work layout.  Each warp owns a contiguous slice of the operation batch.
 // Its lanes form 32/G groups of G lanes; a group probes one key at a time
-// over an aligned window of W = G*V cells (V = 2 cells per lane for G = 1,
-// fetched with one 256-bit load = one 32-byte DRAM sector; V = 1 otherwise).
+// over an aligned window of W = G*V cells, each lane fetching V cells (V = 2:
+// one 256-bit load = one 32-byte DRAM sector; V = 1: one 16-byte load).
 // A group that finishes its key immediately takes the next key of the warp's
 // slice ("refill"), so every probe step of the warp issues loads for all of
 // its groups instead of idling while the slowest probe of a fixed set of 32
@@ -74,9 +74,8 @@ __device__ __forceinline__ int modify_at(Cell* cp, bool is_key, u64 key, u64 d) 
     return kStepContinue;
 }
 
-template <int G, int MODE>
+template <int G, int V, int MODE>
 __global__ void __launch_bounds__(kOpBlock) op_kernel(OpArgs a) {
-    constexpr int V = (G == 1) ? 2 : 1;
     constexpr u32 W = G * V;
     constexpr u32 FULL = 0xffffffffu;
     constexpr bool kModify = MODE != kFind;

@@ -161,8 +161,9 @@ class Staging {
 cht_config default_config() {
     cht_config c;
     c.group_width = 0;
+    c.lane_cells = 0;
     c.ctas_per_sm = 0;
-    c.migrate_tile = 256;
+    c.migrate_tile = 0;
     c.alpha = 0.5;
     c.iou_aggregate = 1;
     return c;
@@ -171,6 +172,7 @@ cht_config default_config() {
 bool valid_config(const cht_config& c) {
     const int g = c.group_width;
     if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32)) return false;
+    if (c.lane_cells < 0 || c.lane_cells > 2 || (g == 32 && c.lane_cells == 2)) return false;
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64) return false;
     const int t = c.migrate_tile;
     if (t != 0 && (t < 64 || t > 8192 || (t & (t - 1)) != 0)) return false;
@@ -241,15 +243,19 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
         lib_free(dst, bytes, s);
         return CHT_ERR_CUDA;
     }
+    // tile: short clusters (load below 0.6) want small tiles for parallelism,
+    // long ones want large tiles so few clusters straddle tile borders
+    int tile = h->cfg.migrate_tile;
+    if (tile == 0) tile = double(h->i_bound) < 0.6 * double(h->cap()) ? 256 : 1024;
     // scratch: the moved border of every migration tile
-    const u64 nb = cht::migrate_border_count(h->log2c, h->cfg.migrate_tile);
+    const u64 nb = cht::migrate_border_count(h->log2c, tile);
     u64* border = nullptr;
     r = lib_alloc(reinterpret_cast<void**>(&border), nb * sizeof(u64), s);
     if (r != CHT_OK) {
         lib_free(dst, bytes, s);
         return r;
     }
-    cudaError_t e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, h->cfg.migrate_tile, border, s);
+    cudaError_t e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, tile, border, s);
     lib_free(border, nb * sizeof(u64), s);
     if (e != cudaSuccess) {
         lib_free(dst, bytes, s);
@@ -267,20 +273,29 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
     return CHT_OK;
 }
 
-// Group width for a batch: the configured one, or (auto) by the load the
+// Probe width for a batch: the configured one, or (auto) by the load the
 // probes will see -- short probes want one sector per lane (G = 1), long
 // probes at high load want wider windows so fewer dependent steps are needed.
-int pick_group_width(const cht_table* h, cht::Mode mode, u64 n) {
-    if (h->cfg.group_width > 0) return h->cfg.group_width;
-    // Only a plain insert batch is assumed to add n new cells; insertOrUpdate
-    // batches are mostly updates of few hot keys, which want G = 1.
-    u64 filled = h->i_bound;
-    if (mode == cht::kInsert) filled += n;
-    if (filled > h->cap()) filled = h->cap();
-    const double load = double(filled) / double(h->cap());
-    if (load < 0.6) return 1;
-    if (load < 0.75 || mode == cht::kErase) return 4;  // erase ends in an atomic: narrower groups
-    return 8;
+struct Width {
+    int g, v;
+};
+
+Width pick_width(const cht_table* h, cht::Mode mode, u64 n) {
+    Width w{h->cfg.group_width, h->cfg.lane_cells};
+    if (w.g == 0) {
+        // Only a plain insert batch is assumed to add n new cells; insertOrUpdate
+        // batches are mostly updates of few hot keys, which want G = 1.
+        u64 filled = h->i_bound;
+        if (mode == cht::kInsert) filled += n;
+        if (filled > h->cap()) filled = h->cap();
+        const double load = double(filled) / double(h->cap());
+        if (load < 0.6) w.g = 1;
+        else if (load < 0.75 || mode == cht::kErase) w.g = 4;  // erase ends in an atomic: narrower groups
+        else w.g = 8;
+    }
+    if (w.g == 1) w.v = 2;
+    else if (w.v == 0 || w.g == 32) w.v = 1;
+    return w;
 }
 
 cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals, u64* vals_out,
@@ -296,16 +311,18 @@ cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals
     a.st = h->st;
     if ((mode == cht::kIouAdd || mode == cht::kIouOverwrite) && h->cfg.iou_aggregate)
         return cuda_status(cht::launch_iou_aggregated(mode, a, h->cfg.ctas_per_sm, s));
-    return cuda_status(cht::launch_op(mode, a, pick_group_width(h, mode, n), h->cfg.ctas_per_sm, s));
+    const Width w = pick_width(h, mode, n);
+    return cuda_status(cht::launch_op(mode, a, w.g, w.v, h->cfg.ctas_per_sm, s));
 }
 
 // insert / insert_or_update with the growth policy of growable tables.
 cht_status run_modify(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals,
                       unsigned char* codes, u64 n, cudaStream_t s) {
     if (!h->growable) {
-        h->i_bound += n;
+        const cht_status r = launch(h, mode, keys, vals, nullptr, codes, n, s);
+        h->i_bound += n;  // after the launch: the width choice projects n itself
         h->i_exact = false;
-        return launch(h, mode, keys, vals, nullptr, codes, n, s);
+        return r;
     }
     u64 done = 0;
     while (done < n) {
@@ -377,12 +394,14 @@ int sm_count() {
 }
 
 void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int* device, int* group_width,
-                int* ctas_per_sm) {
+                int* lane_cells, int* ctas_per_sm) {
     *cells = h->cells;
     *log2c = h->log2c;
     *st = h->st;
     *device = h->device;
-    *group_width = pick_group_width(h, kFind, 0);  // the width a find would use now
+    const Width w = pick_width(h, kFind, 0);  // the width a find would use now
+    *group_width = w.g;
+    *lane_cells = w.v;
     *ctas_per_sm = h->cfg.ctas_per_sm;
 }
 
@@ -437,7 +456,6 @@ cht_status cht_destroy(cht_handle h) {
 cht_status cht_set_config(cht_handle h, const cht_config* cfg) {
     if (!h) return CHT_ERR_INVALID_ARG;
     cht_config c = cfg ? *cfg : default_config();
-    if (c.migrate_tile == 0) c.migrate_tile = 256;
     if (!valid_config(c)) return CHT_ERR_INVALID_ARG;
     h->cfg = c;
     return CHT_OK;

@@ -15,23 +15,25 @@ from gpu_helpers import (assert_one_winner, assert_same_live_set, codes_buf, ops
 pytestmark = pytest.mark.gpu
 
 GROUPS = [0, 1, 2, 4, 8, 16, 32]  # 0 = chosen by load
+# (group width, cells per lane): every probe window shape the kernels support
+WIDTHS = [(g, 0) for g in GROUPS] + [(2, 2), (4, 2), (8, 2), (16, 2)]
 
 
-def _table(cht, cap, g=1, growable=False, **cfg):
+def _table(cht, cap, g=1, growable=False, v=0, **cfg):
     t = cht.Table(cap, growable=growable)
-    t.set_config(group_width=g, **cfg)
+    t.set_config(group_width=g, lane_cells=v, **cfg)
     return t
 
 
-@pytest.mark.parametrize("g", GROUPS)
+@pytest.mark.parametrize("g,v", WIDTHS)
 @pytest.mark.parametrize("load", [0.5, 0.9])
-def test_insert_find_uniform(cuda_lib, oracle_mod, g, load):
+def test_insert_find_uniform(cuda_lib, oracle_mod, g, v, load):
     log2c = 16
     c = 1 << log2c
     wl = W.bounded_workload(log2c, loads=(load,), n_find=(c // 3) + 17)
     n = wl["counts"][load]
     keys, vals = wl["keys"][:n], wl["vals"][:n]
-    t = _table(cuda_lib, c, g)
+    t = _table(cuda_lib, c, g, v=v)
     o = oracle_mod.OracleTable(c)
     codes = codes_buf(n)
     t.insert(to_dev(keys), to_dev(vals), codes)
@@ -51,15 +53,15 @@ def test_insert_find_uniform(cuda_lib, oracle_mod, g, load):
     assert_same_live_set(t, o)
 
 
-@pytest.mark.parametrize("g", [1, 8])
-def test_insert_duplicates_one_winner(cuda_lib, oracle_mod, g):
+@pytest.mark.parametrize("g,v", [(1, 0), (8, 0), (8, 2)])
+def test_insert_duplicates_one_winner(cuda_lib, oracle_mod, g, v):
     c = 1 << 14
     base = W.uniform_keys(3000, seed=51)
     rng = np.random.default_rng(1)
     pre = base[:500]
     keys = base[rng.integers(0, base.size, 9001)]
     vals = rng.integers(1, 1 << 62, keys.size).astype(np.uint64)
-    t = _table(cuda_lib, c, g)
+    t = _table(cuda_lib, c, g, v=v)
     t.insert(to_dev(pre), to_dev(pre))
     codes = codes_buf(keys.size)
     t.insert(to_dev(keys), to_dev(vals), codes)
@@ -130,11 +132,11 @@ def test_insert_or_update_overwrite(cuda_lib, oracle_mod, g, agg):
         assert v in {r[0] for r in by[k]}
 
 
-@pytest.mark.parametrize("g", [1, 2, 8, 32])
-def test_erase_and_tombstones(cuda_lib, oracle_mod, g):
+@pytest.mark.parametrize("g,v", [(1, 0), (2, 0), (8, 0), (32, 0), (4, 2), (8, 2)])
+def test_erase_and_tombstones(cuda_lib, oracle_mod, g, v):
     c = 1 << 15
     keys = W.uniform_keys(20_000, seed=54)
-    t = _table(cuda_lib, c, g)
+    t = _table(cuda_lib, c, g, v=v)
     o = oracle_mod.OracleTable(c)
     t.insert(to_dev(keys), to_dev(keys))
     o.insert(keys, keys)
@@ -182,9 +184,9 @@ def test_reserved_keys(cuda_lib):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("g", [1, 8, 32])
-def test_full_bounded_table(cuda_lib, g):
-    t = _table(cuda_lib, 64, g)
+@pytest.mark.parametrize("g,v", [(1, 0), (8, 0), (32, 0), (16, 2)])
+def test_full_bounded_table(cuda_lib, g, v):
+    t = _table(cuda_lib, 64, g, v=v)
     keys = W.uniform_keys(100, seed=55)
     codes = codes_buf(100)
     t.insert(to_dev(keys), to_dev(keys), codes)
@@ -212,6 +214,8 @@ def test_empty_batches_and_bad_args(cuda_lib):
     assert t.size() == (0, 0, 1024)
     with pytest.raises(cuda_lib.ChtError):
         t.set_config(group_width=3)
+    with pytest.raises(cuda_lib.ChtError):
+        t.set_config(group_width=32, lane_cells=2)
     with pytest.raises(cuda_lib.ChtError):
         t.insert_or_update(to_dev(np.array([1], np.uint64)), to_dev(np.array([1], np.uint64)), op=7)
 
