@@ -7,7 +7,9 @@ One step is one pass of the whole path over the 2^28-cell workload
   find 2^27 hits + 2^27 misses | for s in {0.5, 1.0, 1.25, 1.5}: a fresh
   2^28-cell table and 2^28 insertOrUpdate(add 1) ops drawn Zipf(s) over 2^26
   keys (word count) | erase 2^27 keys | migrate the load-0.9 table to 2^29
-  cells (gamma = 2) | destroy.
+  cells (gamma = 2) | destroy | a growable table of 2^12 cells takes the
+  2^27 load-0.5 keys in one insert call, doubling 15 times at load 0.5
+  (growth policy and migrations).
 value = operations (inserts + finds + insertOrUpdates + erases) per second of
 the whole step, migration and table creation included.  Inputs are resident
 in HBM before the timed region; every input is far larger than the 129 MB L2.
@@ -38,6 +40,7 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 LOG2C = 28
+GROW_LOG2C0 = 12
 ZIPF_S = (0.5, 1.0, 1.25, 1.5)
 ZIPF_RANKS = 1 << 26
 METRIC = "Mops/s for insert/find/insertOrUpdate at 1 GB300 vs random-access roofline; p50/p99"
@@ -195,9 +198,9 @@ class StepRunner:
             mk = lambda n, dt: torch.empty(n, dtype=dt, device=dev)  # noqa: E731
         self.codes = mk(1 << 28, torch.uint8)
         self.vout = mk(nf, torch.int64)
-        self.ops_per_step = n09 + 4 * nf + 4 * (1 << 28) + nf
-        self.h2d = 8 * (2 * n09 + 4 * nf + 4 * 2 * (1 << 28) + nf) if host else 0
-        self.d2h = (n09 + 4 * (9 * nf) + 4 * (1 << 28) + nf) if host else 0
+        self.ops_per_step = n09 + 4 * nf + 4 * (1 << 28) + nf + n05
+        self.h2d = 8 * (2 * n09 + 4 * nf + 4 * 2 * (1 << 28) + nf + 2 * n05) if host else 0
+        self.d2h = (n09 + 4 * (9 * nf) + 4 * (1 << 28) + nf + n05) if host else 0
 
     def step(self, events: dict | None = None):
         cht, torch = self.cht, self.torch
@@ -228,6 +231,9 @@ class StepRunner:
         timed("erase", lambda: t.erase(self.keys[:nf], self.codes[:nf]))
         timed("migrate_x2", lambda: t.migrate(2 << LOG2C))
         t.destroy()
+        tg = cht.Table(1 << GROW_LOG2C0, growable=True)
+        timed("grow_insert", lambda: tg.insert(self.keys[:n05], self.vals[:n05], self.codes[:n05]))
+        tg.destroy()
 
 
 def per_op_bytes(inp):
@@ -242,6 +248,11 @@ def per_op_bytes(inp):
     }
     for sv in ZIPF_S:
         b[f"iou_add_s{sv}"] = algorithmic_bytes("iou", distinct=inp["distinct"][sv], ops=1 << 28)
+    # growth: the inserts (at loads 0.25..0.5) plus every doubling's migration
+    # traffic (48 B per source cell, 2^12 + ... + 2^27 source cells), per insert
+    n05 = inp["wl"]["counts"][0.5]
+    src_cells = sum(1 << k for k in range(GROW_LOG2C0, LOG2C))
+    b["grow_insert"] = algorithmic_bytes("insert", a0=0.25, a1=0.5) + 48.0 * src_cells / n05
     return b
 
 
@@ -250,7 +261,8 @@ def op_counts(inp):
     n05, n09 = wl["counts"][0.5], wl["counts"][0.9]
     nf = 1 << 27
     d = {"insert_0.5": n05, "insert_0.9": n09 - n05, "find_hit_0.5": nf, "find_miss_0.5": nf,
-         "find_hit_0.9": nf, "find_miss_0.9": nf, "erase": nf, "migrate_x2": 1 << LOG2C}
+         "find_hit_0.9": nf, "find_miss_0.9": nf, "erase": nf, "migrate_x2": 1 << LOG2C,
+         "grow_insert": n05}
     for sv in ZIPF_S:
         d[f"iou_add_s{sv}"] = 1 << 28
     return d
@@ -381,7 +393,7 @@ def run_gpu(args):
             row.update({"bytes_per_src_cell": 48, "gbs": round(gbs, 1),
                         "frac_of_" + peak_kind: round(gbs / peak, 4)})
         breakdown[name] = row
-    probe_rows = {k: v for k, v in breakdown.items() if k != "migrate_x2"}
+    probe_rows = {k: v for k, v in breakdown.items() if k not in ("migrate_x2", "grow_insert")}
     dom = max(probe_rows, key=lambda k: probe_rows[k]["ms"])
     dom_t = probe_rows[dom]["ms"]
     achieved = bpo[dom] * counts[dom] / (dom_t * 1e-3) / 1e9
@@ -426,11 +438,12 @@ def run_gpu(args):
             "data": "synthetic (SplitMix64 uniform keys, Zipf rejection-inversion; generated on device)",
             "config": {"workload": "bounded table 2^28 cells: insert to load 0.5/0.9, find 2^27 hits + "
                                    "2^27 misses at each load, insertOrUpdate(add 1) 2^28 Zipf ops over "
-                                   "2^26 keys for s in {0.5,1.0,1.25,1.5}, erase 2^27, migrate x2",
+                                   "2^26 keys for s in {0.5,1.0,1.25,1.5}, erase 2^27, migrate x2; "
+                                   "growable table 2^12 cells taking 2^27 inserts (15 doublings)",
                        "capacity_cells": 1 << LOG2C, "ops_per_step": runner.ops_per_step,
                        "l2": "inputs and table far larger than L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "group_width": 1},
+                       "probe_window": "auto by load (G=1 below 0.6; 4x32B or 8x32B above)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "breakdown": breakdown, "latency_config1": lat,
         }
@@ -470,6 +483,10 @@ def cpu_sample_step(oracle, inp) -> tuple[int, float]:
     ops += nf
     t.migrate(2 << CPU_LOG2C)
     t.close()
+    tg = oracle.OracleTable(1 << 12, growable=True, alpha=0.5)
+    tg.insert(wl["keys"][:n05], wl["vals"][:n05])
+    ops += n05
+    tg.close()
     return ops, time.perf_counter() - t0
 
 
@@ -480,7 +497,8 @@ def cpu_inputs():
 
 
 SAMPLE_DESC = ("the same step recipe at 2^22 cells: insert to load 0.5/0.9, 2^21 find hits + misses at "
-               "each load, 2^22 Zipf insertOrUpdate(add) per s over 2^20 keys, erase 2^21, migrate x2")
+               "each load, 2^22 Zipf insertOrUpdate(add) per s over 2^20 keys, erase 2^21, migrate x2, "
+               "growable 2^12-cell table taking 2^21 inserts")
 
 
 def cpu_baseline_once():

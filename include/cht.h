@@ -80,11 +80,12 @@ typedef enum {
 
 /* Tunables.  group_width G: lanes that probe one key together, each loading
  * 16 bytes (G in {1,2,4,8,16,32}); G = 1 uses one 32-byte load (two cells,
- * one DRAM sector) per lane and probe step; 0 (default) picks G per batch
- * from the table's load (for insert: the load after the batch): 1 below 0.6,
- * 4 below 0.75 (and for erase above it), else 8.  lane_cells V: cells each
- * lane of a group loads per probe step, 1 (16 bytes) or 2 (one 32-byte
- * sector); 0 = default (2 for G = 1, else 1); G = 32 allows only 1.  ctas_per_sm: resident CTAs per
+ * one DRAM sector) per lane and probe step; 0 (default) picks the window
+ * per batch from the table's load (for insert: the load after the batch):
+ * G = 1 below 0.6, else G = 4 with one sector per lane (G = 8 for finds at
+ * load 0.8 and above).  lane_cells V: cells each lane of a group loads per
+ * probe step, 1 (16 bytes) or 2 (one 32-byte sector); 0 = default (2 for
+ * G = 1 and for the automatic wide windows, else 1); G = 32 allows only 1.  ctas_per_sm: resident CTAs per
  * SM for the operation kernels (0 = occupancy maximum).  migrate_tile:
  * source cells per migration warp task (power of two, 64..8192; 0 = by load:
  * 256 below load 0.6, else 1024).  alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).

@@ -284,14 +284,20 @@ Width pick_width(const cht_table* h, cht::Mode mode, u64 n) {
     Width w{h->cfg.group_width, h->cfg.lane_cells};
     if (w.g == 0) {
         // Only a plain insert batch is assumed to add n new cells; insertOrUpdate
-        // batches are mostly updates of few hot keys, which want G = 1.
+        // batches are mostly updates of few hot keys, which want G = 1.  Measured
+        // on GB300 (2^28 cells): below load 0.6 one sector per lane is best;
+        // above it 4 lanes x 1 sector (128 B windows), and for finds at load
+        // 0.8 and more, 8 lanes x 1 sector (256 B windows).
         u64 filled = h->i_bound;
         if (mode == cht::kInsert) filled += n;
         if (filled > h->cap()) filled = h->cap();
         const double load = double(filled) / double(h->cap());
-        if (load < 0.6) w.g = 1;
-        else if (load < 0.75 || mode == cht::kErase) w.g = 4;  // erase ends in an atomic: narrower groups
-        else w.g = 8;
+        if (load < 0.6) {
+            w.g = 1;
+        } else {
+            w.g = (mode == cht::kFind && load >= 0.8) ? 8 : 4;
+            if (w.v == 0) w.v = 2;
+        }
     }
     if (w.g == 1) w.v = 2;
     else if (w.v == 0 || w.g == 32) w.v = 1;
