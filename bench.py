@@ -541,6 +541,127 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# single-operation cases (small inputs for ncu captures) and the random-access
+# ceiling of the HBM (a pure gather, no hash table)
+# ----------------------------------------------------------------------------
+def run_case(args):
+    """One small case of one operation, timed with CUDA events; prints JSON."""
+    import torch
+
+    import paper_1601_04017_gb300 as cht
+
+    cht.load_library()
+    log2c, load = args.case_log2c, args.case_load
+    c = 1 << log2c
+    s = torch.cuda.current_stream()
+
+    def tm(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        return round(a.elapsed_time(b), 4)
+
+    out = {"case": args.case, "log2c": log2c, "load": load}
+    if args.case in ("find", "insert", "migrate"):
+        wl = W.bounded_workload(log2c, loads=(load,), n_find=c // 2, backend="cuda")
+        n = wl["counts"][load]
+        t = cht.Table(c)
+        codes = torch.empty(n, dtype=torch.uint8, device="cuda")
+        out["insert_ms"] = tm(lambda: t.insert(wl["keys"][:n], wl["vals"][:n], codes))
+        if args.case == "find":
+            vout = torch.empty(c // 2, dtype=torch.int64, device="cuda")
+            out["find_hit_ms"] = tm(lambda: t.find(wl["hits"][load], vout, codes[: c // 2]))
+            out["find_miss_ms"] = tm(lambda: t.find(wl["misses"], vout, codes[: c // 2]))
+        if args.case == "migrate":
+            out["migrate_x2_ms"] = tm(lambda: t.migrate(2 * c))
+        t.destroy()
+    elif args.case == "iou":
+        z = W.zipf_keys(c, args.case_s, min(ZIPF_RANKS, c // 4), W.SEED_ZIPF, backend="cuda")
+        ones = torch.ones(c, dtype=torch.int64, device="cuda")
+        codes = torch.empty(c, dtype=torch.uint8, device="cuda")
+        t = cht.Table(c)
+        out["iou_ms"] = tm(lambda: t.insert_or_update(z, ones, cht.ADD, codes))
+        t.destroy()
+    elif args.case == "grow":
+        keys = W.uniform_keys(c // 2, backend="cuda")
+        vals = W.values_for(keys, backend="cuda")
+        t = cht.Table(1 << GROW_LOG2C0, growable=True)
+        out["grow_insert_ms"] = tm(lambda: t.insert(keys, vals))
+        out["capacity"] = t.size()[2]
+        t.destroy()
+    print(json.dumps(out), flush=True)
+
+
+RANDOM_READ_CU = r"""
+#include <cuda_runtime.h>
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 mix(u64 x) { x ^= x >> 31; x *= 0x7fb5d329728ea185ull; x ^= x >> 27;
+    x *= 0x81dadef4bc2dd44dull; x ^= x >> 33; return x; }
+template <int W> __global__ void rr(const unsigned char* buf, u64 mask, u64 n, u64* out) {
+  u64 acc = 0; const u64 stride = u64(gridDim.x) * blockDim.x;
+  for (u64 i = u64(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned char* p = buf + (mix(i + 1) & mask) * W;
+    if (W == 16) { u64 a, b; asm volatile("ld.global.nc.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p)); acc ^= a ^ b; }
+    else for (int k = 0; k < W / 32; ++k) { u64 a, b, c, d;
+      asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p + 32 * k));
+      acc ^= a ^ b ^ c ^ d; }
+  }
+  out[u64(blockIdx.x) * blockDim.x + threadIdx.x] = acc;
+}
+extern "C" float run_rr(const void* buf, u64 bytes, u64 n, int width, u64* out, int grid) {
+  cudaEvent_t a, b; cudaEventCreate(&a); cudaEventCreate(&b);
+  const u64 mask = bytes / width - 1; cudaEventRecord(a);
+  if (width == 16) rr<16><<<grid, 256>>>((const unsigned char*)buf, mask, n, out);
+  if (width == 32) rr<32><<<grid, 256>>>((const unsigned char*)buf, mask, n, out);
+  if (width == 64) rr<64><<<grid, 256>>>((const unsigned char*)buf, mask, n, out);
+  if (width == 128) rr<128><<<grid, 256>>>((const unsigned char*)buf, mask, n, out);
+  cudaEventRecord(b); cudaEventSynchronize(b); float ms = 0; cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a); cudaEventDestroy(b); return cudaGetLastError() == cudaSuccess ? ms : -1.0f;
+}
+"""
+
+
+def probe_random_access():
+    """Random-read bandwidth of the HBM: n reads of W bytes at uniformly random
+    W-aligned offsets of a 4 GiB buffer (and of a 16 MiB, L2-resident one).
+    This is the practical ceiling of a probe that touches one sector per step."""
+    import ctypes
+    import tempfile
+
+    import torch
+
+    from paper_1601_04017_gb300 import _build
+
+    d = tempfile.mkdtemp(prefix="cht_probe_")
+    src, so = os.path.join(d, "rr.cu"), os.path.join(d, "rr.so")
+    with open(src, "w") as f:
+        f.write(RANDOM_READ_CU)
+    subprocess.check_call([_build.nvcc_path(), *_build.ARCH, "-O3", "-shared", "-Xcompiler", "-fPIC",
+                           "-o", so, src])
+    lib = ctypes.CDLL(so)
+    lib.run_rr.restype = ctypes.c_float
+    lib.run_rr.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
+                           ctypes.c_int]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    grid = sms * 32
+    out = torch.empty(grid * 256, dtype=torch.int64, device="cuda")
+    res = []
+    for log2b in (24, 32):
+        nbytes = 1 << log2b
+        buf = torch.randint(0, 1 << 62, (nbytes // 8,), dtype=torch.int64, device="cuda")
+        for width in (16, 32, 64, 128):
+            n = (1 << 32) // width
+            lib.run_rr(buf.data_ptr(), nbytes, n, width, out.data_ptr(), grid)
+            ms = lib.run_rr(buf.data_ptr(), nbytes, n, width, out.data_ptr(), grid)
+            res.append({"buffer_bytes": nbytes, "width_bytes": width, "ms": round(ms, 4),
+                        "gbs": round(n * width / ms / 1e6, 1), "greads_per_s": round(n / ms / 1e6, 2)})
+        del buf
+    print(json.dumps({"probe": "random_read", "results": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -551,7 +672,20 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-reps", type=int, default=100)
+    ap.add_argument("--case", choices=["find", "insert", "migrate", "iou", "grow"],
+                    help="run one small single-operation case (for profiling) instead of the benchmark")
+    ap.add_argument("--case-log2c", type=int, default=26)
+    ap.add_argument("--case-load", type=float, default=0.9)
+    ap.add_argument("--case-s", type=float, default=1.0)
+    ap.add_argument("--probe-random-access", action="store_true",
+                    help="measure the HBM random-read ceiling instead of the benchmark")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
+    if args.probe_random_access:
+        probe_random_access()
+        return
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
