@@ -22,8 +22,10 @@
 // each lane walks one cluster, re-inserting its live cells in order.  The
 // occupancy of the warp's owned target range is a bitmap in shared memory
 // (lanes own disjoint target ranges, so a lane only ever claims its own
-// cells), elements are stored straight to the target, and the cells left
-// free are zero-filled afterwards, so every target cell is written once.
+// cells).  For owned ranges of up to 2048 cells (nearly all at load 0.5) a
+// lane records which source cell went to each target cell, and the warp then
+// writes the whole range in one coalesced pass -- every 32-byte sector once
+// and whole; longer ranges store elements directly and zero-fill the rest.
 // A border scan that finds no empty cell within kMaxScan cells (a full
 // table, or a cluster longer than that) sets mig_fail; a single-CTA fallback
 // kernel, always launched after the tile kernel, then redoes the whole
@@ -36,7 +38,9 @@ namespace {
 constexpr int kMigBlock = 256;
 constexpr int kMigWarps = kMigBlock / 32;
 constexpr u32 kMaxScan = 1u << 16;      // longest overhang of a tile's last cluster
-constexpr u32 kBitmapWords = 1024;      // per warp: 32768 target cells
+constexpr u32 kMapCells = 2048;        // per warp: owned ranges written through the map
+constexpr u32 kRegionWords = 1024;     // per warp: map (2048 x u16) or a 32768-cell bitmap
+constexpr u32 kSmallBitWords = kMapCells / 32;
 constexpr u64 kNoBorder = ~0ull;
 
 struct MigArgs {
@@ -88,9 +92,14 @@ __device__ __forceinline__ u64 warp_sum(u64 x) {
 __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    u32* const bm = reinterpret_cast<u32*>(smem) + wib * kBitmapWords;
+    // per warp: a region of kRegionWords words (the source-offset map of a
+    // short owned range, or the occupancy bitmap of a long one), the small
+    // bitmap of the map mode, and the cluster-start list
+    u32* const region = reinterpret_cast<u32*>(smem) + wib * (kRegionWords + kSmallBitWords);
+    unsigned short* const map = reinterpret_cast<unsigned short*>(region);
+    u32* const small_bm = region + kRegionWords;
     unsigned short* const starts =
-        reinterpret_cast<unsigned short*>(reinterpret_cast<u32*>(smem) + kMigWarps * kBitmapWords) +
+        reinterpret_cast<unsigned short*>(reinterpret_cast<u32*>(smem) + kMigWarps * (kRegionWords + kSmallBitWords)) +
         wib * a.start_cap;
 
     const u64 c = 1ull << a.slog2, cmask = c - 1;
@@ -114,7 +123,10 @@ __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
         const u64 L = m1 - m0;     // source cells of this tile's clusters
         const u64 tl = L << g;     // owned target cells
         const u64 tbase = m0 << g; // first owned target cell (unwrapped)
-        const bool use_bm = tl <= u64(kBitmapWords) * 32;
+        // map mode: placements recorded, target written in one full-cell pass;
+        // bitmap mode: direct stores plus a zero fill; else global probing
+        const int mode = tl <= kMapCells ? 0 : (tl <= u64(kRegionWords) * 32 ? 1 : 2);
+        u32* const bm = mode == 0 ? small_bm : region;
 
         // ---- cluster starts in [m0, min(m1, d+T)): non-empty after an empty
         const u64 sl = (m1 < d + T ? m1 : d + T) - m0;
@@ -130,7 +142,7 @@ __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
             if (st) starts[ns + __popc(b & ((1u << lane) - 1u))] = (unsigned short)j;
             ns += __popc(b);
         }
-        if (use_bm) {
+        if (mode < 2) {
             const u32 words = u32((tl + 31) / 32);
             for (u32 w = lane; w < words; w += 32) bm[w] = 0;
         } else {
@@ -145,10 +157,9 @@ __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
                 ld_cell_nc(a.src + (i & cmask), k, v);
                 if (k == kEmpty) break;
                 if (k == kTomb) continue;
-                const u64 loc0 = (home_of(k, dshift) - tbase) & nmask;
-                u64 loc = loc0;
-                if (use_bm) {
-                    // first free bit >= loc0 (bits of other lanes' ranges are
+                u64 loc = (home_of(k, dshift) - tbase) & nmask;
+                if (mode < 2) {
+                    // first free bit >= loc (bits of other lanes' ranges are
                     // never in this cluster's window, so a plain read is safe)
                     u32 w = u32(loc >> 5);
                     u32 free = ~reinterpret_cast<volatile u32*>(bm)[w] & (~0u << (loc & 31));
@@ -162,6 +173,14 @@ __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
                         break;
                     }
                     atomicOr(&bm[w], 1u << (loc & 31));
+                    if (mode == 0) {
+                        map[loc] = (unsigned short)(i - m0);
+                    } else {
+                        Cell cl;
+                        cl.key = k;
+                        cl.val = v;
+                        a.dst[(tbase + loc) & nmask] = cl;
+                    }
                 } else {
                     for (;; ++loc) {
                         if (loc >= tl) {
@@ -173,17 +192,23 @@ __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
                         if (tk == kEmpty) break;
                     }
                     if (bad) break;
+                    Cell cl;
+                    cl.key = k;
+                    cl.val = v;
+                    a.dst[(tbase + loc) & nmask] = cl;
                 }
-                Cell cl;
-                cl.key = k;
-                cl.val = v;
-                a.dst[(tbase + loc) & nmask] = cl;
                 ++moved;
             }
         }
         __syncwarp();
-        // ---- zero the owned target cells nothing was placed in
-        if (use_bm) {
+        // ---- write the owned target range: every cell once
+        if (mode == 0) {
+            for (u64 k = lane; k < tl; k += 32) {
+                Cell cl = zero;
+                if ((bm[k >> 5] >> (k & 31)) & 1u) ld_cell_nc(a.src + ((m0 + map[k]) & cmask), cl.key, cl.val);
+                a.dst[(tbase + k) & nmask] = cl;
+            }
+        } else if (mode == 1) {
             for (u64 k = lane; k < tl; k += 32)
                 if (!((bm[k >> 5] >> (k & 31)) & 1u)) a.dst[(tbase + k) & nmask] = zero;
         }
@@ -296,7 +321,7 @@ cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = size_t(kMigWarps) * (kBitmapWords * 4 + size_t(a.start_cap) * 2);
+    const size_t smem = size_t(kMigWarps) * ((kRegionWords + kSmallBitWords) * 4 + size_t(a.start_cap) * 2);
     e = cudaFuncSetAttribute(migrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;

@@ -280,7 +280,8 @@ namespace cht {
 // insertOrUpdate with CTA-level aggregation in shared memory.
 //
 // A CTA takes windows of kAggWindow consecutive operations.  Equal keys of a
-// window are folded into one slot of a shared-memory table (open addressing,
+// warp's load step are first combined with __match_any_sync; then equal keys
+// of the window are folded into one slot of a shared-memory table (open addressing,
 // kAggSlots >= 2 * kAggWindow slots, so every key finds a slot): the add
 // operator sums the values (fetch-and-add on the slot), overwrite keeps the
 // value of the slot's first operation.  The window is then flushed: one
@@ -356,14 +357,41 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
         for (int j = 0; j < kAggWindow / kAggBlock; ++j) {
             const u32 off = u32(j * kAggBlock + tid);
             const u64 idx = w0 + off;
-            if (idx >= a.n) continue;
-            const u64 key = ld_stream(a.keys + idx);
-            const u64 d = ld_stream(a.vals + idx);
-            if (is_reserved(key)) {
-                if (a.codes) a.codes[idx] = kCodeReserved;
-                sbits |= kReserved;
-                continue;
+            bool valid = idx < a.n;
+            u64 key = 0, d = 0;
+            if (valid) {
+                key = ld_stream(a.keys + idx);
+                d = ld_stream(a.vals + idx);
+                if (is_reserved(key)) {
+                    if (a.codes) a.codes[idx] = kCodeReserved;
+                    sbits |= kReserved;
+                    valid = false;
+                }
             }
+            // equal keys within the warp first: one lane per key goes on
+            const u32 vm = __ballot_sync(0xffffffffu, valid);
+            if (valid) {
+                const u32 same = __match_any_sync(vm, key);
+                const int lane = tid & 31;
+                if (MODE == kIouAdd) {
+                    u32 rem = same;
+                    u64 total = 0;
+                    while (__any_sync(vm, rem != 0)) {
+                        const int src = rem ? __ffs(rem) - 1 : lane;
+                        const u64 x = __shfl_sync(vm, d, src);
+                        if (rem) {
+                            total += x;
+                            rem &= rem - 1u;
+                        }
+                    }
+                    d = total;
+                }
+                if (lane != __ffs(same) - 1) {
+                    if (a.codes) a.codes[idx] = kNo;
+                    valid = false;
+                }
+            }
+            if (!valid) continue;
             u32 s = u32(fmix64(key)) & (kAggSlots - 1);
             for (;;) {
                 const u64 k0 = *reinterpret_cast<volatile u64*>(skey + s);
