@@ -91,7 +91,9 @@ typedef enum {
  * 256 below load 0.6, else 1024).  alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).
  * iou_aggregate: 1 (default) folds equal keys of each window of 1024
  * insertOrUpdate operations in shared memory first (one table operation per
- * distinct key and window); 0 probes every operation with the group kernel. */
+ * distinct key and window); 2 also combines equal keys within each warp step
+ * before that (faster only under extreme skew); 0 probes every operation
+ * with the group kernel. */
 typedef struct {
     int group_width;
     int lane_cells;

@@ -31,7 +31,8 @@ cudaError_t launch_op(Mode mode, const OpArgs& a, int group_width, int lane_cell
 
 // insertOrUpdate (mode kIouAdd or kIouOverwrite) with CTA-level
 // aggregation of equal keys in shared memory before the table is touched.
-cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, int ctas_per_sm, cudaStream_t s);
+// warp_dedup: first combine equal keys of each warp step (extreme skew).
+cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, bool warp_dedup, int ctas_per_sm, cudaStream_t s);
 
 // Cluster-wise migration of `src` (2^src_log2 cells) into `dst`
 // (2^dst_log2 cells, dst_log2 >= src_log2).  dst needs no initialisation:

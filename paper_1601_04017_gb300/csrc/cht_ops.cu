@@ -51,16 +51,16 @@ cudaError_t launch_mode(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStre
     }
 }
 
-template <int MODE>
+template <int MODE, bool WD>
 cudaError_t launch_agg(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     constexpr size_t smem = size_t(kAggSlots) * (8 + 8 + 4);
     static std::atomic<int> occ{0};
     int per_sm = occ.load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(iou_agg_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(iou_agg_kernel<MODE, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smem));
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iou_agg_kernel<MODE>, kAggBlock, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iou_agg_kernel<MODE, WD>, kAggBlock, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         occ.store(per_sm, std::memory_order_relaxed);
@@ -70,17 +70,20 @@ cudaError_t launch_agg(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     const u64 nwin = (a.n + kAggWindow - 1) / kAggWindow;
     if (grid > nwin) grid = nwin;
     if (grid < 1) grid = 1;
-    iou_agg_kernel<MODE><<<unsigned(grid), kAggBlock, smem, s>>>(a);
+    iou_agg_kernel<MODE, WD><<<unsigned(grid), kAggBlock, smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
+cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, bool warp_dedup, int ctas_per_sm, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    if (mode == kIouAdd) return launch_agg<kIouAdd>(a, ctas_per_sm, s);
-    if (mode == kIouOverwrite) return launch_agg<kIouOverwrite>(a, ctas_per_sm, s);
+    if (mode == kIouAdd)
+        return warp_dedup ? launch_agg<kIouAdd, true>(a, ctas_per_sm, s) : launch_agg<kIouAdd, false>(a, ctas_per_sm, s);
+    if (mode == kIouOverwrite)
+        return warp_dedup ? launch_agg<kIouOverwrite, true>(a, ctas_per_sm, s)
+                          : launch_agg<kIouOverwrite, false>(a, ctas_per_sm, s);
     return cudaErrorInvalidValue;
 }
 

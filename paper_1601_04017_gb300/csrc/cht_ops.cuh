@@ -279,9 +279,8 @@ namespace cht {
 // ---------------------------------------------------------------------------
 // insertOrUpdate with CTA-level aggregation in shared memory.
 //
-// A CTA takes windows of kAggWindow consecutive operations.  Equal keys of a
-// warp's load step are first combined with __match_any_sync; then equal keys
-// of the window are folded into one slot of a shared-memory table (open addressing,
+// A CTA takes windows of kAggWindow consecutive operations.  Equal keys of the
+// window are folded into one slot of a shared-memory table (open addressing,
 // kAggSlots >= 2 * kAggWindow slots, so every key finds a slot): the add
 // operator sums the values (fetch-and-add on the slot), overwrite keeps the
 // value of the slot's first operation.  The window is then flushed: one
@@ -289,7 +288,9 @@ namespace cht {
 // atomicUpdate), whose result -- inserted or updated -- goes to the slot's
 // first operation; every other operation of the key reports "updated"
 // (linearized right after it).  Under skewed keys this turns millions of
-// atomics on one hot cell into one per window.
+// atomics on one hot cell into one per window.  Variant WARP_DEDUP first
+// combines equal keys of a warp's load step with __match_any_sync, which
+// pays off only under extreme skew (many lanes on one shared-memory slot).
 // ---------------------------------------------------------------------------
 constexpr int kAggBlock = 256;
 constexpr int kAggWindow = 1024;
@@ -333,7 +334,7 @@ __device__ __forceinline__ unsigned char global_modify(const OpArgs& a, u64 key,
     return kCodeFull;
 }
 
-template <int MODE>
+template <int MODE, bool WARP_DEDUP>
 __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
     extern __shared__ __align__(16) unsigned char agg_smem[];
     u64* const skey = reinterpret_cast<u64*>(agg_smem);
@@ -368,9 +369,9 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
                     valid = false;
                 }
             }
-            // equal keys within the warp first: one lane per key goes on
-            const u32 vm = __ballot_sync(0xffffffffu, valid);
-            if (valid) {
+            // optionally, equal keys within the warp first: one lane per key goes on
+            const u32 vm = WARP_DEDUP ? __ballot_sync(0xffffffffu, valid) : 0u;
+            if (WARP_DEDUP && valid) {
                 const u32 same = __match_any_sync(vm, key);
                 const int lane = tid & 31;
                 if (MODE == kIouAdd) {

@@ -177,7 +177,7 @@ bool valid_config(const cht_config& c) {
     const int t = c.migrate_tile;
     if (t != 0 && (t < 64 || t > 8192 || (t & (t - 1)) != 0)) return false;
     if (!(c.alpha > 0.0 && c.alpha < 1.0)) return false;
-    if (c.iou_aggregate < 0 || c.iou_aggregate > 1) return false;
+    if (c.iou_aggregate < 0 || c.iou_aggregate > 2) return false;
     return true;
 }
 
@@ -316,7 +316,7 @@ cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals
     a.n = n;
     a.st = h->st;
     if ((mode == cht::kIouAdd || mode == cht::kIouOverwrite) && h->cfg.iou_aggregate)
-        return cuda_status(cht::launch_iou_aggregated(mode, a, h->cfg.ctas_per_sm, s));
+        return cuda_status(cht::launch_iou_aggregated(mode, a, h->cfg.iou_aggregate == 2, h->cfg.ctas_per_sm, s));
     const Width w = pick_width(h, mode, n);
     return cuda_status(cht::launch_op(mode, a, w.g, w.v, h->cfg.ctas_per_sm, s));
 }

@@ -84,7 +84,7 @@ def test_insert_duplicates_one_winner(cuda_lib, oracle_mod, g, v):
     assert live == len(pre_set | set(keys.tolist()))
 
 
-IOU_PATHS = [(0, 1)] + [(g, 0) for g in GROUPS]  # (group width, shared-memory aggregation)
+IOU_PATHS = [(0, 1), (0, 2)] + [(g, 0) for g in GROUPS]  # (group width, shared-memory aggregation)
 
 
 @pytest.mark.parametrize("g,agg", IOU_PATHS)
@@ -112,7 +112,7 @@ def test_insert_or_update_add_exact(cuda_lib, oracle_mod, g, agg, s):
     assert live == o.live and ne == o.nonempty
 
 
-@pytest.mark.parametrize("g,agg", [(0, 1), (1, 0), (4, 0)])
+@pytest.mark.parametrize("g,agg", [(0, 1), (0, 2), (1, 0), (4, 0)])
 def test_insert_or_update_overwrite(cuda_lib, oracle_mod, g, agg):
     c = 1 << 15
     keys = W.zipf_keys(40_000, 1.0, n_ranks=1 << 12, seed=53)
