@@ -74,8 +74,12 @@ __device__ __forceinline__ int modify_at(Cell* cp, bool is_key, u64 key, u64 d) 
     return kStepContinue;
 }
 
+// One warp runs the operations [next, end) of the batch with the group
+// refill loop; counters and status bits accumulate into the caller's
+// registers (every lane of the warp must call it).
 template <int G, int V, int MODE>
-__global__ void __launch_bounds__(kOpBlock) op_kernel(OpArgs a) {
+__device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 end, u64& n_ins, u64& n_del,
+                                         u32& sbits) {
     constexpr u32 W = G * V;
     constexpr u32 FULL = 0xffffffffu;
     constexpr bool kModify = MODE != kFind;
@@ -90,16 +94,8 @@ __global__ void __launch_bounds__(kOpBlock) op_kernel(OpArgs a) {
     const u32 group_lanes = (G == 32) ? FULL : (((1u << G) - 1u) << g0);
     const u32 below_group = (1u << g0) - 1u;
 
-    const u64 warp = (u64(blockIdx.x) * kOpBlock + threadIdx.x) >> 5;
-    const u64 nwarps = (u64(gridDim.x) * kOpBlock) >> 5;
-    const u64 per = (a.n + nwarps - 1) / nwarps;
-    u64 next = warp * per;
-    const u64 end = next + per < a.n ? next + per : a.n;
-
     bool active = false;
     u64 idx = 0, key = 0, d = 0, pos = 0, probed = 0;
-    u64 n_ins = 0, n_del = 0;
-    u32 sbits = 0;
 
     for (;;) {
         // ---- refill idle groups from this warp's slice
@@ -257,19 +253,35 @@ __global__ void __launch_bounds__(kOpBlock) op_kernel(OpArgs a) {
         }
     }
 
-    // ---- per-warp aggregation of the counters and status bits
-    if (kModify) {
-        for (int o = 16; o > 0; o >>= 1) {
-            n_ins += __shfl_xor_sync(FULL, n_ins, o);
-            n_del += __shfl_xor_sync(FULL, n_del, o);
-        }
+}
+
+// Sum the warp's counters and status bits into the table's device state.
+__device__ __forceinline__ void warp_flush_counters(DevState* st, u64 n_ins, u64 n_del, u32 sbits) {
+    constexpr u32 FULL = 0xffffffffu;
+    for (int o = 16; o > 0; o >>= 1) {
+        n_ins += __shfl_xor_sync(FULL, n_ins, o);
+        n_del += __shfl_xor_sync(FULL, n_del, o);
     }
     const u32 any_status = __reduce_or_sync(FULL, sbits);
-    if (lane == 0) {
-        if (n_ins) atomicAdd(&a.st->I, n_ins);
-        if (n_del) atomicAdd(&a.st->D, n_del);
-        if (any_status) atomicOr(&a.st->status, any_status);
+    if ((threadIdx.x & 31) == 0) {
+        if (n_ins) atomicAdd(&st->I, n_ins);
+        if (n_del) atomicAdd(&st->D, n_del);
+        if (any_status) atomicOr(&st->status, any_status);
     }
+}
+
+template <int G, int V, int MODE>
+__global__ void __launch_bounds__(kOpBlock) op_kernel(OpArgs a) {
+    // each warp owns a contiguous slice of the batch
+    const u64 warp = (u64(blockIdx.x) * kOpBlock + threadIdx.x) >> 5;
+    const u64 nwarps = (u64(gridDim.x) * kOpBlock) >> 5;
+    const u64 per = (a.n + nwarps - 1) / nwarps;
+    const u64 begin = warp * per;
+    const u64 end = begin + per < a.n ? begin + per : a.n;
+    u64 n_ins = 0, n_del = 0;
+    u32 sbits = 0;
+    warp_ops<G, V, MODE>(a, begin, end, n_ins, n_del, sbits);
+    warp_flush_counters(a.st, n_ins, n_del, sbits);
 }
 
 }  // namespace cht
