@@ -186,6 +186,72 @@ cht_status cht_copy_cells(cht_handle h, uint64_t *cells_out, uint64_t max_cells,
 /* Make every cell empty again and reset the counters (capacity unchanged). */
 cht_status cht_clear(cht_handle h, cht_stream_t stream);
 
+/* ---- Batched engine: many tables, many batches, one persistent launch -------
+ * A plan holds a list of batches over any number of tables (all on one
+ * device).  Each batch is one operation type on one table, exactly as a
+ * single call of cht_find / cht_insert / cht_insert_or_update / cht_erase
+ * would run it; batches on the same table run in list order with phase
+ * semantics (every operation of an earlier batch before any of a later one),
+ * batches on different tables are independent and overlap on the device.
+ * cht_plan_launch runs the whole plan in ONE kernel launch: the batches are
+ * cut into work items of 256 operations that warps of a persistent grid take
+ * from a device work queue; an item waits (bounded) until its table's earlier
+ * items are done.  Arrays must be device memory and stay valid while the plan
+ * exists; the plan applies no growth policy (a full table reports code 2).
+ * The launch is stream-ordered and can be captured in a CUDA graph. */
+typedef enum {
+    CHT_OP_FIND = 0,
+    CHT_OP_INSERT = 1,
+    CHT_OP_IOU_ADD = 2,
+    CHT_OP_IOU_OVERWRITE = 3,
+    CHT_OP_ERASE = 4
+} cht_op_kind;
+
+typedef struct {
+    cht_handle table;
+    int op;                 /* cht_op_kind */
+    const uint64_t *keys;   /* n keys */
+    const uint64_t *vals;   /* n values (insert, insert-or-update), else NULL */
+    uint64_t n;
+    uint64_t *vals_out;     /* n found values (find), else NULL */
+    uint8_t *codes;         /* n result codes as for the single calls, or NULL */
+} cht_batch_op;
+
+typedef struct cht_plan *cht_plan_handle;
+
+/* group_width / lane_cells: probe window as in cht_config (0 = 1 lane x one
+ * sector); ctas_per_sm: 0 = occupancy maximum; spin_limit_us: bound of one
+ * dependency wait (0 = about one second) -- a wait that runs out stops the
+ * launch with CHT_PLAN_TIMEOUT in the plan status; fault_inject: testing
+ * only, bit 0 makes the first work item wait for a count nothing reaches. */
+typedef struct {
+    int group_width;
+    int lane_cells;
+    int ctas_per_sm;
+    int spin_limit_us;
+    int fault_inject;
+} cht_plan_config;
+
+#define CHT_PLAN_TIMEOUT 0x1u
+
+/* Build a plan from n_ops batch descriptors (copied; the arrays they point to
+ * are not).  Validates every descriptor (host arrays are rejected with
+ * CHT_ERR_INVALID_ARG).  Allocates the plan's device buffers. */
+cht_status cht_plan_create(const cht_batch_op *ops, uint64_t n_ops, cht_plan_handle *out);
+cht_status cht_plan_set_config(cht_plan_handle p, const cht_plan_config *cfg);
+cht_status cht_plan_get_config(cht_plan_handle p, cht_plan_config *cfg);
+/* Run the plan: reset its counters and launch the engine on `stream`. */
+cht_status cht_plan_launch(cht_plan_handle p, cht_stream_t stream);
+/* Synchronize `stream` and return the status bits of the last launch. */
+cht_status cht_plan_status(cht_plan_handle p, uint32_t *bits, cht_stream_t stream);
+/* Try the engine's probe windows and CTAs/SM on this plan and keep the
+ * fastest: each trial runs on a copy of the plan's tables, which are restored
+ * afterwards (their contents are unchanged on return; the plan's output
+ * arrays hold the results of the last trial).  *best_ms (nullable) receives
+ * the best time.  Needs device memory for one copy of every table. */
+cht_status cht_plan_autotune(cht_plan_handle p, cht_stream_t stream, double *best_ms);
+cht_status cht_plan_destroy(cht_plan_handle p);
+
 /* Cap, in bytes, on the device memory this library allocates at any time for
  * tables and staging (0 = no cap).  An allocation that would exceed it fails
  * with CHT_ERR_OOM exactly like a failed cudaMalloc. */

@@ -48,6 +48,21 @@ class ChtConfig(ctypes.Structure):
                 ("iou_aggregate", ctypes.c_int)]
 
 
+OP_FIND, OP_INSERT, OP_IOU_ADD, OP_IOU_OVERWRITE, OP_ERASE = 0, 1, 2, 3, 4
+PLAN_TIMEOUT = 0x1
+
+
+class BatchOp(ctypes.Structure):
+    _fields_ = [("table", ctypes.c_void_p), ("op", ctypes.c_int), ("keys", ctypes.c_void_p),
+                ("vals", ctypes.c_void_p), ("n", ctypes.c_uint64), ("vals_out", ctypes.c_void_p),
+                ("codes", ctypes.c_void_p)]
+
+
+class PlanConfig(ctypes.Structure):
+    _fields_ = [("group_width", ctypes.c_int), ("lane_cells", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("spin_limit_us", ctypes.c_int), ("fault_inject", ctypes.c_int)]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -83,6 +98,13 @@ def load_library(build: bool = True):
             "cht_launch_count": (u64, []),
             "cht_status_string": (ctypes.c_char_p, [i32]),
             "cht_version": (i32, []),
+            "cht_plan_create": (i32, [p, u64, ctypes.POINTER(p)]),
+            "cht_plan_set_config": (i32, [p, ctypes.POINTER(PlanConfig)]),
+            "cht_plan_get_config": (i32, [p, ctypes.POINTER(PlanConfig)]),
+            "cht_plan_launch": (i32, [p, p]),
+            "cht_plan_status": (i32, [p, ctypes.POINTER(ctypes.c_uint32), p]),
+            "cht_plan_autotune": (i32, [p, p, ctypes.POINTER(ctypes.c_double)]),
+            "cht_plan_destroy": (i32, [p]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -264,6 +286,65 @@ class Table:
         _check(self._lib.cht_copy_cells(self._h, out.data_ptr(), cap, ctypes.byref(n), _stream(stream)),
                "cht_copy_cells")
         return out
+
+
+class Plan:
+    """cht_plan_*: many batches over many tables, run by one kernel launch.
+
+    `ops` is a list of (table, op, keys, vals, vals_out, codes) tuples with CUDA
+    tensors (vals / vals_out / codes may be None where unused).  Batches on the
+    same table run in list order; the arrays must stay alive with the plan.
+    """
+
+    def __init__(self, ops):
+        self._lib = load_library()
+        arr = (BatchOp * max(len(ops), 1))()
+        self._keep = []
+        for i, (table, op, keys, vals, vals_out, codes) in enumerate(ops):
+            kp, n, _ = _ptr(keys, 8, what="keys")
+            vp, _, _ = _ptr(vals, 8, n, "vals")
+            op_, _, _ = _ptr(vals_out, 8, n, "vals_out")
+            cp, _, _ = _ptr(codes, 1, n, "codes")
+            arr[i] = BatchOp(table._h.value, int(op), kp, vp, n, op_, cp)
+            self._keep.append((keys, vals, vals_out, codes))
+        h = ctypes.c_void_p()
+        _check(self._lib.cht_plan_create(arr, len(ops), ctypes.byref(h)), "cht_plan_create")
+        self._h = h
+
+    def config(self) -> dict:
+        c = PlanConfig()
+        _check(self._lib.cht_plan_get_config(self._h, ctypes.byref(c)), "cht_plan_get_config")
+        return {f: getattr(c, f) for f, _ in PlanConfig._fields_}
+
+    def set_config(self, **kw):
+        cur = self.config()
+        cur.update(kw)
+        c = PlanConfig(*(int(cur[f]) for f, _ in PlanConfig._fields_))
+        _check(self._lib.cht_plan_set_config(self._h, ctypes.byref(c)), "cht_plan_set_config")
+
+    def launch(self, stream=None):
+        _check(self._lib.cht_plan_launch(self._h, _stream(stream)), "cht_plan_launch")
+
+    def status(self, stream=None) -> int:
+        bits = ctypes.c_uint32()
+        _check(self._lib.cht_plan_status(self._h, ctypes.byref(bits), _stream(stream)), "cht_plan_status")
+        return int(bits.value)
+
+    def autotune(self, stream=None) -> float:
+        ms = ctypes.c_double()
+        _check(self._lib.cht_plan_autotune(self._h, _stream(stream), ctypes.byref(ms)), "cht_plan_autotune")
+        return float(ms.value)
+
+    def destroy(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _check(self._lib.cht_plan_destroy(self._h), "cht_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 NOALLOC_MAX_KEYS = 65536

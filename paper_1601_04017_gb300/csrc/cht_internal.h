@@ -48,6 +48,47 @@ cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log
 cudaError_t launch_export(const Cell* cells, u32 log2c, u64* keys_out, u64* vals_out, u64 max_n,
                           DevState* st, cudaStream_t s);
 
+// ---- batched engine (cht_engine.cu) ----------------------------------------
+constexpr u32 kChunkOps = 256;  // operations per engine work item
+
+struct EngineTable {
+    Cell* cells;
+    u32 log2c;
+    u32 pad;
+    DevState* st;
+};
+
+struct EngineBatch {
+    const u64* keys;
+    const u64* vals;
+    u64* vals_out;
+    unsigned char* codes;
+    u64 n;
+    u32 table;  // index into the plan's table array
+    u32 mode;   // Mode
+};
+
+struct EngineChunk {
+    u64 start;  // first operation of the batch in this chunk
+    u64 need;   // chunks of the table's earlier batches that must be done first
+    u32 batch;
+    u32 count;
+};
+
+struct EngineArgs {
+    const EngineTable* tables;
+    const EngineBatch* batches;
+    const EngineChunk* chunks;
+    u64 n_chunks;
+    unsigned long long* next;  // work-queue cursor (zero before a launch)
+    unsigned long long* done;  // per table: completed chunks (zero before a launch)
+    u32* status;               // engine status bits (zero before a launch)
+    long long spin_limit;      // bound of one dependency wait, in clock cycles
+    int inject_stall;          // testing: the first chunk waits for a count nothing reaches
+};
+
+cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, cudaStream_t s);
+
 // Kernel launches issued so far (process-wide).
 void count_launch();
 

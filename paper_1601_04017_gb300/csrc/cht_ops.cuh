@@ -76,8 +76,10 @@ __device__ __forceinline__ int modify_at(Cell* cp, bool is_key, u64 key, u64 d) 
 
 // One warp runs the operations [next, end) of the batch with the group
 // refill loop; counters and status bits accumulate into the caller's
-// registers (every lane of the warp must call it).
-template <int G, int V, int MODE>
+// registers (every lane of the warp must call it).  kCoherent: finds read the
+// table through L2 like the modifying modes (required when the same kernel
+// launch also modifies the table); otherwise finds use the read-only path.
+template <int G, int V, int MODE, bool kCoherent = false>
 __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 end, u64& n_ins, u64& n_del,
                                          u32& sbits) {
     constexpr u32 W = G * V;
@@ -174,10 +176,10 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
         if (active) {
             const Cell* p = a.cells + base + u32(gl) * V;
             if (V == 2) {
-                if (kModify) ld_pair_cg(p, k0, v0, k1, v1);
+                if (kModify || kCoherent) ld_pair_cg(p, k0, v0, k1, v1);
                 else ld_pair_nc(p, k0, v0, k1, v1);
             } else {
-                if (kModify) ld_cell_cg(p, k0, v0);
+                if (kModify || kCoherent) ld_cell_cg(p, k0, v0);
                 else ld_cell_nc(p, k0, v0);
             }
             const u32 o0 = u32(gl) * V;

@@ -10,11 +10,13 @@
 // and operations are ordered on the caller's stream, which gives the
 // "synchronized" growing protocol of Sec. 4.3.2: no operation runs while a
 // migration does, so fetch-and-add updates stay legal.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/cht.h"
@@ -664,5 +666,302 @@ const char* cht_status_string(cht_status s) {
 }
 
 int cht_version(void) { return 100; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched engine plans (declared in cht.h).  The host orders the work items
+// round by round -- the r-th batch of every table forms round r -- and gives
+// every item the number of its table's items in earlier rounds, which the
+// engine kernel waits for.
+// ---------------------------------------------------------------------------
+struct cht_plan {
+    int device = 0;
+    std::vector<cht_table*> tables;
+    std::vector<u64> new_cells;  // per table: upper bound of cells its batches can fill
+    cht::EngineTable* d_tables = nullptr;
+    cht::EngineBatch* d_batches = nullptr;
+    cht::EngineChunk* d_chunks = nullptr;
+    unsigned long long* d_counters = nullptr;  // [0] queue cursor, [1 + t] table t's done items
+    u32* d_status = nullptr;
+    u64 n_batches = 0, n_chunks = 0;
+    u64 bytes_tables = 0, bytes_batches = 0, bytes_chunks = 0, bytes_counters = 0;
+    cht_plan_config cfg{0, 0, 0, 0, 0};
+};
+
+namespace {
+
+cht_status upload(void** dst, u64* bytes_out, const void* src, u64 bytes) {
+    *bytes_out = bytes;
+    cht_status r = lib_alloc(dst, bytes, nullptr);
+    if (r != CHT_OK) return r;
+    if (bytes && cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, nullptr) != cudaSuccess) return CHT_ERR_CUDA;
+    return CHT_OK;
+}
+
+void plan_free(cht_plan* p) {
+    lib_free(p->d_tables, p->bytes_tables, nullptr);
+    lib_free(p->d_batches, p->bytes_batches, nullptr);
+    lib_free(p->d_chunks, p->bytes_chunks, nullptr);
+    lib_free(p->d_counters, p->bytes_counters, nullptr);
+    cudaStreamSynchronize(nullptr);
+}
+
+cht::EngineArgs plan_args(const cht_plan* p) {
+    cht::EngineArgs e;
+    e.tables = p->d_tables;
+    e.batches = p->d_batches;
+    e.chunks = p->d_chunks;
+    e.n_chunks = p->n_chunks;
+    e.next = p->d_counters;
+    e.done = p->d_counters + 1;
+    e.status = p->d_status;
+    e.spin_limit = (p->cfg.spin_limit_us > 0 ? (long long)p->cfg.spin_limit_us : 1000000ll) * 2000;  // ~2 GHz
+    e.inject_stall = p->cfg.fault_inject & 1;
+    return e;
+}
+
+cht_status plan_run(cht_plan* p, cudaStream_t s) {
+    if (cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s) != cudaSuccess) return CHT_ERR_CUDA;
+    const int g = p->cfg.group_width > 0 ? p->cfg.group_width : 1;
+    const int v = g == 1 ? 2 : (p->cfg.lane_cells > 0 ? p->cfg.lane_cells : 1);
+    return cuda_status(cht::launch_engine(plan_args(p), g, v, p->cfg.ctas_per_sm, s));
+}
+
+}  // namespace
+
+extern "C" {
+
+cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_handle* out) {
+    if (!out || (n_ops > 0 && !ops)) return CHT_ERR_INVALID_ARG;
+    *out = nullptr;
+    cht_plan* p = new (std::nothrow) cht_plan();
+    if (!p) return CHT_ERR_OOM;
+    std::unordered_map<cht_table*, u32> index;
+    std::vector<cht::EngineBatch> batches;
+    std::vector<u32> round_of;  // per batch
+    std::vector<u32> rounds;    // per table: batches so far
+    batches.reserve(n_ops);
+    round_of.reserve(n_ops);
+    for (u64 i = 0; i < n_ops; ++i) {
+        const cht_batch_op& o = ops[i];
+        const bool has_vals = o.op == CHT_OP_INSERT || o.op == CHT_OP_IOU_ADD || o.op == CHT_OP_IOU_OVERWRITE;
+        bool ok = o.table && o.op >= CHT_OP_FIND && o.op <= CHT_OP_ERASE;
+        if (ok && o.n > 0) {
+            ok = o.keys && !is_host_pointer(o.keys) && (!has_vals || (o.vals && !is_host_pointer(o.vals))) &&
+                 (o.op != CHT_OP_FIND || (o.vals_out && !is_host_pointer(o.vals_out))) &&
+                 (!o.codes || !is_host_pointer(o.codes));
+        }
+        if (ok && !p->tables.empty() && o.table->device != p->device) ok = false;
+        if (!ok) {
+            delete p;
+            return CHT_ERR_INVALID_ARG;
+        }
+        if (o.n == 0) continue;
+        auto it = index.find(o.table);
+        u32 t;
+        if (it == index.end()) {
+            t = u32(p->tables.size());
+            index.emplace(o.table, t);
+            if (p->tables.empty()) p->device = o.table->device;
+            p->tables.push_back(o.table);
+            p->new_cells.push_back(0);
+            rounds.push_back(0);
+        } else {
+            t = it->second;
+        }
+        cht::EngineBatch b;
+        b.keys = reinterpret_cast<const u64*>(o.keys);
+        b.vals = has_vals ? reinterpret_cast<const u64*>(o.vals) : nullptr;
+        b.vals_out = o.op == CHT_OP_FIND ? reinterpret_cast<u64*>(o.vals_out) : nullptr;
+        b.codes = o.codes;
+        b.n = o.n;
+        b.table = t;
+        b.mode = u32(o.op);
+        batches.push_back(b);
+        round_of.push_back(rounds[t]++);
+        if (has_vals) p->new_cells[t] += o.n;
+    }
+    // work items, round by round; need = the table's items in earlier rounds
+    const u32 n_rounds = rounds.empty() ? 0 : *std::max_element(rounds.begin(), rounds.end());
+    std::vector<std::vector<u32>> by_round(n_rounds);
+    for (u32 b = 0; b < batches.size(); ++b) by_round[round_of[b]].push_back(b);
+    std::vector<u64> items_so_far(p->tables.size(), 0);
+    std::vector<cht::EngineChunk> chunks;
+    for (u32 r = 0; r < n_rounds; ++r) {
+        std::vector<u64> need_now(by_round[r].size());
+        for (size_t k = 0; k < by_round[r].size(); ++k) need_now[k] = items_so_far[batches[by_round[r][k]].table];
+        for (size_t k = 0; k < by_round[r].size(); ++k) {
+            const u32 b = by_round[r][k];
+            const cht::EngineBatch& eb = batches[b];
+            for (u64 s0 = 0; s0 < eb.n; s0 += cht::kChunkOps) {
+                cht::EngineChunk ch;
+                ch.start = s0;
+                ch.need = need_now[k];
+                ch.batch = b;
+                ch.count = u32(eb.n - s0 < cht::kChunkOps ? eb.n - s0 : cht::kChunkOps);
+                chunks.push_back(ch);
+                ++items_so_far[eb.table];
+            }
+        }
+    }
+    std::vector<cht::EngineTable> tabs(p->tables.size());
+    for (size_t t = 0; t < p->tables.size(); ++t) {
+        tabs[t].cells = p->tables[t]->cells;
+        tabs[t].log2c = p->tables[t]->log2c;
+        tabs[t].pad = 0;
+        tabs[t].st = p->tables[t]->st;
+    }
+    DeviceGuard g(p->tables.empty() ? current_device() : p->device);
+    p->n_batches = batches.size();
+    p->n_chunks = chunks.size();
+    cht_status r = upload(reinterpret_cast<void**>(&p->d_tables), &p->bytes_tables, tabs.data(),
+                          tabs.size() * sizeof(cht::EngineTable));
+    if (r == CHT_OK)
+        r = upload(reinterpret_cast<void**>(&p->d_batches), &p->bytes_batches, batches.data(),
+                   batches.size() * sizeof(cht::EngineBatch));
+    if (r == CHT_OK)
+        r = upload(reinterpret_cast<void**>(&p->d_chunks), &p->bytes_chunks, chunks.data(),
+                   chunks.size() * sizeof(cht::EngineChunk));
+    if (r == CHT_OK) {
+        // counters and the status word share one allocation
+        p->bytes_counters = (1 + p->tables.size()) * sizeof(unsigned long long) + sizeof(unsigned long long);
+        r = lib_alloc(reinterpret_cast<void**>(&p->d_counters), p->bytes_counters, nullptr);
+        if (r == CHT_OK) p->d_status = reinterpret_cast<u32*>(p->d_counters + 1 + p->tables.size());
+    }
+    if (r == CHT_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) r = CHT_ERR_CUDA;
+    if (r != CHT_OK) {
+        plan_free(p);
+        delete p;
+        return r;
+    }
+    *out = p;
+    return CHT_OK;
+}
+
+cht_status cht_plan_set_config(cht_plan_handle p, const cht_plan_config* cfg) {
+    if (!p) return CHT_ERR_INVALID_ARG;
+    cht_plan_config c = cfg ? *cfg : cht_plan_config{0, 0, 0, 0, 0};
+    const int g = c.group_width;
+    if (!(g == 0 || g == 1 || g == 4 || g == 8 || g == 16 || g == 32)) return CHT_ERR_INVALID_ARG;
+    if (c.lane_cells < 0 || c.lane_cells > 2 || (g == 32 && c.lane_cells == 2)) return CHT_ERR_INVALID_ARG;
+    if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64 || c.spin_limit_us < 0 || c.fault_inject < 0 || c.fault_inject > 1)
+        return CHT_ERR_INVALID_ARG;
+    p->cfg = c;
+    return CHT_OK;
+}
+
+cht_status cht_plan_get_config(cht_plan_handle p, cht_plan_config* cfg) {
+    if (!p || !cfg) return CHT_ERR_INVALID_ARG;
+    *cfg = p->cfg;
+    return CHT_OK;
+}
+
+cht_status cht_plan_launch(cht_plan_handle p, cht_stream_t stream) {
+    if (!p) return CHT_ERR_INVALID_ARG;
+    if (p->n_chunks == 0) return CHT_OK;
+    DeviceGuard g(p->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cht_status r = plan_run(p, s);
+    if (r != CHT_OK) return r;
+    for (size_t t = 0; t < p->tables.size(); ++t) {
+        cht_table* h = p->tables[t];
+        h->i_bound += p->new_cells[t];
+        if (h->i_bound > h->cap()) h->i_bound = h->cap();
+        h->i_exact = false;
+        h->last = s;
+    }
+    return CHT_OK;
+}
+
+cht_status cht_plan_status(cht_plan_handle p, uint32_t* bits, cht_stream_t stream) {
+    if (!p || !bits) return CHT_ERR_INVALID_ARG;
+    *bits = 0;
+    if (p->n_chunks == 0) return CHT_OK;
+    DeviceGuard g(p->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    u32 st = 0;
+    if (cudaMemcpyAsync(&st, p->d_status, sizeof(u32), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CHT_ERR_CUDA;
+    cht_status r = cuda_status(cudaStreamSynchronize(s));
+    *bits = st & CHT_PLAN_TIMEOUT;
+    return r;
+}
+
+cht_status cht_plan_autotune(cht_plan_handle p, cht_stream_t stream, double* best_ms) {
+    if (!p) return CHT_ERR_INVALID_ARG;
+    if (p->n_chunks == 0) return CHT_OK;
+    DeviceGuard g(p->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // one copy of every table (cells + device state) to restore between trials
+    u64 total = 0;
+    for (cht_table* h : p->tables) total += h->cap() * sizeof(Cell) + sizeof(DevState);
+    unsigned char* backup = nullptr;
+    cht_status r = lib_alloc(reinterpret_cast<void**>(&backup), total, s);
+    if (r != CHT_OK) return r;
+    auto copy_tables = [&](bool save) -> cht_status {
+        u64 off = 0;
+        for (cht_table* h : p->tables) {
+            const u64 nb = h->cap() * sizeof(Cell);
+            void* a = backup + off;
+            if (cudaMemcpyAsync(save ? a : h->cells, save ? static_cast<void*>(h->cells) : a, nb,
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return CHT_ERR_CUDA;
+            off += nb;
+            void* b = backup + off;
+            if (cudaMemcpyAsync(save ? b : h->st, save ? static_cast<void*>(h->st) : b, sizeof(DevState),
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return CHT_ERR_CUDA;
+            off += sizeof(DevState);
+        }
+        return CHT_OK;
+    };
+    const cht_plan_config keep = p->cfg;
+    struct Cand {
+        int g, v, ctas;
+    };
+    const Cand cands[] = {{1, 2, 0}, {4, 2, 0}, {8, 2, 0}, {4, 1, 0}, {8, 1, 0}, {16, 1, 0}, {32, 1, 0}, {1, 2, 2}};
+    double best = 1e30;
+    cht_plan_config best_cfg = keep;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = CHT_ERR_CUDA;
+    if (r == CHT_OK) r = copy_tables(true);
+    for (const Cand& c : cands) {
+        if (r != CHT_OK) break;
+        p->cfg.group_width = c.g;
+        p->cfg.lane_cells = c.v;
+        p->cfg.ctas_per_sm = c.ctas;
+        float ms = 0;
+        if (cudaEventRecord(e0, s) != cudaSuccess) r = CHT_ERR_CUDA;
+        if (r == CHT_OK) r = plan_run(p, s);
+        if (r == CHT_OK && cudaEventRecord(e1, s) != cudaSuccess) r = CHT_ERR_CUDA;
+        if (r == CHT_OK && cudaEventSynchronize(e1) != cudaSuccess) r = CHT_ERR_CUDA;
+        if (r == CHT_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = CHT_ERR_CUDA;
+        u32 st = 0;
+        if (r == CHT_OK && cudaMemcpy(&st, p->d_status, sizeof(u32), cudaMemcpyDeviceToHost) != cudaSuccess)
+            r = CHT_ERR_CUDA;
+        if (r == CHT_OK && st == 0 && ms < best) {
+            best = ms;
+            best_cfg = p->cfg;
+        }
+        if (r == CHT_OK) r = copy_tables(false);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    lib_free(backup, total, s);
+    cudaStreamSynchronize(s);
+    p->cfg = best < 1e30 ? best_cfg : keep;
+    p->cfg.spin_limit_us = keep.spin_limit_us;
+    p->cfg.fault_inject = keep.fault_inject;
+    if (best_ms) *best_ms = best < 1e30 ? best : 0.0;
+    return r;
+}
+
+cht_status cht_plan_destroy(cht_plan_handle p) {
+    if (!p) return CHT_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    plan_free(p);
+    delete p;
+    return CHT_OK;
+}
 
 }  // extern "C"

@@ -1,0 +1,142 @@
+"""GPU parity of the batched engine (one persistent launch for many tables).
+
+Every table's batches must give exactly what the single calls give, in
+order: find values and codes bit-exact against the oracle run table by
+table; insertOrUpdate codes set-valued (per distinct key of a batch, the
+number of 1 codes equals the oracle's); final contents of every table
+bit-exact.  Also: the launch inside a captured CUDA graph, the bounded
+dependency wait running out (a count nothing reaches), and the autotuner.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import to_np_u64, to_np_u8
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(cht, wl):
+    import torch
+
+    keys, vals = W.batched_keys(wl, backend="cuda")
+    total = keys.numel()
+    vout = torch.full((total,), -1, dtype=torch.int64, device="cuda")
+    codes = torch.full((total,), 255, dtype=torch.uint8, device="cuda")
+    tables = [cht.Table(int(c)) for c in wl["capacity"]]
+    ops = []
+    for b in range(len(wl["n"])):
+        lo, hi = int(wl["offsets"][b]), int(wl["offsets"][b + 1])
+        op = int(wl["op"][b])
+        t = tables[int(wl["table"][b])]
+        ops.append((t, op, keys[lo:hi], vals[lo:hi] if op != W.OP_FIND else None,
+                    vout[lo:hi] if op == W.OP_FIND else None, codes[lo:hi]))
+    return tables, ops, vout, codes
+
+
+def _oracle(oracle_mod, wl):
+    keys, vals = W.batched_keys(wl)
+    tabs = [oracle_mod.OracleTable(int(c)) for c in wl["capacity"]]
+    vout = np.zeros(keys.size, np.uint64)
+    codes = np.zeros(keys.size, np.uint8)
+    for b in range(len(wl["n"])):
+        lo, hi = int(wl["offsets"][b]), int(wl["offsets"][b + 1])
+        t, op = tabs[int(wl["table"][b])], int(wl["op"][b])
+        if op == W.OP_FIND:
+            vout[lo:hi], codes[lo:hi] = t.find(keys[lo:hi])
+        elif op == W.OP_INSERT:
+            codes[lo:hi] = t.insert(keys[lo:hi], vals[lo:hi])
+        else:
+            codes[lo:hi] = t.insert_or_update(keys[lo:hi], vals[lo:hi], oracle_mod.ADD)
+    return tabs, keys, vout, codes
+
+
+def _check(wl, keys, tables, vout, codes, otabs, ovout, ocodes):
+    g_v, g_c = to_np_u64(vout), to_np_u8(codes)
+    for b in range(len(wl["n"])):
+        lo, hi = int(wl["offsets"][b]), int(wl["offsets"][b + 1])
+        op = int(wl["op"][b])
+        if op == W.OP_FIND:
+            assert np.array_equal(g_c[lo:hi], ocodes[lo:hi]), b
+            assert np.array_equal(g_v[lo:hi], ovout[lo:hi]), b
+        elif op == W.OP_INSERT:
+            assert np.array_equal(g_c[lo:hi], ocodes[lo:hi]), b
+        else:
+            seg = keys[lo:hi]
+            for k in np.unique(seg):
+                m = seg == k
+                assert int(g_c[lo:hi][m].astype(np.int64).sum()) == int(ocodes[lo:hi][m].astype(np.int64).sum()), b
+    for t, o in zip(tables, otabs):
+        gk, gv = t.export()
+        gk, gv = to_np_u64(gk), to_np_u64(gv)
+        ok, ov = o.export()
+        assert gk.size == ok.size
+        i, j = np.argsort(gk), np.argsort(ok)
+        assert np.array_equal(gk[i], ok[j]) and np.array_equal(gv[i], ov[j])
+
+
+@pytest.mark.parametrize("g,v", [(0, 0), (4, 2), (8, 1), (32, 1)])
+def test_engine_matches_oracle(cuda_lib, oracle_mod, g, v):
+    wl = W.batched_workload(48, 6, 11, seed=31)
+    tables, ops, vout, codes = _setup(cuda_lib, wl)
+    plan = cuda_lib.Plan(ops)
+    plan.set_config(group_width=g, lane_cells=v)
+    plan.launch()
+    assert plan.status() == 0
+    otabs, keys, ovout, ocodes = _oracle(oracle_mod, wl)
+    _check(wl, keys, tables, vout, codes, otabs, ovout, ocodes)
+
+
+def test_engine_in_cuda_graph(cuda_lib, oracle_mod):
+    import torch
+
+    wl = W.batched_workload(32, 6, 10, seed=32)
+    # warm the engine kernel's launch path outside the capture
+    warm_tables, warm_ops, _, _ = _setup(cuda_lib, W.batched_workload(4, 6, 7, seed=33))
+    cuda_lib.Plan(warm_ops).launch()
+    torch.cuda.synchronize()
+    tables, ops, vout, codes = _setup(cuda_lib, wl)
+    plan = cuda_lib.Plan(ops)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.launch()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    otabs, keys, ovout, ocodes = _oracle(oracle_mod, wl)
+    _check(wl, keys, tables, vout, codes, otabs, ovout, ocodes)
+
+
+def test_engine_dependency_wait_times_out(cuda_lib):
+    wl = W.batched_workload(8, 6, 9, seed=34)
+    tables, ops, vout, codes = _setup(cuda_lib, wl)
+    plan = cuda_lib.Plan(ops)
+    plan.set_config(fault_inject=1, spin_limit_us=200)
+    plan.launch()
+    assert plan.status() & cuda_lib.PLAN_TIMEOUT
+    plan.set_config(fault_inject=0, spin_limit_us=0)
+
+
+def test_engine_autotune_restores_tables(cuda_lib, oracle_mod):
+    wl = W.batched_workload(24, 6, 10, seed=35)
+    tables, ops, vout, codes = _setup(cuda_lib, wl)
+    plan = cuda_lib.Plan(ops)
+    ms = plan.autotune()
+    assert ms > 0
+    for t in tables:
+        assert t.size()[:2] == (0, 0)  # contents restored after every trial
+    plan.launch()
+    assert plan.status() == 0
+    otabs, keys, ovout, ocodes = _oracle(oracle_mod, wl)
+    _check(wl, keys, tables, vout, codes, otabs, ovout, ocodes)
+
+
+def test_plan_rejects_host_arrays(cuda_lib):
+    import torch
+
+    t = cuda_lib.Table(1024)
+    keys = np.arange(1, 9, dtype=np.uint64)
+    with pytest.raises(cuda_lib.ChtError):
+        cuda_lib.Plan([(t, cuda_lib.OP_INSERT, keys, keys, None, None)])
+    torch.cuda.synchronize()

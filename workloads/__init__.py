@@ -309,3 +309,151 @@ def bounded_workload(log2_capacity: int, loads=(0.5,), n_find: int | None = None
         "hits": hits,
         "misses": misses,
     }
+
+
+# ----------------------------------------------------------------------------
+# many tables with uneven batches (the batched-engine workload)
+# ----------------------------------------------------------------------------
+OP_FIND, OP_INSERT, OP_IOU_ADD = 0, 1, 2
+STREAM_INSERT, STREAM_MISS, STREAM_IOU = 0, 1, 2
+
+
+def _stream_salt(table, stream, seed):
+    """Per (table, stream) seed of an independent SplitMix64 stream (numpy)."""
+    t = np.asarray(table, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        x = t * np.uint64(8) + np.asarray(stream, dtype=np.uint64) + np.uint64(seed) * np.uint64(1 << 40)
+    return _mix13_np(x ^ np.uint64(0x6A09E667F3BCC909))
+
+
+def batched_workload(n_tables: int, log2_min: int, log2_max: int, seed: int = SEED_TABLES,
+                     mix=(0.4, 0.5, 0.1)):
+    """Structure of the many-tables workload (host side, numpy).
+
+    Table t holds n_t elements, n_t log-uniform on [2^log2_min, 2^log2_max];
+    its capacity is the smallest power of two >= 2 n_t (at least 64).  It gets
+    a sequence of batches with sizes log-uniform on [1, n_t / 4] and types
+    insert / find / insertOrUpdate(add) with probabilities `mix`, until its
+    inserts reach n_t.  Inserts take fresh keys of the table's insert stream;
+    each find key is, with probability 1/2, an earlier-inserted key (else a
+    key of the table's miss stream); each insertOrUpdate key is an earlier key
+    or a fresh key of the table's own insertOrUpdate stream, 1/2 each.
+    Batches are listed round by round (round r = every table's r-th batch).
+    """
+    rng = np.random.default_rng(seed)
+    n_t = np.floor(np.exp2(rng.uniform(log2_min, log2_max, n_tables))).astype(np.int64)
+    cap = np.maximum(64, 1 << np.ceil(np.log2(2 * n_t)).astype(np.int64))
+    per_table = []
+    for t in range(n_tables):
+        nt = int(n_t[t])
+        hi = max(1.0, nt / 4.0)
+        ins = miss = iou = 0
+        rows = []
+        while ins < nt:
+            size = int(np.floor(np.exp(rng.uniform(0.0, np.log(hi + 1.0)))))
+            size = max(1, min(size, int(hi)))
+            r = rng.random()
+            op = OP_INSERT if r < mix[0] else (OP_FIND if r < mix[0] + mix[1] else OP_IOU_ADD)
+            if op == OP_INSERT:
+                size = min(size, nt - ins)
+            rows.append((t, op, size, ins, miss, iou))
+            if op == OP_INSERT:
+                ins += size
+            elif op == OP_FIND:
+                miss += size
+            else:
+                iou += size
+        per_table.append(rows)
+    n_rounds = max(len(r) for r in per_table)
+    rows = [per_table[t][k] for k in range(n_rounds) for t in range(n_tables) if k < len(per_table[t])]
+    arr = np.array(rows, dtype=np.int64).reshape(-1, 6)
+    sizes = arr[:, 2]
+    offsets = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=offsets[1:])
+    return {
+        "n_tables": n_tables, "n_t": n_t, "capacity": cap, "seed": seed,
+        "table": arr[:, 0], "op": arr[:, 1], "n": sizes, "ins_before": arr[:, 3],
+        "miss_base": arr[:, 4], "iou_base": arr[:, 5], "offsets": offsets, "rounds": n_rounds,
+    }
+
+
+def batched_keys(wl, first: int = 0, last: int | None = None, backend="numpy"):
+    """Keys and values of batches [first, last) as flat arrays (batch b's
+    operations at offsets[b] - offsets[first] ...).  Values: key * 3 for
+    inserts, 1 for insertOrUpdate(add), 0 for finds.  The torch backend
+    computes the same bits on the device."""
+    last = len(wl["n"]) if last is None else last
+    if backend != "numpy":
+        return _batched_keys_t(wl, first, last, backend)
+    sizes = wl["n"][first:last]
+    total = int(sizes.sum())
+    bid = np.repeat(np.arange(first, last, dtype=np.int64), sizes)
+    k = np.arange(total, dtype=np.int64) - (wl["offsets"][bid] - wl["offsets"][first])
+    table, op = wl["table"][bid], wl["op"][bid]
+    ins_before = wl["ins_before"][bid]
+    # per-element coin and pick from a counter-based hash of (batch, k)
+    h = _mix13_np((bid.astype(np.uint64) << np.uint64(24)) ^ k.astype(np.uint64) ^ np.uint64(wl["seed"] << 56))
+    coin = (h & np.uint64(1)) == 1
+    pick = (h >> np.uint64(1)) % np.maximum(ins_before, 1).astype(np.uint64)
+    stream = np.full(total, STREAM_INSERT, dtype=np.int64)
+    j = np.zeros(total, dtype=np.int64)
+    is_ins = op == OP_INSERT
+    j[is_ins] = ins_before[is_ins] + k[is_ins]
+    earlier = (~is_ins) & coin & (ins_before > 0)
+    j[earlier] = pick[earlier].astype(np.int64)
+    fresh_find = (op == OP_FIND) & ~earlier
+    stream[fresh_find] = STREAM_MISS
+    j[fresh_find] = wl["miss_base"][bid][fresh_find] + k[fresh_find]
+    fresh_iou = (op == OP_IOU_ADD) & ~earlier
+    stream[fresh_iou] = STREAM_IOU
+    j[fresh_iou] = wl["iou_base"][bid][fresh_iou] + k[fresh_iou]
+    salt = _stream_salt(table, stream, wl["seed"])
+    with np.errstate(over="ignore"):
+        keys = _mix13_np(salt + (j.astype(np.uint64) + np.uint64(1)) * np.uint64(GOLDEN_GAMMA))
+    _check_reserved(keys, "numpy")
+    vals = np.zeros(total, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        vals[is_ins] = keys[is_ins] * np.uint64(3)
+    vals[op == OP_IOU_ADD] = 1
+    return keys, vals
+
+
+def _batched_keys_t(wl, first, last, device):
+    torch = _torch()
+
+    def col(name):
+        return torch.from_numpy(np.ascontiguousarray(wl[name][first:last])).to(device)
+
+    sizes = col("n")
+    total = int(wl["offsets"][last] - wl["offsets"][first])
+    bidl = torch.repeat_interleave(torch.arange(first, last, dtype=torch.int64, device=device), sizes)
+    off = torch.from_numpy(np.ascontiguousarray(wl["offsets"][first:last] - wl["offsets"][first])).to(device)
+    off = torch.repeat_interleave(off, sizes)
+    k = torch.arange(total, dtype=torch.int64, device=device) - off
+    del off
+
+    def per(name):
+        return torch.repeat_interleave(col(name), sizes)
+
+    table, op, ins_before = per("table"), per("op"), per("ins_before")
+    h = _mix13_t((bidl << 24) ^ k ^ _s64(wl["seed"] << 56))
+    del bidl
+    coin = (h & 1) == 1
+    pick = _lsr_t(h, 1) % torch.clamp(ins_before, min=1)
+    stream = torch.full_like(k, STREAM_INSERT)
+    is_ins = op == OP_INSERT
+    j = torch.where(is_ins, ins_before + k, torch.zeros_like(k))
+    earlier = (~is_ins) & coin & (ins_before > 0)
+    j = torch.where(earlier, pick, j)
+    fresh_find = (op == OP_FIND) & ~earlier
+    stream = torch.where(fresh_find, torch.full_like(k, STREAM_MISS), stream)
+    j = torch.where(fresh_find, per("miss_base") + k, j)
+    fresh_iou = (op == OP_IOU_ADD) & ~earlier
+    stream = torch.where(fresh_iou, torch.full_like(k, STREAM_IOU), stream)
+    j = torch.where(fresh_iou, per("iou_base") + k, j)
+    salt = _mix13_t((table * 8 + stream + _s64(wl["seed"] << 40)) ^ _s64(0x6A09E667F3BCC909))
+    keys = _mix13_t(salt + (j + 1) * _s64(GOLDEN_GAMMA))
+    _check_reserved(keys, "torch")
+    vals = torch.where(is_ins, keys * 3, torch.zeros_like(keys))
+    vals = torch.where(op == OP_IOU_ADD, torch.ones_like(keys), vals)
+    return keys, vals
