@@ -307,6 +307,12 @@ def max_over_ranks(pg, x: float, device=None) -> float:
     return float(t.item())
 
 
+def aggregate_mops(ops_per_step: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput of N replicas: all ranks' operations over the
+    slowest rank's time (weak scaling: every rank runs the full step)."""
+    return ops_per_step * steps * world / (ms_max * 1e-3) / 1e6
+
+
 def latency_percentiles(cht, inp, reps: int):
     """p50/p99 of single calls at the small (2^20-cell) workload, 2^19 ops each."""
     import torch
@@ -373,8 +379,7 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(pg, ms, device="cuda")
     ms_step = ms_max / args.steps
-    ops = runner.ops_per_step * args.steps * world
-    value = ops / (ms_max * 1e-3) / 1e6
+    value = aggregate_mops(runner.ops_per_step, args.steps, world, ms_max)
 
     # per-call breakdown and the dominant kernel's roofline
     counts = op_counts(inp)
