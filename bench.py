@@ -818,6 +818,80 @@ def verify_batched_sample(wl, tables, keys, vout, codes, n_sample):
     return checked
 
 
+# ----------------------------------------------------------------------------
+# serving: Poisson requests over resident growing tables
+# ----------------------------------------------------------------------------
+def run_serving(args):
+    """256 growable tables (start 1024 cells; key universes log-uniform
+    2^10..2^24), requests of 1..65536 ops (log-uniform), table ~ Zipf(1.0),
+    find / insert / insertOrUpdate(add) / erase 50/30/15/5, request arrays in
+    pinned host memory, device memory cap 64 GiB.  First the capacity (all
+    requests at time 0), then Poisson arrivals at 0.5 / 0.7 / 0.9 of it:
+    p50 / p99 request latency (arrival to completion) and throughput."""
+    import torch
+
+    import paper_1601_04017_gb300 as cht
+
+    cht.load_library()
+    nreq = args.serving_requests
+    wl = W.serving_workload(nreq, n_tables=256, log2_min=10, log2_max=24, size_log2_max=16, table_s=1.0)
+    total = int(wl["offsets"][-1])
+    keys_h = torch.empty(total, dtype=torch.int64).pin_memory()
+    vals_h = torch.empty(total, dtype=torch.int64).pin_memory()
+    vout_h = torch.zeros(total, dtype=torch.int64).pin_memory()
+    codes_h = torch.zeros(total, dtype=torch.uint8).pin_memory()
+    r0 = 0
+    while r0 < nreq:
+        r1 = int(np.searchsorted(wl["offsets"], wl["offsets"][r0] + (1 << 27), side="right")) - 1
+        r1 = min(max(r1, r0 + 1), nreq)
+        k, v = W.serving_keys(wl, r0, r1, backend="cuda")
+        keys_h[wl["offsets"][r0]:wl["offsets"][r1]].copy_(k)
+        vals_h[wl["offsets"][r0]:wl["offsets"][r1]].copy_(v)
+        del k, v
+        r0 = r1
+    torch.cuda.synchronize()
+    kp, vp, op_, cp = keys_h.data_ptr(), vals_h.data_ptr(), vout_h.data_ptr(), codes_h.data_ptr()
+    reqs = []
+    for r in range(nreq):
+        o, n, op = int(wl["offsets"][r]), int(wl["n"][r]), int(wl["op"][r])
+        reqs.append(cht.cht.Request(int(wl["table"][r]), op, kp + 8 * o,
+                                    vp + 8 * o if op in (W.OP_INSERT, W.OP_IOU_ADD) else None, n,
+                                    op_ + 8 * o if op == W.OP_FIND else None, cp + o))
+
+    def run(arrivals):
+        tables = [cht.Table(1024, growable=True) for _ in range(256)]
+        srv = cht.Server(tables, memory_cap_bytes=64 << 30, arena_bytes=1 << 30, max_inflight_steps=2)
+        lat, mk = srv.replay(reqs, arrivals)
+        steps, done = srv.stats()
+        grown = sum(t.size()[2] for t in tables) * 16
+        srv.destroy()
+        for t in tables:
+            t.destroy()
+        torch.cuda.synchronize()
+        return lat, mk, steps, done, grown
+
+    lat0, mk0, steps0, done0, grown = run(np.zeros(nreq))
+    assert done0 == nreq
+    cap_rps = nreq / mk0
+    out = {"workload": "serving: 256 growable tables (key universes log-uniform 2^10..2^24), requests of 1..65536 "
+                       "ops (log-uniform), table ~ Zipf(1.0), find/insert/insertOrUpdate(add)/erase 50/30/15/5, "
+                       "request arrays in pinned host memory, memory cap 64 GiB",
+           "requests": nreq, "ops": total, "final_table_bytes": grown,
+           "capacity": {"makespan_s": round(mk0, 4), "requests_per_s": round(cap_rps, 1),
+                        "mops": round(total / mk0 / 1e6, 1), "steps": steps0,
+                        "p50_ms": round(float(np.percentile(lat0, 50)) * 1e3, 3),
+                        "p99_ms": round(float(np.percentile(lat0, 99)) * 1e3, 3)}}
+    for frac in args.serving_loads:
+        arr = W.poisson_arrivals(nreq, frac * cap_rps)
+        lat, mk, steps, done, _ = run(arr)
+        out[f"load_{frac}"] = {"offered_requests_per_s": round(frac * cap_rps, 1), "makespan_s": round(mk, 4),
+                               "mops": round(total / mk / 1e6, 1), "steps": steps,
+                               "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                               "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                               "max_ms": round(float(lat.max()) * 1e3, 3)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -835,7 +909,7 @@ def main():
     ap.add_argument("--case-s", type=float, default=1.0)
     ap.add_argument("--probe-random-access", action="store_true",
                     help="measure the HBM random-read ceiling instead of the benchmark")
-    ap.add_argument("--workload", default="bounded", choices=["bounded", "batched"],
+    ap.add_argument("--workload", default="bounded", choices=["bounded", "batched", "serving"],
                     help="bounded: the 2^28-cell table step (the bench line); batched: many tables, "
                          "one engine launch vs one launch per batch")
     ap.add_argument("--batched-tables", type=int, default=4096)
@@ -843,9 +917,14 @@ def main():
     ap.add_argument("--batched-log2-max", type=int, default=20)
     ap.add_argument("--batched-verify", type=int, default=16)
     ap.add_argument("--no-graph-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=100_000)
+    ap.add_argument("--serving-loads", type=float, nargs="*", default=[0.5, 0.7, 0.9])
     args = ap.parse_args()
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
     if args.case:
         run_case(args)

@@ -252,6 +252,75 @@ cht_status cht_plan_status(cht_plan_handle p, uint32_t *bits, cht_stream_t strea
 cht_status cht_plan_autotune(cht_plan_handle p, cht_stream_t stream, double *best_ms);
 cht_status cht_plan_destroy(cht_plan_handle p);
 
+/* ---- Serving loop: continuous batching over resident tables ----------------
+ * A server owns a queue of requests over a fixed set of tables (each request:
+ * one operation type on one table, host or device arrays).  Every scheduling
+ * step admits queued requests as device memory in its request arena frees up,
+ * copies their inputs in, runs all of them in ONE engine launch (requests on
+ * the same table in arrival order, phase semantics as for single calls; other
+ * tables overlap), copies the results back and records when each request
+ * completes.  The next step is prepared and launched while the previous one
+ * still runs (up to max_inflight_steps), so requests that arrive meanwhile
+ * join the next step: continuous batching.  Growable tables keep their growth
+ * policy: a step admits at most a table's remaining room (alpha * c minus its
+ * non-empty cells, known exactly from counters snapshotted after each step)
+ * of insert / insert-or-update operations; a larger request is admitted in
+ * parts over several steps while later requests on that table wait; a table
+ * with no room and nothing in flight is migrated first.  Admission also keeps
+ * the tables plus the arena within memory_cap_bytes. */
+typedef struct cht_server *cht_server_handle;
+
+typedef struct {
+    uint64_t memory_cap_bytes;   /* tables + request arena (0 = no cap) */
+    uint64_t arena_bytes;        /* device ring for staged request data (0 = 1 GiB) */
+    uint32_t max_inflight_steps; /* 0 = 2 */
+    uint32_t max_step_requests;  /* 0 = 8192 */
+    uint64_t max_step_ops;       /* 0 = 2^26 */
+    int stage_inputs;            /* 0: the engine reads and writes request arrays the
+                                    GPU can address (device memory, pinned host memory,
+                                    pageable host memory where the device reports
+                                    pageable-memory access -- NVLink-C2C on Grace) in
+                                    place and stages only the others through the
+                                    arena; 1: stage every request through the arena */
+} cht_server_config;
+
+typedef struct {
+    uint32_t table;          /* index into the server's table list */
+    int op;                  /* cht_op_kind */
+    const uint64_t *keys;
+    const uint64_t *vals;    /* insert / insert-or-update */
+    uint64_t n;              /* 0 < n */
+    uint64_t *vals_out;      /* find */
+    uint8_t *codes;          /* nullable */
+} cht_request;
+
+/* tables: n_tables handles on one device; the server does not own them. */
+cht_status cht_server_create(const cht_handle *tables, uint32_t n_tables, const cht_server_config *cfg,
+                             cht_stream_t stream, cht_server_handle *out);
+/* Queue a request; its arrival time is now.  *id (nullable) receives its id
+ * (0, 1, 2, ... in submission order).  The arrays must stay valid until the
+ * request completes. */
+cht_status cht_server_submit(cht_server_handle s, const cht_request *req, uint64_t *id);
+/* One scheduling iteration without blocking: note completed steps, admit
+ * queued requests and launch a step if there is room.  Counts are nullable. */
+cht_status cht_server_step(cht_server_handle s, uint32_t *admitted, uint32_t *completed);
+/* Run scheduling iterations until every submitted request has completed. */
+cht_status cht_server_drain(cht_server_handle s);
+/* State of request id: *done = 1 when completed (its outputs are in place),
+ * *latency_s = completion - arrival, *req_status = CHT_OK or the reason it
+ * was rejected (a request larger than the arena: CHT_ERR_OOM). */
+cht_status cht_server_result(cht_server_handle s, uint64_t id, int *done, double *latency_s,
+                             cht_status *req_status);
+/* Replay: submit request i when arrival_s[i] seconds have passed since the
+ * call started (arrival_s non-decreasing), schedule continuously until all
+ * have completed; latency_s[i] (nullable) = completion - scheduled arrival;
+ * *makespan_s (nullable) = last completion - start. */
+cht_status cht_server_replay(cht_server_handle s, const cht_request *reqs, const double *arrival_s,
+                             uint64_t n, double *latency_s, double *makespan_s);
+/* Steps launched so far and requests completed so far. */
+cht_status cht_server_stats(cht_server_handle s, uint64_t *steps, uint64_t *completed);
+cht_status cht_server_destroy(cht_server_handle s);
+
 /* Cap, in bytes, on the device memory this library allocates at any time for
  * tables and staging (0 = no cap).  An allocation that would exceed it fails
  * with CHT_ERR_OOM exactly like a failed cudaMalloc. */

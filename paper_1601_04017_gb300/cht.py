@@ -58,6 +58,18 @@ class BatchOp(ctypes.Structure):
                 ("codes", ctypes.c_void_p)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_cap_bytes", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64),
+                ("max_inflight_steps", ctypes.c_uint32), ("max_step_requests", ctypes.c_uint32),
+                ("max_step_ops", ctypes.c_uint64), ("stage_inputs", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("table", ctypes.c_uint32), ("op", ctypes.c_int), ("keys", ctypes.c_void_p),
+                ("vals", ctypes.c_void_p), ("n", ctypes.c_uint64), ("vals_out", ctypes.c_void_p),
+                ("codes", ctypes.c_void_p)]
+
+
 class PlanConfig(ctypes.Structure):
     _fields_ = [("group_width", ctypes.c_int), ("lane_cells", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("spin_limit_us", ctypes.c_int), ("fault_inject", ctypes.c_int)]
@@ -105,6 +117,15 @@ def load_library(build: bool = True):
             "cht_plan_status": (i32, [p, ctypes.POINTER(ctypes.c_uint32), p]),
             "cht_plan_autotune": (i32, [p, p, ctypes.POINTER(ctypes.c_double)]),
             "cht_plan_destroy": (i32, [p]),
+            "cht_server_create": (i32, [p, ctypes.c_uint32, ctypes.POINTER(ServerConfig), p, ctypes.POINTER(p)]),
+            "cht_server_submit": (i32, [p, ctypes.POINTER(Request), ctypes.POINTER(u64)]),
+            "cht_server_step": (i32, [p, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
+            "cht_server_drain": (i32, [p]),
+            "cht_server_result": (i32, [p, u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int)]),
+            "cht_server_replay": (i32, [p, p, p, u64, p, ctypes.POINTER(ctypes.c_double)]),
+            "cht_server_stats": (i32, [p, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+            "cht_server_destroy": (i32, [p]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -338,6 +359,84 @@ class Plan:
     def destroy(self):
         if getattr(self, "_h", None) and self._h.value:
             _check(self._lib.cht_plan_destroy(self._h), "cht_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Server:
+    """cht_server_*: continuous batching of requests over resident tables.
+
+    Requests are (table index, op, keys, vals, vals_out, codes) with host or
+    device arrays that stay alive until the request completes.
+    """
+
+    def __init__(self, tables, memory_cap_bytes=0, arena_bytes=0, max_inflight_steps=0, max_step_requests=0,
+                 max_step_ops=0, stage_inputs=0, stream=None):
+        self._lib = load_library()
+        arr = (ctypes.c_void_p * len(tables))(*[t._h.value for t in tables])
+        cfg = ServerConfig(int(memory_cap_bytes), int(arena_bytes), int(max_inflight_steps),
+                           int(max_step_requests), int(max_step_ops), int(stage_inputs))
+        h = ctypes.c_void_p()
+        _check(self._lib.cht_server_create(arr, len(tables), ctypes.byref(cfg), _stream(stream), ctypes.byref(h)),
+               "cht_server_create")
+        self._h = h
+        self._tables = tables
+        self._keep = []
+
+    @staticmethod
+    def request(table, op, keys, vals=None, vals_out=None, codes=None) -> Request:
+        kp, n, _ = _ptr(keys, 8, what="keys")
+        vp, _, _ = _ptr(vals, 8, n, "vals")
+        op_, _, _ = _ptr(vals_out, 8, n, "vals_out")
+        cp, _, _ = _ptr(codes, 1, n, "codes")
+        return Request(int(table), int(op), kp, vp, n, op_, cp)
+
+    def submit(self, table, op, keys, vals=None, vals_out=None, codes=None) -> int:
+        r = self.request(table, op, keys, vals, vals_out, codes)
+        self._keep.append((keys, vals, vals_out, codes))
+        rid = ctypes.c_uint64()
+        _check(self._lib.cht_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)), "cht_server_submit")
+        return int(rid.value)
+
+    def step(self):
+        a, c = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(self._lib.cht_server_step(self._h, ctypes.byref(a), ctypes.byref(c)), "cht_server_step")
+        return int(a.value), int(c.value)
+
+    def drain(self):
+        _check(self._lib.cht_server_drain(self._h), "cht_server_drain")
+
+    def result(self, rid):
+        done, lat, st = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        _check(self._lib.cht_server_result(self._h, int(rid), ctypes.byref(done), ctypes.byref(lat),
+                                           ctypes.byref(st)), "cht_server_result")
+        return bool(done.value), float(lat.value), int(st.value)
+
+    def replay(self, requests, arrival_s):
+        """Submit requests[i] at arrival_s[i] (seconds from now); returns
+        (latencies, makespan)."""
+        n = len(requests)
+        arr = (Request * max(n, 1))(*requests)
+        arrivals = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.zeros(max(n, 1), dtype=np.float64)
+        mk = ctypes.c_double()
+        _check(self._lib.cht_server_replay(self._h, arr, arrivals.ctypes.data, n, lat.ctypes.data, ctypes.byref(mk)),
+               "cht_server_replay")
+        return lat[:n], float(mk.value)
+
+    def stats(self):
+        st, done = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._lib.cht_server_stats(self._h, ctypes.byref(st), ctypes.byref(done)), "cht_server_stats")
+        return int(st.value), int(done.value)
+
+    def destroy(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _check(self._lib.cht_server_destroy(self._h), "cht_server_destroy")
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -89,6 +89,37 @@ struct EngineArgs {
 
 cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, cudaStream_t s);
 
+}  // namespace cht
+
+#include <vector>
+
+#include "../../include/cht.h"
+
+namespace cht {
+
+// Order batches into engine work items round by round (round r = every
+// table's r-th batch); `need` of an item = its table's items in earlier rounds.
+void plan_order(const std::vector<EngineBatch>& batches, size_t n_tables, std::vector<EngineChunk>& chunks);
+
+// Runtime services for translation units outside the runtime.
+struct TableInfo {
+    Cell* cells;
+    u32 log2c;
+    DevState* st;
+    int device;
+    int growable;
+    double alpha;
+    u64 bound;  // upper bound on the number of non-empty cells
+};
+TableInfo table_info(const cht_table* h);
+void table_set_bound(cht_table* h, u64 bound, bool exact);
+// Synchronize s and read the table's exact counters (also refreshes its bound).
+cht_status table_read_counts(cht_table* h, u64* I, u64* D, cudaStream_t s);
+// Migrate into 2^new_log2 cells; live = exact live count (or ~0 if unknown).
+cht_status table_migrate_to(cht_table* h, u32 new_log2, u64 live, cudaStream_t s);
+cht_status runtime_alloc(void** p, u64 bytes, cudaStream_t s);
+void runtime_free(void* p, u64 bytes, cudaStream_t s);
+
 // Kernel launches issued so far (process-wide).
 void count_launch();
 

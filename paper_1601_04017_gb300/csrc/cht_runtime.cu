@@ -401,6 +401,68 @@ int sm_count() {
     return v;
 }
 
+void plan_order(const std::vector<EngineBatch>& batches, size_t n_tables, std::vector<EngineChunk>& chunks) {
+    std::vector<u32> rounds(n_tables, 0), round_of(batches.size());
+    for (size_t b = 0; b < batches.size(); ++b) round_of[b] = rounds[batches[b].table]++;
+    const u32 n_rounds = n_tables ? *std::max_element(rounds.begin(), rounds.end()) : 0;
+    std::vector<std::vector<u32>> by_round(n_rounds);
+    for (u32 b = 0; b < batches.size(); ++b) by_round[round_of[b]].push_back(b);
+    std::vector<u64> items_so_far(n_tables, 0);
+    chunks.clear();
+    for (u32 r = 0; r < n_rounds; ++r) {
+        std::vector<u64> need_now(by_round[r].size());
+        for (size_t k = 0; k < by_round[r].size(); ++k) need_now[k] = items_so_far[batches[by_round[r][k]].table];
+        for (size_t k = 0; k < by_round[r].size(); ++k) {
+            const u32 b = by_round[r][k];
+            const EngineBatch& eb = batches[b];
+            for (u64 s0 = 0; s0 < eb.n; s0 += kChunkOps) {
+                EngineChunk ch;
+                ch.start = s0;
+                ch.need = need_now[k];
+                ch.batch = b;
+                ch.count = u32(eb.n - s0 < kChunkOps ? eb.n - s0 : kChunkOps);
+                chunks.push_back(ch);
+                ++items_so_far[eb.table];
+            }
+        }
+    }
+}
+
+TableInfo table_info(const cht_table* h) {
+    TableInfo i;
+    i.cells = h->cells;
+    i.log2c = h->log2c;
+    i.st = h->st;
+    i.device = h->device;
+    i.growable = h->growable;
+    i.alpha = h->cfg.alpha;
+    i.bound = h->i_bound;
+    return i;
+}
+
+void table_set_bound(cht_table* h, u64 bound, bool exact) {
+    h->i_bound = bound;
+    h->i_exact = exact;
+}
+
+cht_status table_read_counts(cht_table* h, u64* I, u64* D, cudaStream_t s) {
+    DevState ds;
+    cht_status r = read_state(h, &ds, s);
+    if (r != CHT_OK) return r;
+    *I = ds.I;
+    *D = ds.D;
+    h->i_bound = ds.I;
+    h->i_exact = true;
+    return CHT_OK;
+}
+
+cht_status table_migrate_to(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
+    return do_migrate(h, new_log2, live, s);
+}
+
+cht_status runtime_alloc(void** p, u64 bytes, cudaStream_t s) { return lib_alloc(p, bytes, s); }
+void runtime_free(void* p, u64 bytes, cudaStream_t s) { lib_free(p, bytes, s); }
+
 void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int* device, int* group_width,
                 int* lane_cells, int* ctas_per_sm) {
     *cells = h->cells;
@@ -739,10 +801,7 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
     if (!p) return CHT_ERR_OOM;
     std::unordered_map<cht_table*, u32> index;
     std::vector<cht::EngineBatch> batches;
-    std::vector<u32> round_of;  // per batch
-    std::vector<u32> rounds;    // per table: batches so far
     batches.reserve(n_ops);
-    round_of.reserve(n_ops);
     for (u64 i = 0; i < n_ops; ++i) {
         const cht_batch_op& o = ops[i];
         const bool has_vals = o.op == CHT_OP_INSERT || o.op == CHT_OP_IOU_ADD || o.op == CHT_OP_IOU_OVERWRITE;
@@ -766,7 +825,6 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
             if (p->tables.empty()) p->device = o.table->device;
             p->tables.push_back(o.table);
             p->new_cells.push_back(0);
-            rounds.push_back(0);
         } else {
             t = it->second;
         }
@@ -779,32 +837,11 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
         b.table = t;
         b.mode = u32(o.op);
         batches.push_back(b);
-        round_of.push_back(rounds[t]++);
         if (has_vals) p->new_cells[t] += o.n;
     }
     // work items, round by round; need = the table's items in earlier rounds
-    const u32 n_rounds = rounds.empty() ? 0 : *std::max_element(rounds.begin(), rounds.end());
-    std::vector<std::vector<u32>> by_round(n_rounds);
-    for (u32 b = 0; b < batches.size(); ++b) by_round[round_of[b]].push_back(b);
-    std::vector<u64> items_so_far(p->tables.size(), 0);
     std::vector<cht::EngineChunk> chunks;
-    for (u32 r = 0; r < n_rounds; ++r) {
-        std::vector<u64> need_now(by_round[r].size());
-        for (size_t k = 0; k < by_round[r].size(); ++k) need_now[k] = items_so_far[batches[by_round[r][k]].table];
-        for (size_t k = 0; k < by_round[r].size(); ++k) {
-            const u32 b = by_round[r][k];
-            const cht::EngineBatch& eb = batches[b];
-            for (u64 s0 = 0; s0 < eb.n; s0 += cht::kChunkOps) {
-                cht::EngineChunk ch;
-                ch.start = s0;
-                ch.need = need_now[k];
-                ch.batch = b;
-                ch.count = u32(eb.n - s0 < cht::kChunkOps ? eb.n - s0 : cht::kChunkOps);
-                chunks.push_back(ch);
-                ++items_so_far[eb.table];
-            }
-        }
-    }
+    cht::plan_order(batches, p->tables.size(), chunks);
     std::vector<cht::EngineTable> tabs(p->tables.size());
     for (size_t t = 0; t < p->tables.size(); ++t) {
         tabs[t].cells = p->tables[t]->cells;

@@ -1,0 +1,571 @@
+// Serving loop of libcht (declared in include/cht.h): continuous batching of
+// requests over resident tables, built on the batched engine.
+//
+// Scheduling step: note completed steps (event queries; no blocking), then
+// admit queued requests in arrival order -- skipping a table whose earlier
+// request is not fully admitted, so every table sees its requests in arrival
+// order -- while the step's limits and the request arena allow; run all
+// admitted requests in one engine launch, snapshot the touched tables'
+// counters and record an event.  Request arrays the GPU can address (device
+// memory, pinned host memory, pageable host memory on systems such as Grace
+// with NVLink-C2C) are read and written by the kernel in place -- no copy
+// calls per request; the others are staged through a device ring (the
+// arena): inputs copied in before the launch, results copied back after it.
+// Up to max_inflight_steps steps are in flight; the host prepares the next
+// step while the device runs the current one.
+//
+// Growth (growable tables, Sec. 4.3.2 trigger): the host knows each table's
+// non-empty cells exactly as of its last completed step (the snapshots) plus
+// an upper bound of what its in-flight steps add.  A step admits at most the
+// remaining room floor(alpha*c) - bound of insert / insert-or-update
+// operations; a larger request is admitted in parts.  A table with no room
+// and nothing in flight is migrated before the step: doubled if more than
+// alpha*c/2 elements are live, else rebuilt at the same size to drop
+// tombstones (Sec. 4.4) -- the same policy as single calls.
+#include <chrono>
+#include <cmath>
+#include <deque>
+#include <list>
+#include <new>
+#include <vector>
+
+#include "cht_internal.h"
+
+using cht::u32;
+using cht::u64;
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// FIFO ring allocator over [0, cap) with monotone logical offsets; an
+// allocation never wraps (it skips the ring's tail end instead).
+struct Ring {
+    u64 cap = 0, head = 0, tail = 0;
+    bool alloc(u64 bytes, u64* off) {
+        bytes = (bytes + 255) & ~255ull;
+        if (bytes == 0 || bytes > cap) return false;
+        u64 h = head;
+        if ((h % cap) + bytes > cap) h += cap - (h % cap);
+        if (h + bytes - tail > cap) return false;
+        *off = h % cap;
+        head = h + bytes;
+        return true;
+    }
+    // bytes a new allocation could get right now without wrapping
+    u64 contiguous_free() const {
+        const u64 used = head - tail;
+        const u64 to_end = cap - (head % cap);
+        const u64 free_total = cap - used;
+        if (to_end >= free_total) return free_total;
+        // skipping to the start wastes to_end bytes
+        return to_end > free_total - to_end ? to_end : free_total - to_end;
+    }
+};
+
+struct Part {
+    u64 req;
+    u64 off;  // first operation of the request in this part
+    u64 n;
+    bool direct;  // arrays addressed in place (no staging copies)
+    u64* d_keys;
+    u64* d_vals;
+    u64* d_vout;
+    unsigned char* d_codes;
+};
+
+struct Step {
+    std::vector<Part> parts;
+    cudaEvent_t ev = nullptr;
+    u64 arena_end = 0, meta_end = 0, dmeta_end = 0;
+    std::vector<u32> touched;
+    std::vector<u64> new_cells;          // per touched table
+    unsigned long long* snap = nullptr;  // pinned: (I, D) per touched table
+};
+
+struct Req {
+    cht_request r;
+    bool direct = false;  // the engine addresses the request's arrays in place
+    double t_arrival = 0, t_done = 0;
+    u64 admitted = 0;
+    u32 parts_inflight = 0;
+    int state = 0;  // 0 queued, 1 fully admitted, 2 done, 3 rejected
+    cht_status status = CHT_OK;
+};
+
+bool has_vals(int op) { return op == CHT_OP_INSERT || op == CHT_OP_IOU_ADD || op == CHT_OP_IOU_OVERWRITE; }
+
+u64 per_op_bytes(const cht_request& r) {
+    return 8 + (has_vals(r.op) ? 8 : 0) + (r.op == CHT_OP_FIND ? 8 : 0) + (r.codes ? 1 : 0);
+}
+
+}  // namespace
+
+struct cht_server {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<cht_table*> tables;
+    cht_server_config cfg{};
+    unsigned char* arena = nullptr;  // device: request data
+    Ring aring;
+    unsigned char* meta = nullptr;  // pinned host: step metadata before upload
+    Ring mring;
+    unsigned char* dmeta = nullptr;  // device: step metadata
+    Ring dring;
+    u64 meta_bytes = 0;
+    std::vector<Req> reqs;
+    std::list<u64> queue;
+    std::deque<Step> inflight;
+    std::vector<u64> known_I, known_D, pending_new;
+    std::vector<u32> parts_inflight;
+    std::vector<cudaEvent_t> spare_events;
+    u64 steps = 0, completed = 0;
+    bool pageable_ok = false;  // device can address pageable host memory
+};
+
+namespace {
+
+u64 tables_bytes(const cht_server* s) {
+    u64 b = 0;
+    for (cht_table* h : s->tables) b += (1ull << cht::table_info(h).log2c) * sizeof(cht::Cell);
+    return b;
+}
+
+cht_status poll(cht_server* s, u32* completed_now) {
+    u32 done = 0;
+    while (!s->inflight.empty()) {
+        Step& st = s->inflight.front();
+        const cudaError_t q = cudaEventQuery(st.ev);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) {
+            cudaGetLastError();
+            return CHT_ERR_CUDA;
+        }
+        const double t = now_s();
+        for (const Part& p : st.parts) {
+            Req& rq = s->reqs[p.req];
+            --rq.parts_inflight;
+            --s->parts_inflight[rq.r.table];
+            if (rq.state == 1 && rq.parts_inflight == 0) {
+                rq.state = 2;
+                rq.t_done = t;
+                ++s->completed;
+                ++done;
+            }
+        }
+        for (size_t k = 0; k < st.touched.size(); ++k) {
+            const u32 t_ = st.touched[k];
+            s->known_I[t_] = st.snap[2 * k];
+            s->known_D[t_] = st.snap[2 * k + 1];
+            s->pending_new[t_] -= st.new_cells[k];
+            cht::table_set_bound(s->tables[t_], s->known_I[t_] + s->pending_new[t_], s->pending_new[t_] == 0);
+        }
+        s->aring.tail = st.arena_end;
+        s->mring.tail = st.meta_end;
+        s->dring.tail = st.dmeta_end;
+        s->spare_events.push_back(st.ev);
+        s->inflight.pop_front();
+    }
+    if (completed_now) *completed_now = done;
+    return CHT_OK;
+}
+
+// Admit what fits and launch one step.  *admitted = requests (or parts) in it.
+cht_status admit_and_launch(cht_server* s, u32* admitted) {
+    *admitted = 0;
+    if (s->inflight.size() >= s->cfg.max_inflight_steps || s->queue.empty()) return CHT_OK;
+    const size_t nt = s->tables.size();
+    std::vector<char> blocked(nt, 0);
+    std::vector<u64> step_new(nt, 0);
+    std::vector<Part> parts;
+    u64 ops = 0;
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+        if (parts.size() >= s->cfg.max_step_requests || ops >= s->cfg.max_step_ops) break;
+        Req& rq = s->reqs[*it];
+        const u32 t = rq.r.table;
+        if (blocked[t]) {
+            ++it;
+            continue;
+        }
+        cht_table* h = s->tables[t];
+        u64 m = rq.r.n - rq.admitted;
+        if (m > s->cfg.max_step_ops - ops) m = s->cfg.max_step_ops - ops;
+        const cht::TableInfo ti = cht::table_info(h);
+        if (has_vals(rq.r.op) && ti.growable) {
+            const u64 cap = 1ull << ti.log2c;
+            const u64 limit = u64(std::floor(ti.alpha * double(cap)));
+            u64 used = s->known_I[t] + s->pending_new[t] + step_new[t];
+            if (used >= limit) {
+                if (s->parts_inflight[t] != 0 || step_new[t] != 0) {  // wait for exact counts
+                    blocked[t] = 1;
+                    ++it;
+                    continue;
+                }
+                // nothing of this table in flight: its counts are exact; migrate now
+                const u64 live = s->known_I[t] - s->known_D[t];
+                const u64 half = u64(std::floor(ti.alpha * double(cap) / 2.0));
+                const u32 nl = ti.log2c + (live > half ? 1u : 0u);
+                const u64 need = (1ull << nl) * sizeof(cht::Cell);
+                if (s->cfg.memory_cap_bytes &&
+                    tables_bytes(s) + need + s->cfg.arena_bytes > s->cfg.memory_cap_bytes) {
+                    if (s->inflight.empty() && parts.empty()) {  // can never fit: reject
+                        rq.state = 3;
+                        rq.status = CHT_ERR_OOM;
+                        rq.t_done = now_s();
+                        ++s->completed;
+                        it = s->queue.erase(it);
+                        continue;
+                    }
+                    blocked[t] = 1;
+                    ++it;
+                    continue;
+                }
+                cht_status r = cht::table_migrate_to(h, nl, live, s->stream);
+                if (r != CHT_OK) return r;
+                s->known_I[t] = live;
+                s->known_D[t] = 0;
+                used = live;
+            }
+            const u64 limit2 = u64(std::floor(ti.alpha * double(1ull << cht::table_info(h).log2c)));
+            if (m > limit2 - used) m = limit2 - used;
+        }
+        if (rq.direct) {  // the engine reads / writes the request's arrays in place
+            Part p;
+            p.req = *it;
+            p.off = rq.admitted;
+            p.n = m;
+            p.d_keys = const_cast<u64*>(reinterpret_cast<const u64*>(rq.r.keys)) + rq.admitted;
+            p.d_vals = has_vals(rq.r.op) ? const_cast<u64*>(reinterpret_cast<const u64*>(rq.r.vals)) + rq.admitted : nullptr;
+            p.d_vout = rq.r.op == CHT_OP_FIND ? reinterpret_cast<u64*>(rq.r.vals_out) + rq.admitted : nullptr;
+            p.d_codes = rq.r.codes ? rq.r.codes + rq.admitted : nullptr;
+            p.direct = true;
+            parts.push_back(p);
+        } else {
+        // arena space for this part
+        const u64 pb = per_op_bytes(rq.r);
+        const u64 fit = s->aring.contiguous_free() / pb;
+        if (fit == 0) break;
+        if (m > fit) m = fit;
+        // up to four regions (keys, values or found values, codes), 256-byte aligned
+        auto part_bytes = [&](u64 mm) {
+            const u64 kb = (mm * 8 + 255) & ~255ull;
+            return kb * (1 + (has_vals(rq.r.op) || rq.r.op == CHT_OP_FIND ? 1 : 0)) +
+                   (rq.r.codes ? ((mm + 255) & ~255ull) : 0);
+        };
+        u64 off = 0;
+        while (m > 0 && !s->aring.alloc(part_bytes(m), &off)) m /= 2;  // padding or ring end: smaller part
+        if (m == 0) break;
+        const u64 kb2 = (m * 8 + 255) & ~255ull;
+        Part p;
+        p.req = *it;
+        p.off = rq.admitted;
+        p.n = m;
+        unsigned char* base = s->arena + off;
+        p.d_keys = reinterpret_cast<u64*>(base);
+        p.d_vals = has_vals(rq.r.op) ? reinterpret_cast<u64*>(base + kb2) : nullptr;
+        p.d_vout = rq.r.op == CHT_OP_FIND ? reinterpret_cast<u64*>(base + kb2) : nullptr;
+        p.d_codes = rq.r.codes ? base + kb2 * (has_vals(rq.r.op) || rq.r.op == CHT_OP_FIND ? 2 : 1) : nullptr;
+        if (cudaMemcpyAsync(p.d_keys, rq.r.keys + rq.admitted, m * 8, cudaMemcpyDefault, s->stream) != cudaSuccess)
+            return CHT_ERR_CUDA;
+        if (p.d_vals &&
+            cudaMemcpyAsync(p.d_vals, rq.r.vals + rq.admitted, m * 8, cudaMemcpyDefault, s->stream) != cudaSuccess)
+            return CHT_ERR_CUDA;
+        p.direct = false;
+        parts.push_back(p);
+        }
+        rq.admitted += m;
+        ++rq.parts_inflight;
+        ++s->parts_inflight[t];
+        if (has_vals(rq.r.op)) step_new[t] += m;
+        ops += m;
+        if (rq.admitted == rq.r.n) {
+            rq.state = 1;
+            it = s->queue.erase(it);
+        } else {
+            blocked[t] = 1;  // later requests of this table wait for the rest
+            ++it;
+        }
+    }
+    if (parts.empty()) return CHT_OK;
+
+    // ---- step metadata: tables, batches (one per part, arrival order), items
+    std::vector<cht::EngineTable> tabs(nt);
+    for (size_t t = 0; t < nt; ++t) {
+        const cht::TableInfo ti = cht::table_info(s->tables[t]);
+        tabs[t].cells = ti.cells;
+        tabs[t].log2c = ti.log2c;
+        tabs[t].pad = 0;
+        tabs[t].st = ti.st;
+    }
+    std::vector<cht::EngineBatch> batches(parts.size());
+    for (size_t i = 0; i < parts.size(); ++i) {
+        const Req& rq = s->reqs[parts[i].req];
+        batches[i].keys = parts[i].d_keys;
+        batches[i].vals = parts[i].d_vals;
+        batches[i].vals_out = parts[i].d_vout;
+        batches[i].codes = parts[i].d_codes;
+        batches[i].n = parts[i].n;
+        batches[i].table = rq.r.table;
+        batches[i].mode = u32(rq.r.op);
+    }
+    std::vector<cht::EngineChunk> chunks;
+    cht::plan_order(batches, nt, chunks);
+    std::vector<u32> touched;
+    std::vector<u64> tnew;
+    {
+        std::vector<char> seen(nt, 0);
+        for (const cht::EngineBatch& b : batches)
+            if (!seen[b.table]) {
+                seen[b.table] = 1;
+                touched.push_back(b.table);
+                tnew.push_back(step_new[b.table]);
+            }
+    }
+    const u64 b_tabs = nt * sizeof(cht::EngineTable), b_bat = batches.size() * sizeof(cht::EngineBatch);
+    const u64 b_chk = chunks.size() * sizeof(cht::EngineChunk), b_cnt = (2 + nt) * sizeof(unsigned long long);
+    const u64 o_bat = (b_tabs + 255) & ~255ull, o_chk = o_bat + ((b_bat + 255) & ~255ull);
+    const u64 o_cnt = o_chk + ((b_chk + 255) & ~255ull), o_snap = o_cnt + ((b_cnt + 255) & ~255ull);
+    const u64 total_meta = o_snap + touched.size() * 16;
+    u64 hoff = 0, doff = 0;
+    if (!s->mring.alloc(total_meta, &hoff) || !s->dring.alloc(o_snap, &doff)) return CHT_ERR_OOM;
+    unsigned char* hm = s->meta + hoff;
+    unsigned char* dm = s->dmeta + doff;
+    memcpy(hm, tabs.data(), b_tabs);
+    memcpy(hm + o_bat, batches.data(), b_bat);
+    memcpy(hm + o_chk, chunks.data(), b_chk);
+    if (cudaMemcpyAsync(dm, hm, o_cnt, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
+    if (cudaMemsetAsync(dm + o_cnt, 0, b_cnt, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
+    cht::EngineArgs e;
+    e.tables = reinterpret_cast<const cht::EngineTable*>(dm);
+    e.batches = reinterpret_cast<const cht::EngineBatch*>(dm + o_bat);
+    e.chunks = reinterpret_cast<const cht::EngineChunk*>(dm + o_chk);
+    e.n_chunks = chunks.size();
+    e.next = reinterpret_cast<unsigned long long*>(dm + o_cnt);
+    e.done = e.next + 1;
+    e.status = reinterpret_cast<u32*>(e.done + nt);
+    e.spin_limit = 2000000000ll;
+    e.inject_stall = 0;
+    if (cht::launch_engine(e, 1, 2, 0, s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CHT_ERR_CUDA;
+    }
+    // staged results back to the caller's arrays
+    for (const Part& p : parts) {
+        if (p.direct) continue;
+        const Req& rq = s->reqs[p.req];
+        if (p.d_vout && cudaMemcpyAsync(rq.r.vals_out + p.off, p.d_vout, p.n * 8, cudaMemcpyDefault, s->stream) !=
+                            cudaSuccess)
+            return CHT_ERR_CUDA;
+        if (p.d_codes &&
+            cudaMemcpyAsync(rq.r.codes + p.off, p.d_codes, p.n, cudaMemcpyDefault, s->stream) != cudaSuccess)
+            return CHT_ERR_CUDA;
+    }
+    Step st;
+    st.snap = reinterpret_cast<unsigned long long*>(hm + o_snap);
+    for (size_t k = 0; k < touched.size(); ++k) {
+        // DevState starts with I then D
+        if (cudaMemcpyAsync(st.snap + 2 * k, tabs[touched[k]].st, 16, cudaMemcpyDeviceToHost, s->stream) !=
+            cudaSuccess)
+            return CHT_ERR_CUDA;
+    }
+    if (!s->spare_events.empty()) {
+        st.ev = s->spare_events.back();
+        s->spare_events.pop_back();
+    } else if (cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming) != cudaSuccess) {
+        return CHT_ERR_CUDA;
+    }
+    if (cudaEventRecord(st.ev, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
+    st.arena_end = s->aring.head;
+    st.meta_end = s->mring.head;
+    st.dmeta_end = s->dring.head;
+    for (size_t k = 0; k < touched.size(); ++k) s->pending_new[touched[k]] += tnew[k];
+    st.touched = std::move(touched);
+    st.new_cells = std::move(tnew);
+    *admitted = u32(parts.size());
+    st.parts = std::move(parts);
+    s->inflight.push_back(std::move(st));
+    ++s->steps;
+    return CHT_OK;
+}
+
+}  // namespace
+
+// Can kernels on the server's device read and write p in place?
+bool addressable(const cht_server* s, const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return at.device == s->device;
+    if (at.type == cudaMemoryTypeHost) return true;  // pinned: mapped into the device's address space
+    return s->pageable_ok;
+}
+
+extern "C" {
+
+cht_status cht_server_create(const cht_handle* tables, uint32_t n_tables, const cht_server_config* cfg,
+                             cht_stream_t stream, cht_server_handle* out) {
+    if (!out || !tables || n_tables == 0) return CHT_ERR_INVALID_ARG;
+    *out = nullptr;
+    cht_server* s = new (std::nothrow) cht_server();
+    if (!s) return CHT_ERR_OOM;
+    s->cfg = cfg ? *cfg : cht_server_config{0, 0, 0, 0, 0, 0};
+    if (s->cfg.arena_bytes == 0) s->cfg.arena_bytes = 1ull << 30;
+    if (s->cfg.max_inflight_steps == 0) s->cfg.max_inflight_steps = 2;
+    if (s->cfg.max_step_requests == 0) s->cfg.max_step_requests = 8192;
+    if (s->cfg.max_step_ops == 0) s->cfg.max_step_ops = 1ull << 26;
+    s->stream = reinterpret_cast<cudaStream_t>(stream);
+    for (uint32_t i = 0; i < n_tables; ++i) {
+        if (!tables[i]) {
+            delete s;
+            return CHT_ERR_INVALID_ARG;
+        }
+        const cht::TableInfo ti = cht::table_info(tables[i]);
+        if (i == 0) s->device = ti.device;
+        if (ti.device != s->device) {
+            delete s;
+            return CHT_ERR_INVALID_ARG;
+        }
+        s->tables.push_back(tables[i]);
+    }
+    const size_t nt = s->tables.size();
+    s->known_I.assign(nt, 0);
+    s->known_D.assign(nt, 0);
+    s->pending_new.assign(nt, 0);
+    s->parts_inflight.assign(nt, 0);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, s->device) != cudaSuccess) {
+        cudaGetLastError();
+        pageable = 0;
+    }
+    s->pageable_ok = pageable != 0;
+    // exact starting counts of every table
+    cht_status r = CHT_OK;
+    for (size_t t = 0; t < nt && r == CHT_OK; ++t) r = cht::table_read_counts(s->tables[t], &s->known_I[t], &s->known_D[t], s->stream);
+    // metadata rings: room for several steps of the largest size
+    s->meta_bytes = (s->cfg.max_step_ops / cht::kChunkOps + s->cfg.max_step_requests + 1) * 48 +
+                    nt * (sizeof(cht::EngineTable) + 40) + (1u << 20);
+    s->meta_bytes *= (s->cfg.max_inflight_steps + 1);
+    s->aring.cap = s->cfg.arena_bytes;
+    s->mring.cap = s->meta_bytes;
+    s->dring.cap = s->meta_bytes;
+    if (r == CHT_OK) r = cht::runtime_alloc(reinterpret_cast<void**>(&s->arena), s->cfg.arena_bytes, s->stream);
+    if (r == CHT_OK) r = cht::runtime_alloc(reinterpret_cast<void**>(&s->dmeta), s->meta_bytes, s->stream);
+    if (r == CHT_OK && cudaHostAlloc(reinterpret_cast<void**>(&s->meta), s->meta_bytes, cudaHostAllocDefault) != cudaSuccess)
+        r = CHT_ERR_OOM;
+    if (r == CHT_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) r = CHT_ERR_CUDA;
+    if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+    if (r != CHT_OK) {
+        cht_server_destroy(s);
+        return r;
+    }
+    *out = s;
+    return CHT_OK;
+}
+
+cht_status cht_server_submit(cht_server_handle s, const cht_request* req, uint64_t* id) {
+    if (!s || !req || req->table >= s->tables.size() || req->op < CHT_OP_FIND || req->op > CHT_OP_ERASE ||
+        req->n == 0 || !req->keys || (has_vals(req->op) && !req->vals) || (req->op == CHT_OP_FIND && !req->vals_out))
+        return CHT_ERR_INVALID_ARG;
+    Req rq;
+    rq.r = *req;
+    rq.direct = !s->cfg.stage_inputs && addressable(s, req->keys) && (!has_vals(req->op) || addressable(s, req->vals)) &&
+                (req->op != CHT_OP_FIND || addressable(s, req->vals_out)) && (!req->codes || addressable(s, req->codes));
+    rq.t_arrival = now_s();
+    const u64 i = s->reqs.size();
+    s->reqs.push_back(rq);
+    s->queue.push_back(i);
+    if (id) *id = i;
+    return CHT_OK;
+}
+
+cht_status cht_server_step(cht_server_handle s, uint32_t* admitted, uint32_t* completed) {
+    if (!s) return CHT_ERR_INVALID_ARG;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    u32 c = 0, a = 0;
+    cht_status r = poll(s, &c);
+    if (r == CHT_OK) r = admit_and_launch(s, &a);
+    if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+    if (admitted) *admitted = a;
+    if (completed) *completed = c;
+    return r;
+}
+
+cht_status cht_server_drain(cht_server_handle s) {
+    if (!s) return CHT_ERR_INVALID_ARG;
+    while (s->completed < s->reqs.size()) {
+        cht_status r = cht_server_step(s, nullptr, nullptr);
+        if (r != CHT_OK) return r;
+        if (!s->inflight.empty() && s->inflight.size() >= s->cfg.max_inflight_steps) cudaEventSynchronize(s->inflight.front().ev);
+        else if (s->queue.empty() && !s->inflight.empty()) cudaEventSynchronize(s->inflight.front().ev);
+    }
+    return CHT_OK;
+}
+
+cht_status cht_server_result(cht_server_handle s, uint64_t id, int* done, double* latency_s, cht_status* req_status) {
+    if (!s || id >= s->reqs.size()) return CHT_ERR_INVALID_ARG;
+    const Req& rq = s->reqs[id];
+    if (done) *done = rq.state >= 2;
+    if (latency_s) *latency_s = rq.state >= 2 ? rq.t_done - rq.t_arrival : 0.0;
+    if (req_status) *req_status = rq.status;
+    return CHT_OK;
+}
+
+cht_status cht_server_replay(cht_server_handle s, const cht_request* reqs, const double* arrival_s, uint64_t n,
+                             double* latency_s, double* makespan_s) {
+    if (!s || (n > 0 && (!reqs || !arrival_s))) return CHT_ERR_INVALID_ARG;
+    const u64 first = s->reqs.size();
+    const double t0 = now_s();
+    u64 next = 0;
+    while (next < n || s->completed < s->reqs.size()) {
+        const double t = now_s() - t0;
+        while (next < n && arrival_s[next] <= t) {
+            uint64_t id;
+            cht_status r = cht_server_submit(s, &reqs[next], &id);
+            if (r != CHT_OK) return r;
+            s->reqs[id].t_arrival = t0 + arrival_s[next];  // scheduled arrival
+            ++next;
+        }
+        cht_status r = cht_server_step(s, nullptr, nullptr);
+        if (r != CHT_OK) return r;
+    }
+    double last = t0;
+    for (u64 i = 0; i < n; ++i) {
+        const Req& rq = s->reqs[first + i];
+        if (latency_s) latency_s[i] = rq.t_done - rq.t_arrival;
+        if (rq.t_done > last) last = rq.t_done;
+    }
+    if (makespan_s) *makespan_s = last - t0;
+    return CHT_OK;
+}
+
+cht_status cht_server_stats(cht_server_handle s, uint64_t* steps, uint64_t* completed) {
+    if (!s) return CHT_ERR_INVALID_ARG;
+    if (steps) *steps = s->steps;
+    if (completed) *completed = s->completed;
+    return CHT_OK;
+}
+
+cht_status cht_server_destroy(cht_server_handle s) {
+    if (!s) return CHT_ERR_INVALID_ARG;
+    if (s->stream || !s->inflight.empty()) cudaStreamSynchronize(s->stream);
+    for (Step& st : s->inflight)
+        if (st.ev) cudaEventDestroy(st.ev);
+    for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
+    if (s->arena) cht::runtime_free(s->arena, s->cfg.arena_bytes, s->stream);
+    if (s->dmeta) cht::runtime_free(s->dmeta, s->meta_bytes, s->stream);
+    if (s->meta) cudaFreeHost(s->meta);
+    cudaStreamSynchronize(s->stream);
+    delete s;
+    return CHT_OK;
+}
+
+}  // extern "C"

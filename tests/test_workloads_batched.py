@@ -44,3 +44,17 @@ def test_keys_numpy_torch_agree_and_streams_are_sane():
             s.update(seg.tolist())
     all_ins = [x for s in inserted.values() for x in s]
     assert len(all_ins) == len(set(all_ins)) == int(wl["n_t"].sum())
+
+
+def test_serving_workload_recipe():
+    wl = W.serving_workload(20_000, n_tables=64, log2_min=8, log2_max=12, size_log2_max=12, seed=3)
+    assert (wl["n"] >= 1).all() and (wl["n"] <= 1 << 12).all()
+    frac = np.bincount(wl["op"], minlength=5) / len(wl["op"])
+    assert abs(frac[W.OP_FIND] - 0.5) < 0.02 and abs(frac[W.OP_INSERT] - 0.3) < 0.02
+    assert abs(frac[W.OP_IOU_ADD] - 0.15) < 0.02 and abs(frac[W.OP_ERASE] - 0.05) < 0.01
+    counts = np.bincount(wl["table"], minlength=64)
+    assert counts[0] > counts[1] > counts[3] > counts[15]  # Zipf(1.0) over the tables
+    k, _ = W.serving_keys(wl, 0, 500)
+    t = np.repeat(wl["table"][:500], wl["n"][:500])
+    for tt in np.unique(t)[:5]:
+        assert np.unique(k[t == tt]).size <= wl["n_t"][tt]  # drawn from the table's universe

@@ -457,3 +457,98 @@ def _batched_keys_t(wl, first, last, device):
     vals = torch.where(is_ins, keys * 3, torch.zeros_like(keys))
     vals = torch.where(op == OP_IOU_ADD, torch.ones_like(keys), vals)
     return keys, vals
+
+
+# ----------------------------------------------------------------------------
+# serving: requests over resident growing tables
+# ----------------------------------------------------------------------------
+OP_ERASE = 4
+STREAM_UNIVERSE = 3
+SEED_SERVING = 5
+
+
+def serving_workload(n_requests: int, n_tables: int = 256, log2_min: int = 10, log2_max: int = 24,
+                     size_log2_max: int = 16, table_s: float = 1.0, mix=(0.5, 0.3, 0.15, 0.05),
+                     seed: int = SEED_SERVING):
+    """Structure of the serving workload (host side, numpy).
+
+    Table t has a key universe of n_t keys, n_t log-uniform on
+    [2^log2_min, 2^log2_max] (its final size); requests pick their table by
+    Zipf(table_s) over the tables (rank r -> table r-1), their size
+    log-uniform on [1, 2^size_log2_max] and one operation type: find / insert /
+    insertOrUpdate(add) / erase with probabilities `mix`.  Every key is drawn
+    uniformly from the request's table universe, so tables never hold more
+    than n_t keys and finds hit or miss depending on what is present.
+    """
+    rng = np.random.default_rng(seed)
+    n_t = np.floor(np.exp2(rng.uniform(log2_min, log2_max, n_tables))).astype(np.int64)
+    ranks = np.arange(1, n_tables + 1, dtype=np.float64)
+    p = ranks ** -table_s
+    p /= p.sum()
+    table = rng.choice(n_tables, size=n_requests, p=p).astype(np.int64)
+    size = np.floor(np.exp(rng.uniform(0.0, size_log2_max * np.log(2.0), n_requests))).astype(np.int64)
+    size = np.clip(size, 1, 1 << size_log2_max)
+    u = rng.random(n_requests)
+    cum = np.cumsum(mix)
+    op = np.where(u < cum[0], OP_FIND, np.where(u < cum[1], OP_INSERT, np.where(u < cum[2], OP_IOU_ADD, OP_ERASE)))
+    offsets = np.zeros(n_requests + 1, dtype=np.int64)
+    np.cumsum(size, out=offsets[1:])
+    return {"n_tables": n_tables, "n_t": n_t, "table": table, "n": size, "op": op.astype(np.int64),
+            "offsets": offsets, "seed": seed}
+
+
+def serving_keys(wl, first: int = 0, last: int | None = None, backend="numpy"):
+    """Keys and values of requests [first, last): key = universe key
+    hash(request, j) mod n_t of the request's table; values: key * 3 for
+    inserts, 1 for insertOrUpdate(add)."""
+    last = len(wl["n"]) if last is None else last
+    if backend == "numpy":
+        sizes = wl["n"][first:last]
+        total = int(sizes.sum())
+        rid = np.repeat(np.arange(first, last, dtype=np.int64), sizes)
+        j = np.arange(total, dtype=np.int64) - (wl["offsets"][rid] - wl["offsets"][first])
+        t = wl["table"][rid]
+        h = _mix13_np((rid.astype(np.uint64) << np.uint64(20)) ^ j.astype(np.uint64) ^ np.uint64(wl["seed"] << 58))
+        idx = (h % wl["n_t"][t].astype(np.uint64)).astype(np.int64)
+        salt = _stream_salt(t, np.full(total, STREAM_UNIVERSE), wl["seed"])
+        with np.errstate(over="ignore"):
+            keys = _mix13_np(salt + (idx.astype(np.uint64) + np.uint64(1)) * np.uint64(GOLDEN_GAMMA))
+        _check_reserved(keys, "numpy")
+        op = wl["op"][rid]
+        vals = np.zeros(total, dtype=np.uint64)
+        with np.errstate(over="ignore"):
+            vals[op == OP_INSERT] = keys[op == OP_INSERT] * np.uint64(3)
+        vals[op == OP_IOU_ADD] = 1
+        return keys, vals
+    torch = _torch()
+
+    def col(name):
+        return torch.from_numpy(np.ascontiguousarray(wl[name][first:last])).to(backend)
+
+    sizes = col("n")
+    total = int(wl["offsets"][last] - wl["offsets"][first])
+    rid = torch.repeat_interleave(torch.arange(first, last, dtype=torch.int64, device=backend), sizes)
+    off = torch.repeat_interleave(
+        torch.from_numpy(np.ascontiguousarray(wl["offsets"][first:last] - wl["offsets"][first])).to(backend), sizes)
+    j = torch.arange(total, dtype=torch.int64, device=backend) - off
+    del off
+    t = torch.repeat_interleave(col("table"), sizes)
+    nt = torch.from_numpy(np.ascontiguousarray(wl["n_t"])).to(backend)[t]
+    h = _mix13_t((rid << 20) ^ j ^ _s64(wl["seed"] << 58))
+    # unsigned h mod n_t with int64 arithmetic: (hi * 2^32 + lo) mod n
+    hi = _lsr_t(h, 32)
+    lo = h & 0xFFFFFFFF
+    idx = ((hi % nt) * (1 << 32) % nt + lo % nt) % nt
+    salt = _mix13_t((t * 8 + STREAM_UNIVERSE + _s64(wl["seed"] << 40)) ^ _s64(0x6A09E667F3BCC909))
+    keys = _mix13_t(salt + (idx + 1) * _s64(GOLDEN_GAMMA))
+    _check_reserved(keys, "torch")
+    op = torch.repeat_interleave(col("op"), sizes)
+    vals = torch.where(op == OP_INSERT, keys * 3, torch.zeros_like(keys))
+    vals = torch.where(op == OP_IOU_ADD, torch.ones_like(keys), vals)
+    return keys, vals
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int = SEED_SERVING + 1) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson process with the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, n))
