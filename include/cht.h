@@ -261,13 +261,15 @@ cht_status cht_plan_destroy(cht_plan_handle p);
  * tables overlap), copies the results back and records when each request
  * completes.  The next step is prepared and launched while the previous one
  * still runs (up to max_inflight_steps), so requests that arrive meanwhile
- * join the next step: continuous batching.  Growable tables keep their growth
- * policy: a step admits at most a table's remaining room (alpha * c minus its
- * non-empty cells, known exactly from counters snapshotted after each step)
- * of insert / insert-or-update operations; a larger request is admitted in
- * parts over several steps while later requests on that table wait; a table
- * with no room and nothing in flight is migrated first.  Admission also keeps
- * the tables plus the arena within memory_cap_bytes. */
+ * join the next step: continuous batching.  Growable tables keep the load
+ * bound: before an insert / insert-or-update request whose operations could
+ * push a table's non-empty cells (known exactly from counters snapshotted
+ * after each step, plus what is in flight) past alpha * c, the table is
+ * migrated, stream-ordered, to the smallest capacity that holds them all.  A
+ * request larger than a step (max_step_ops) or than the free arena is
+ * admitted in parts; later requests on its table wait for the rest.
+ * Admission keeps the tables plus the arena within memory_cap_bytes; a
+ * request whose table can never fit is rejected (CHT_ERR_OOM). */
 typedef struct cht_server *cht_server_handle;
 
 typedef struct {

@@ -16,12 +16,12 @@
 //
 // Growth (growable tables, Sec. 4.3.2 trigger): the host knows each table's
 // non-empty cells exactly as of its last completed step (the snapshots) plus
-// an upper bound of what its in-flight steps add.  A step admits at most the
-// remaining room floor(alpha*c) - bound of insert / insert-or-update
-// operations; a larger request is admitted in parts.  A table with no room
-// and nothing in flight is migrated before the step: doubled if more than
-// alpha*c/2 elements are live, else rebuilt at the same size to drop
-// tombstones (Sec. 4.4) -- the same policy as single calls.
+// an upper bound of what its in-flight steps add.  When an insert /
+// insert-or-update request would push that bound past alpha * c, the table is
+// first migrated to the smallest power-of-two capacity that holds the bound
+// plus the whole request (bulk pre-sizing, Sec. 4.5; tombstones are dropped,
+// Sec. 4.4).  The migration is ordered on the stream after the steps in
+// flight, so admission never waits for counts.
 #include <chrono>
 #include <cmath>
 #include <deque>
@@ -194,22 +194,20 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
         if (m > s->cfg.max_step_ops - ops) m = s->cfg.max_step_ops - ops;
         const cht::TableInfo ti = cht::table_info(h);
         if (has_vals(rq.r.op) && ti.growable) {
-            const u64 cap = 1ull << ti.log2c;
-            const u64 limit = u64(std::floor(ti.alpha * double(cap)));
-            u64 used = s->known_I[t] + s->pending_new[t] + step_new[t];
-            if (used >= limit) {
-                if (s->parts_inflight[t] != 0 || step_new[t] != 0) {  // wait for exact counts
-                    blocked[t] = 1;
-                    ++it;
-                    continue;
-                }
-                // nothing of this table in flight: its counts are exact; migrate now
-                const u64 live = s->known_I[t] - s->known_D[t];
-                const u64 half = u64(std::floor(ti.alpha * double(cap) / 2.0));
-                const u32 nl = ti.log2c + (live > half ? 1u : 0u);
+            // Room check with an upper bound of the non-empty cells (every
+            // admitted insert counted as new).  If the part does not fit, grow
+            // now to the smallest capacity whose alpha-limit holds the bound
+            // plus the whole part (the bulk pre-sizing of Sec. 4.5); the
+            // migration is stream-ordered after the steps in flight, so it
+            // needs neither a wait nor the exact count (it also drops
+            // tombstones, which only lowers the count).
+            const u64 used = s->known_I[t] + s->pending_new[t] + step_new[t];
+            const u64 limit = u64(std::floor(ti.alpha * double(1ull << ti.log2c)));
+            if (used + m > limit) {
+                u32 nl = ti.log2c;
+                while (nl < 40 && u64(std::floor(ti.alpha * double(1ull << nl))) < used + m) ++nl;
                 const u64 need = (1ull << nl) * sizeof(cht::Cell);
-                if (s->cfg.memory_cap_bytes &&
-                    tables_bytes(s) + need + s->cfg.arena_bytes > s->cfg.memory_cap_bytes) {
+                if (s->cfg.memory_cap_bytes && tables_bytes(s) + need + s->cfg.arena_bytes > s->cfg.memory_cap_bytes) {
                     if (s->inflight.empty() && parts.empty()) {  // can never fit: reject
                         rq.state = 3;
                         rq.status = CHT_ERR_OOM;
@@ -222,14 +220,9 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
                     ++it;
                     continue;
                 }
-                cht_status r = cht::table_migrate_to(h, nl, live, s->stream);
+                cht_status r = cht::table_migrate_to(h, nl, ~0ull, s->stream);
                 if (r != CHT_OK) return r;
-                s->known_I[t] = live;
-                s->known_D[t] = 0;
-                used = live;
             }
-            const u64 limit2 = u64(std::floor(ti.alpha * double(1ull << cht::table_info(h).log2c)));
-            if (m > limit2 - used) m = limit2 - used;
         }
         if (rq.direct) {  // the engine reads / writes the request's arrays in place
             Part p;

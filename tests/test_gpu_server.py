@@ -126,7 +126,7 @@ def test_server_matches_oracle(cuda_lib, oracle_mod):
     srv.destroy()
 
 
-def test_server_admits_large_insert_in_parts(cuda_lib):
+def test_server_grows_for_a_large_insert(cuda_lib):
     n = 20_000
     keys = W.uniform_keys(n, seed=43)
     codes = np.zeros(n, np.uint8)
@@ -138,8 +138,21 @@ def test_server_admits_large_insert_in_parts(cuda_lib):
     assert done and st == cuda_lib.CHT_OK and lat > 0
     assert (codes == 1).all()
     live, ne, cap = t.size(check=True)
-    assert live == n and cap == 1 << 16  # grown step by step at load 0.5
-    assert srv.stats()[0] > 1  # admitted in parts over several steps
+    assert live == n and cap == 1 << 16  # pre-sized once for the whole request at load 0.5
+    srv.destroy()
+
+
+def test_server_splits_requests_larger_than_a_step(cuda_lib):
+    n = 20_000
+    keys = W.uniform_keys(n, seed=45)
+    codes = np.zeros(n, np.uint8)
+    t = cuda_lib.Table(1 << 16)
+    srv = cuda_lib.Server([t], arena_bytes=1 << 20, max_step_ops=4096, stage_inputs=1)
+    rid = srv.submit(0, cuda_lib.OP_INSERT, keys, keys, None, codes)
+    srv.drain()
+    assert srv.result(rid)[0] and (codes == 1).all()
+    assert srv.stats()[0] >= 5  # admitted in parts over several steps
+    assert t.size()[0] == n
     srv.destroy()
 
 
