@@ -860,35 +860,46 @@ def run_serving(args):
 
     def run(arrivals):
         tables = [cht.Table(1024, growable=True) for _ in range(256)]
-        srv = cht.Server(tables, memory_cap_bytes=64 << 30, arena_bytes=1 << 30, max_inflight_steps=2)
+        srv = cht.Server(tables, memory_cap_bytes=64 << 30, arena_bytes=1 << 30, max_inflight_steps=2,
+                         stage_inputs=args.serving_stage_inputs)
         lat, mk = srv.replay(reqs, arrivals)
         steps, done = srv.stats()
+        prof = srv.profile()
         grown = sum(t.size()[2] for t in tables) * 16
         srv.destroy()
         for t in tables:
             t.destroy()
         torch.cuda.synchronize()
-        return lat, mk, steps, done, grown
+        return lat, mk, steps, done, grown, prof
 
-    lat0, mk0, steps0, done0, grown = run(np.zeros(nreq))
+    def breakdown(prof, mk):
+        return {"gpu_busy_s": round(prof["gpu_step_ms"] / 1e3, 4), "engine_s": round(prof["engine_ms"] / 1e3, 4),
+                "host_admit_s": round(prof["host_admit_ms"] / 1e3, 4), "makespan_s": round(mk, 4),
+                "dependent_rounds": prof["rounds"], "parts": prof["parts"], "work_items": prof["chunks"],
+                "migrations": prof["migrations"]}
+
+    lat0, mk0, steps0, done0, grown, prof0 = run(np.zeros(nreq))
     assert done0 == nreq
     cap_rps = nreq / mk0
     out = {"workload": "serving: 256 growable tables (key universes log-uniform 2^10..2^24), requests of 1..65536 "
                        "ops (log-uniform), table ~ Zipf(1.0), find/insert/insertOrUpdate(add)/erase 50/30/15/5, "
                        "request arrays in pinned host memory, memory cap 64 GiB",
+           "request_arrays": "copied through the device arena" if args.serving_stage_inputs else
+                             "read and written in place (zero-copy)",
            "requests": nreq, "ops": total, "final_table_bytes": grown,
            "capacity": {"makespan_s": round(mk0, 4), "requests_per_s": round(cap_rps, 1),
                         "mops": round(total / mk0 / 1e6, 1), "steps": steps0,
                         "p50_ms": round(float(np.percentile(lat0, 50)) * 1e3, 3),
-                        "p99_ms": round(float(np.percentile(lat0, 99)) * 1e3, 3)}}
+                        "p99_ms": round(float(np.percentile(lat0, 99)) * 1e3, 3),
+                        "time": breakdown(prof0, mk0)}}
     for frac in args.serving_loads:
         arr = W.poisson_arrivals(nreq, frac * cap_rps)
-        lat, mk, steps, done, _ = run(arr)
+        lat, mk, steps, done, _, prof = run(arr)
         out[f"load_{frac}"] = {"offered_requests_per_s": round(frac * cap_rps, 1), "makespan_s": round(mk, 4),
                                "mops": round(total / mk / 1e6, 1), "steps": steps,
                                "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
-                               "max_ms": round(float(lat.max()) * 1e3, 3)}
+                               "max_ms": round(float(lat.max()) * 1e3, 3), "time": breakdown(prof, mk)}
     print(json.dumps(out), flush=True)
 
 
@@ -919,6 +930,8 @@ def main():
     ap.add_argument("--no-graph-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=100_000)
     ap.add_argument("--serving-loads", type=float, nargs="*", default=[0.5, 0.7, 0.9])
+    ap.add_argument("--serving-stage-inputs", type=int, default=0, choices=[0, 1],
+                    help="1: copy every request through the device arena instead of reading it in place")
     args = ap.parse_args()
     if args.workload == "batched":
         run_batched(args)

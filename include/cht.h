@@ -223,13 +223,18 @@ typedef struct cht_plan *cht_plan_handle;
  * sector); ctas_per_sm: 0 = occupancy maximum; spin_limit_us: bound of one
  * dependency wait (0 = about one second) -- a wait that runs out stops the
  * launch with CHT_PLAN_TIMEOUT in the plan status; fault_inject: testing
- * only, bit 0 makes the first work item wait for a count nothing reaches. */
+ * only, bit 0 makes the first work item wait for a count nothing reaches;
+ * direct_io: 0 = each warp copies its work item's keys and values into
+ * shared memory with one coalesced pass and writes results back with one
+ * (the default), 1 = the probe loops read and write the batch arrays in
+ * place. */
 typedef struct {
     int group_width;
     int lane_cells;
     int ctas_per_sm;
     int spin_limit_us;
     int fault_inject;
+    int direct_io;
 } cht_plan_config;
 
 #define CHT_PLAN_TIMEOUT 0x1u
@@ -321,6 +326,29 @@ cht_status cht_server_replay(cht_server_handle s, const cht_request *reqs, const
                              uint64_t n, double *latency_s, double *makespan_s);
 /* Steps launched so far and requests completed so far. */
 cht_status cht_server_stats(cht_server_handle s, uint64_t *steps, uint64_t *completed);
+
+/* Where a server's time went, summed over the steps that have completed
+ * (times from CUDA events on the server's stream; host time from the wall
+ * clock).  gpu_step_ms: device time from a step's first migration or copy to
+ * its last copy back (steps run one after another on the stream, so the
+ * makespan minus this is time the stream had no step to run); engine_ms: the
+ * engine launches alone; host_admit_ms: host time spent admitting requests
+ * and preparing launches (steps that launched); rounds: sum over steps of
+ * the longest chain of dependent batches (one table's requests in arrival
+ * order); parts: request parts launched; chunks: engine work items;
+ * migrations: growth migrations started. */
+typedef struct {
+    uint64_t steps;
+    uint64_t completed;
+    uint64_t parts;
+    uint64_t chunks;
+    uint64_t rounds;
+    uint64_t migrations;
+    double gpu_step_ms;
+    double engine_ms;
+    double host_admit_ms;
+} cht_server_profile;
+cht_status cht_server_get_profile(cht_server_handle s, cht_server_profile *out);
 cht_status cht_server_destroy(cht_server_handle s);
 
 /* Cap, in bytes, on the device memory this library allocates at any time for

@@ -70,9 +70,15 @@ class Request(ctypes.Structure):
                 ("codes", ctypes.c_void_p)]
 
 
+class ServerProfile(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("parts", ctypes.c_uint64),
+                ("chunks", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("migrations", ctypes.c_uint64),
+                ("gpu_step_ms", ctypes.c_double), ("engine_ms", ctypes.c_double), ("host_admit_ms", ctypes.c_double)]
+
+
 class PlanConfig(ctypes.Structure):
     _fields_ = [("group_width", ctypes.c_int), ("lane_cells", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("spin_limit_us", ctypes.c_int), ("fault_inject", ctypes.c_int)]
+                ("spin_limit_us", ctypes.c_int), ("fault_inject", ctypes.c_int), ("direct_io", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -125,6 +131,7 @@ def load_library(build: bool = True):
                                         ctypes.POINTER(ctypes.c_int)]),
             "cht_server_replay": (i32, [p, p, p, u64, p, ctypes.POINTER(ctypes.c_double)]),
             "cht_server_stats": (i32, [p, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+            "cht_server_get_profile": (i32, [p, ctypes.POINTER(ServerProfile)]),
             "cht_server_destroy": (i32, [p]),
         }
         for name, (res, args) in sigs.items():
@@ -433,6 +440,12 @@ class Server:
         st, done = ctypes.c_uint64(), ctypes.c_uint64()
         _check(self._lib.cht_server_stats(self._h, ctypes.byref(st), ctypes.byref(done)), "cht_server_stats")
         return int(st.value), int(done.value)
+
+    def profile(self) -> dict:
+        """Where the server's time went (cht_server_get_profile)."""
+        pr = ServerProfile()
+        _check(self._lib.cht_server_get_profile(self._h, ctypes.byref(pr)), "cht_server_get_profile")
+        return {f: getattr(pr, f) for f, _ in ServerProfile._fields_}
 
     def destroy(self):
         if getattr(self, "_h", None) and self._h.value:

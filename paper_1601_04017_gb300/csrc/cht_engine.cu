@@ -21,6 +21,15 @@
 // earlier one modified the table, so every table read in the engine goes
 // through L2 (finds included); writers fence before they count a chunk done
 // and waiters load the counter with acquire semantics.
+//
+// Staged I/O (the default): a warp copies its chunk's keys and values, in
+// windows of kStageOps operations, into its own shared-memory area with one
+// coalesced pass, runs the probe loop from there and writes the found values
+// and result codes back with one coalesced pass.  The probe loop itself
+// touches the request arrays one scattered element at a time; when those
+// arrays are in host memory (a serving loop reading requests in place across
+// NVLink-C2C) every such access is a separate round trip, and staging turns
+// them into a few full-width transfers per window.
 #include <atomic>
 
 #include "cht_ops.cuh"
@@ -41,10 +50,47 @@ __device__ __forceinline__ void red_release_add(unsigned long long* p, u64 v) {
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-template <int G, int V>
+// Operations per staging window and the shared memory one warp uses for it:
+// keys, values (find results reuse this array: finds read no values) and
+// one result byte per operation.
+constexpr u32 kStageOps = 128;
+constexpr u32 kStageWarpBytes = kStageOps * (8 + 8 + 1);
+static_assert(kChunkOps % kStageOps == 0, "a chunk is a whole number of windows");
+static_assert(kStageWarpBytes % 8 == 0, "warp areas stay 8-byte aligned");
+
+template <int G, int V, int MODE, bool kStaged>
+__device__ __forceinline__ void engine_window(const OpArgs& a, u64 first, u64 end, u64& n_ins, u64& n_del,
+                                              u32& sbits, const WarpStage& sg) {
+    warp_ops<G, V, MODE, true, kStaged>(a, first, end, n_ins, n_del, sbits, sg);
+}
+
+template <int G, int V, bool kStaged>
+__device__ __forceinline__ void engine_run(int mode, const OpArgs& a, u64 first, u64 end, u64& n_ins,
+                                           u64& n_del, u32& sbits, const WarpStage& sg) {
+    switch (mode) {
+        case kFind: engine_window<G, V, kFind, kStaged>(a, first, end, n_ins, n_del, sbits, sg); break;
+        case kInsert: engine_window<G, V, kInsert, kStaged>(a, first, end, n_ins, n_del, sbits, sg); break;
+        case kIouAdd: engine_window<G, V, kIouAdd, kStaged>(a, first, end, n_ins, n_del, sbits, sg); break;
+        case kIouOverwrite:
+            engine_window<G, V, kIouOverwrite, kStaged>(a, first, end, n_ins, n_del, sbits, sg);
+            break;
+        default: engine_window<G, V, kErase, kStaged>(a, first, end, n_ins, n_del, sbits, sg); break;
+    }
+}
+
+template <int G, int V, bool kStaged>
 __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
     constexpr u32 FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char engine_smem[];
     const int lane = threadIdx.x & 31;
+    WarpStage sg{};
+    if (kStaged) {
+        unsigned char* w = engine_smem + (threadIdx.x >> 5) * kStageWarpBytes;
+        sg.keys = reinterpret_cast<u64*>(w);
+        sg.vals = sg.keys + kStageOps;
+        sg.vout = sg.vals;
+        sg.codes = reinterpret_cast<unsigned char*>(sg.vals + kStageOps);
+    }
     for (;;) {
         u64 c = 0;
         if (lane == 0) c = atomicAdd(e.next, 1ull);
@@ -90,14 +136,28 @@ __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
         a.n = b.n;
         a.st = t.st;
         const u64 end = ch.start + ch.count;
+        const bool has_vals = b.mode == kInsert || b.mode == kIouAdd || b.mode == kIouOverwrite;
         u64 n_ins = 0, n_del = 0;
         u32 sbits = 0;
-        switch (b.mode) {
-            case kFind: warp_ops<G, V, kFind, true>(a, ch.start, end, n_ins, n_del, sbits); break;
-            case kInsert: warp_ops<G, V, kInsert, true>(a, ch.start, end, n_ins, n_del, sbits); break;
-            case kIouAdd: warp_ops<G, V, kIouAdd, true>(a, ch.start, end, n_ins, n_del, sbits); break;
-            case kIouOverwrite: warp_ops<G, V, kIouOverwrite, true>(a, ch.start, end, n_ins, n_del, sbits); break;
-            default: warp_ops<G, V, kErase, true>(a, ch.start, end, n_ins, n_del, sbits); break;
+        if (kStaged) {
+            for (u64 w0 = ch.start; w0 < end; w0 += kStageOps) {
+                const u32 cnt = u32(end - w0 < kStageOps ? end - w0 : kStageOps);
+                sg.base = w0;
+                for (u32 j = lane; j < cnt; j += 32) {
+                    sg.keys[j] = ld_stream(b.keys + w0 + j);
+                    if (has_vals) sg.vals[j] = ld_stream(b.vals + w0 + j);
+                }
+                __syncwarp();
+                engine_run<G, V, true>(b.mode, a, w0, w0 + cnt, n_ins, n_del, sbits, sg);
+                __syncwarp();
+                for (u32 j = lane; j < cnt; j += 32) {
+                    if (b.mode == kFind) b.vals_out[w0 + j] = sg.vout[j];
+                    if (b.codes) b.codes[w0 + j] = sg.codes[j];
+                }
+                __syncwarp();  // the next window overwrites this one's area
+            }
+        } else {
+            engine_run<G, V, false>(b.mode, a, ch.start, end, n_ins, n_del, sbits, sg);
         }
         warp_flush_counters(t.st, n_ins, n_del, sbits);
         __threadfence();  // this lane's table writes before the chunk is counted
@@ -106,12 +166,14 @@ __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
     }
 }
 
-template <int G, int V>
-cudaError_t launch_engine_gv(const EngineArgs& e, int ctas_per_sm, cudaStream_t s) {
+template <int G, int V, bool kStaged>
+cudaError_t launch_engine_gvs(const EngineArgs& e, int ctas_per_sm, cudaStream_t s) {
+    const u32 smem = kStaged ? (kOpBlock / 32) * kStageWarpBytes : 0;
     static std::atomic<int> occ{0};
     int per_sm = occ.load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel<G, V>, kOpBlock, 0);
+        cudaError_t err =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel<G, V, kStaged>, kOpBlock, smem);
         if (err != cudaSuccess) return err;
         if (per_sm < 1) per_sm = 1;
         occ.store(per_sm, std::memory_order_relaxed);
@@ -122,30 +184,37 @@ cudaError_t launch_engine_gv(const EngineArgs& e, int ctas_per_sm, cudaStream_t 
     const u64 need = (e.n_chunks + kOpBlock / 32 - 1) / (kOpBlock / 32);
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    engine_kernel<G, V><<<unsigned(grid), kOpBlock, 0, s>>>(e);
+    engine_kernel<G, V, kStaged><<<unsigned(grid), kOpBlock, smem, s>>>(e);
     count_launch();
     return cudaGetLastError();
 }
 
+template <int G, int V>
+cudaError_t launch_engine_gv(const EngineArgs& e, bool staged, int ctas_per_sm, cudaStream_t s) {
+    return staged ? launch_engine_gvs<G, V, true>(e, ctas_per_sm, s)
+                  : launch_engine_gvs<G, V, false>(e, ctas_per_sm, s);
+}
+
 }  // namespace
 
-cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, cudaStream_t s) {
+cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, bool staged,
+                          cudaStream_t s) {
     if (e.n_chunks == 0) return cudaSuccess;
     if (lane_cells == 2) {
         switch (group_width) {
-            case 1: return launch_engine_gv<1, 2>(e, ctas_per_sm, s);
-            case 4: return launch_engine_gv<4, 2>(e, ctas_per_sm, s);
-            case 8: return launch_engine_gv<8, 2>(e, ctas_per_sm, s);
-            case 16: return launch_engine_gv<16, 2>(e, ctas_per_sm, s);
+            case 1: return launch_engine_gv<1, 2>(e, staged, ctas_per_sm, s);
+            case 4: return launch_engine_gv<4, 2>(e, staged, ctas_per_sm, s);
+            case 8: return launch_engine_gv<8, 2>(e, staged, ctas_per_sm, s);
+            case 16: return launch_engine_gv<16, 2>(e, staged, ctas_per_sm, s);
             default: return cudaErrorInvalidValue;
         }
     }
     switch (group_width) {
-        case 1: return launch_engine_gv<1, 2>(e, ctas_per_sm, s);
-        case 4: return launch_engine_gv<4, 1>(e, ctas_per_sm, s);
-        case 8: return launch_engine_gv<8, 1>(e, ctas_per_sm, s);
-        case 16: return launch_engine_gv<16, 1>(e, ctas_per_sm, s);
-        case 32: return launch_engine_gv<32, 1>(e, ctas_per_sm, s);
+        case 1: return launch_engine_gv<1, 2>(e, staged, ctas_per_sm, s);
+        case 4: return launch_engine_gv<4, 1>(e, staged, ctas_per_sm, s);
+        case 8: return launch_engine_gv<8, 1>(e, staged, ctas_per_sm, s);
+        case 16: return launch_engine_gv<16, 1>(e, staged, ctas_per_sm, s);
+        case 32: return launch_engine_gv<32, 1>(e, staged, ctas_per_sm, s);
         default: return cudaErrorInvalidValue;
     }
 }

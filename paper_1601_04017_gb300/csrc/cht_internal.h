@@ -87,7 +87,10 @@ struct EngineArgs {
     int inject_stall;          // testing: the first chunk waits for a count nothing reaches
 };
 
-cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, cudaStream_t s);
+// staged: copy each work item's keys / values through shared memory (else
+// the probe loops access the batch arrays in place).
+cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, bool staged,
+                          cudaStream_t s);
 
 }  // namespace cht
 

@@ -79,9 +79,41 @@ __device__ __forceinline__ int modify_at(Cell* cp, bool is_key, u64 key, u64 d) 
 // registers (every lane of the warp must call it).  kCoherent: finds read the
 // table through L2 like the modifying modes (required when the same kernel
 // launch also modifies the table); otherwise finds use the read-only path.
-template <int G, int V, int MODE, bool kCoherent = false>
+// Where a warp takes its keys / values and puts its results: the batch's
+// arrays in global memory, or (kStaged) a per-warp area in shared memory that
+// holds operations [base, base + count) -- the engine fills it with one
+// coalesced pass and writes the results back with one, which matters when
+// the arrays live in host memory across NVLink-C2C.
+struct WarpStage {
+    u64* keys;
+    u64* vals;
+    u64* vout;
+    unsigned char* codes;
+    u64 base;
+};
+
+template <bool kStaged>
+__device__ __forceinline__ u64 op_key(const OpArgs& a, const WarpStage& sg, u64 idx) {
+    return kStaged ? sg.keys[idx - sg.base] : ld_stream(a.keys + idx);
+}
+template <bool kStaged>
+__device__ __forceinline__ u64 op_val(const OpArgs& a, const WarpStage& sg, u64 idx) {
+    return kStaged ? sg.vals[idx - sg.base] : ld_stream(a.vals + idx);
+}
+template <bool kStaged>
+__device__ __forceinline__ void op_code(const OpArgs& a, const WarpStage& sg, u64 idx, unsigned char c) {
+    if (kStaged) sg.codes[idx - sg.base] = c;
+    else if (a.codes) a.codes[idx] = c;
+}
+template <bool kStaged>
+__device__ __forceinline__ void op_vout(const OpArgs& a, const WarpStage& sg, u64 idx, u64 v) {
+    if (kStaged) sg.vout[idx - sg.base] = v;
+    else a.vals_out[idx] = v;
+}
+
+template <int G, int V, int MODE, bool kCoherent = false, bool kStaged = false>
 __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 end, u64& n_ins, u64& n_del,
-                                         u32& sbits) {
+                                         u32& sbits, const WarpStage& sg = WarpStage{}) {
     constexpr u32 W = G * V;
     constexpr u32 FULL = 0xffffffffu;
     constexpr bool kModify = MODE != kFind;
@@ -108,12 +140,12 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                 const u64 my = next + __popc(idle & below_group);
                 if (my < end) {
                     idx = my;
-                    key = ld_stream(a.keys + idx);
-                    if (kHasVals) d = ld_stream(a.vals + idx);
+                    key = op_key<kStaged>(a, sg, idx);
+                    if (kHasVals) d = op_val<kStaged>(a, sg, idx);
                     if (is_reserved(key)) {
                         if (gl == 0) {
-                            if (a.codes) a.codes[idx] = kCodeReserved;
-                            if (MODE == kFind) a.vals_out[idx] = 0;
+                            op_code<kStaged>(a, sg, idx, kCodeReserved);
+                            if (MODE == kFind) op_vout<kStaged>(a, sg, idx, 0);
                         }
                         sbits |= kReserved;
                     } else {
@@ -155,7 +187,7 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                     if (MODE == kIouAdd) d = __shfl_sync(FULL, d, g0);
                 }
                 if (dup) {
-                    if (gl == 0 && a.codes) a.codes[idx] = kNo;
+                    if (gl == 0) op_code<kStaged>(a, sg, idx, kNo);
                     active = false;
                 }
             }
@@ -208,8 +240,8 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
         if (active && ghit >= 0) {
             if (MODE == kFind) {
                 if (gl == 0) {
-                    a.vals_out[idx] = gmatch ? gval : 0;
-                    if (a.codes) a.codes[idx] = gmatch ? kYes : kNo;
+                    op_vout<kStaged>(a, sg, idx, gmatch ? gval : 0);
+                    op_code<kStaged>(a, sg, idx, gmatch ? kYes : kNo);
                 }
                 active = false;
             } else if (gl == 0) {
@@ -228,7 +260,7 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                     pos = (base + u32(ghit) + 1) & cmask;
                 } else {
                     if (gl == 0) {
-                        if (a.codes) a.codes[idx] = (unsigned char)outcome;
+                        op_code<kStaged>(a, sg, idx, (unsigned char)outcome);
                         if (outcome == kStepDoneYes) {
                             if (MODE == kErase) ++n_del;
                             else ++n_ins;
@@ -241,12 +273,12 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                 // every cell was examined without a decision
                 if (gl == 0) {
                     if (MODE == kFind) {
-                        a.vals_out[idx] = 0;
-                        if (a.codes) a.codes[idx] = kNo;
+                        op_vout<kStaged>(a, sg, idx, 0);
+                        op_code<kStaged>(a, sg, idx, kNo);
                     } else if (MODE == kErase) {
-                        if (a.codes) a.codes[idx] = kNo;
+                        op_code<kStaged>(a, sg, idx, kNo);
                     } else {
-                        if (a.codes) a.codes[idx] = kCodeFull;
+                        op_code<kStaged>(a, sg, idx, kCodeFull);
                     }
                 }
                 if (MODE != kFind && MODE != kErase) sbits |= kFull;

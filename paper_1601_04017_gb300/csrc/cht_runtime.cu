@@ -748,7 +748,7 @@ struct cht_plan {
     u32* d_status = nullptr;
     u64 n_batches = 0, n_chunks = 0;
     u64 bytes_tables = 0, bytes_batches = 0, bytes_chunks = 0, bytes_counters = 0;
-    cht_plan_config cfg{0, 0, 0, 0, 0};
+    cht_plan_config cfg{0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -787,7 +787,7 @@ cht_status plan_run(cht_plan* p, cudaStream_t s) {
     if (cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s) != cudaSuccess) return CHT_ERR_CUDA;
     const int g = p->cfg.group_width > 0 ? p->cfg.group_width : 1;
     const int v = g == 1 ? 2 : (p->cfg.lane_cells > 0 ? p->cfg.lane_cells : 1);
-    return cuda_status(cht::launch_engine(plan_args(p), g, v, p->cfg.ctas_per_sm, s));
+    return cuda_status(cht::launch_engine(plan_args(p), g, v, p->cfg.ctas_per_sm, p->cfg.direct_io == 0, s));
 }
 
 }  // namespace
@@ -878,11 +878,12 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
 
 cht_status cht_plan_set_config(cht_plan_handle p, const cht_plan_config* cfg) {
     if (!p) return CHT_ERR_INVALID_ARG;
-    cht_plan_config c = cfg ? *cfg : cht_plan_config{0, 0, 0, 0, 0};
+    cht_plan_config c = cfg ? *cfg : cht_plan_config{0, 0, 0, 0, 0, 0};
     const int g = c.group_width;
     if (!(g == 0 || g == 1 || g == 4 || g == 8 || g == 16 || g == 32)) return CHT_ERR_INVALID_ARG;
     if (c.lane_cells < 0 || c.lane_cells > 2 || (g == 32 && c.lane_cells == 2)) return CHT_ERR_INVALID_ARG;
-    if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64 || c.spin_limit_us < 0 || c.fault_inject < 0 || c.fault_inject > 1)
+    if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64 || c.spin_limit_us < 0 || c.fault_inject < 0 || c.fault_inject > 1 ||
+        c.direct_io < 0 || c.direct_io > 1)
         return CHT_ERR_INVALID_ARG;
     p->cfg = c;
     return CHT_OK;
@@ -954,9 +955,10 @@ cht_status cht_plan_autotune(cht_plan_handle p, cht_stream_t stream, double* bes
     };
     const cht_plan_config keep = p->cfg;
     struct Cand {
-        int g, v, ctas;
+        int g, v, ctas, direct;
     };
-    const Cand cands[] = {{1, 2, 0}, {4, 2, 0}, {8, 2, 0}, {4, 1, 0}, {8, 1, 0}, {16, 1, 0}, {32, 1, 0}, {1, 2, 2}};
+    const Cand cands[] = {{1, 2, 0, 0}, {4, 2, 0, 0}, {8, 2, 0, 0},  {4, 1, 0, 0},  {8, 1, 0, 0},
+                          {16, 1, 0, 0}, {32, 1, 0, 0}, {1, 2, 2, 0}, {1, 2, 0, 1}, {4, 2, 0, 1}};
     double best = 1e30;
     cht_plan_config best_cfg = keep;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -967,6 +969,7 @@ cht_status cht_plan_autotune(cht_plan_handle p, cht_stream_t stream, double* bes
         p->cfg.group_width = c.g;
         p->cfg.lane_cells = c.v;
         p->cfg.ctas_per_sm = c.ctas;
+        p->cfg.direct_io = c.direct;
         float ms = 0;
         if (cudaEventRecord(e0, s) != cudaSuccess) r = CHT_ERR_CUDA;
         if (r == CHT_OK) r = plan_run(p, s);

@@ -22,9 +22,11 @@
 // plus the whole request (bulk pre-sizing, Sec. 4.5; tombstones are dropped,
 // Sec. 4.4).  The migration is ordered on the stream after the steps in
 // flight, so admission never waits for counts.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <deque>
+#include <initializer_list>
 #include <list>
 #include <new>
 #include <vector>
@@ -79,6 +81,9 @@ struct Part {
 struct Step {
     std::vector<Part> parts;
     cudaEvent_t ev = nullptr;
+    // timing: start of the step's device work (migrations, copies), engine
+    // launch start / end; the step ends at `ev`
+    cudaEvent_t t_begin = nullptr, t_eng0 = nullptr, t_eng1 = nullptr;
     u64 arena_end = 0, meta_end = 0, dmeta_end = 0;
     std::vector<u32> touched;
     std::vector<u64> new_cells;          // per touched table
@@ -121,7 +126,9 @@ struct cht_server {
     std::vector<u64> known_I, known_D, pending_new;
     std::vector<u32> parts_inflight;
     std::vector<cudaEvent_t> spare_events;
+    std::vector<cudaEvent_t> spare_timers;
     u64 steps = 0, completed = 0;
+    cht_server_profile prof{};
     bool pageable_ok = false;  // device can address pageable host memory
 };
 
@@ -162,10 +169,17 @@ cht_status poll(cht_server* s, u32* completed_now) {
             s->pending_new[t_] -= st.new_cells[k];
             cht::table_set_bound(s->tables[t_], s->known_I[t_] + s->pending_new[t_], s->pending_new[t_] == 0);
         }
+        float ms_step = 0, ms_eng = 0;
+        if (cudaEventElapsedTime(&ms_step, st.t_begin, st.ev) == cudaSuccess) s->prof.gpu_step_ms += ms_step;
+        if (cudaEventElapsedTime(&ms_eng, st.t_eng0, st.t_eng1) == cudaSuccess) s->prof.engine_ms += ms_eng;
+        cudaGetLastError();
         s->aring.tail = st.arena_end;
         s->mring.tail = st.meta_end;
         s->dring.tail = st.dmeta_end;
         s->spare_events.push_back(st.ev);
+        s->spare_timers.push_back(st.t_begin);
+        s->spare_timers.push_back(st.t_eng0);
+        s->spare_timers.push_back(st.t_eng1);
         s->inflight.pop_front();
     }
     if (completed_now) *completed_now = done;
@@ -173,10 +187,44 @@ cht_status poll(cht_server* s, u32* completed_now) {
 }
 
 // Admit what fits and launch one step.  *admitted = requests (or parts) in it.
+cudaEvent_t take_timer(cht_server* s) {
+    cudaEvent_t e = nullptr;
+    if (!s->spare_timers.empty()) {
+        e = s->spare_timers.back();
+        s->spare_timers.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
 cht_status admit_and_launch(cht_server* s, u32* admitted) {
     *admitted = 0;
     if (s->inflight.size() >= s->cfg.max_inflight_steps || s->queue.empty()) return CHT_OK;
     const size_t nt = s->tables.size();
+    Step st;
+    st.t_begin = take_timer(s);
+    st.t_eng0 = take_timer(s);
+    st.t_eng1 = take_timer(s);
+    if (!st.t_begin || !st.t_eng0 || !st.t_eng1) {
+        for (cudaEvent_t e : {st.t_begin, st.t_eng0, st.t_eng1})
+            if (e) s->spare_timers.push_back(e);
+        return CHT_ERR_CUDA;
+    }
+    // the timers go back to the spare list unless a step takes them
+    struct TimerGuard {
+        cht_server* s;
+        Step* st;
+        ~TimerGuard() {
+            if (st && st->t_begin) {
+                s->spare_timers.push_back(st->t_begin);
+                s->spare_timers.push_back(st->t_eng0);
+                s->spare_timers.push_back(st->t_eng1);
+            }
+        }
+    } guard{s, &st};
+    if (cudaEventRecord(st.t_begin, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
     std::vector<char> blocked(nt, 0);
     std::vector<u64> step_new(nt, 0);
     std::vector<Part> parts;
@@ -222,6 +270,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
                 }
                 cht_status r = cht::table_migrate_to(h, nl, ~0ull, s->stream);
                 if (r != CHT_OK) return r;
+                ++s->prof.migrations;
             }
         }
         if (rq.direct) {  // the engine reads / writes the request's arrays in place
@@ -340,9 +389,20 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
     e.status = reinterpret_cast<u32*>(e.done + nt);
     e.spin_limit = 2000000000ll;
     e.inject_stall = 0;
-    if (cht::launch_engine(e, 1, 2, 0, s->stream) != cudaSuccess) {
+    if (cudaEventRecord(st.t_eng0, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
+    if (cht::launch_engine(e, 1, 2, 0, true, s->stream) != cudaSuccess) {
         cudaGetLastError();
         return CHT_ERR_CUDA;
+    }
+    if (cudaEventRecord(st.t_eng1, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
+    {
+        // longest chain of dependent batches in this step (= its rounds)
+        std::vector<u32> per_table(nt, 0);
+        u32 rounds = 0;
+        for (const cht::EngineBatch& b : batches) rounds = std::max(rounds, ++per_table[b.table]);
+        s->prof.rounds += rounds;
+        s->prof.chunks += chunks.size();
+        s->prof.parts += batches.size();
     }
     // staged results back to the caller's arrays
     for (const Part& p : parts) {
@@ -355,7 +415,6 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
             cudaMemcpyAsync(rq.r.codes + p.off, p.d_codes, p.n, cudaMemcpyDefault, s->stream) != cudaSuccess)
             return CHT_ERR_CUDA;
     }
-    Step st;
     st.snap = reinterpret_cast<unsigned long long*>(hm + o_snap);
     for (size_t k = 0; k < touched.size(); ++k) {
         // DevState starts with I then D
@@ -379,6 +438,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
     *admitted = u32(parts.size());
     st.parts = std::move(parts);
     s->inflight.push_back(std::move(st));
+    guard.st = nullptr;  // the step in flight owns its timers now
     ++s->steps;
     return CHT_OK;
 }
@@ -485,7 +545,9 @@ cht_status cht_server_step(cht_server_handle s, uint32_t* admitted, uint32_t* co
     if (prev != s->device) cudaSetDevice(s->device);
     u32 c = 0, a = 0;
     cht_status r = poll(s, &c);
+    const double h0 = now_s();
     if (r == CHT_OK) r = admit_and_launch(s, &a);
+    if (a) s->prof.host_admit_ms += (now_s() - h0) * 1e3;
     if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
     if (admitted) *admitted = a;
     if (completed) *completed = c;
@@ -547,12 +609,22 @@ cht_status cht_server_stats(cht_server_handle s, uint64_t* steps, uint64_t* comp
     return CHT_OK;
 }
 
+cht_status cht_server_get_profile(cht_server_handle s, cht_server_profile* out) {
+    if (!s || !out) return CHT_ERR_INVALID_ARG;
+    *out = s->prof;
+    out->steps = s->steps;
+    out->completed = s->completed;
+    return CHT_OK;
+}
+
 cht_status cht_server_destroy(cht_server_handle s) {
     if (!s) return CHT_ERR_INVALID_ARG;
     if (s->stream || !s->inflight.empty()) cudaStreamSynchronize(s->stream);
     for (Step& st : s->inflight)
-        if (st.ev) cudaEventDestroy(st.ev);
+        for (cudaEvent_t e : {st.ev, st.t_begin, st.t_eng0, st.t_eng1})
+            if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->spare_timers) cudaEventDestroy(e);
     if (s->arena) cht::runtime_free(s->arena, s->cfg.arena_bytes, s->stream);
     if (s->dmeta) cht::runtime_free(s->dmeta, s->meta_bytes, s->stream);
     if (s->meta) cudaFreeHost(s->meta);

@@ -75,12 +75,12 @@ def _check(wl, keys, tables, vout, codes, otabs, ovout, ocodes):
         assert np.array_equal(gk[i], ok[j]) and np.array_equal(gv[i], ov[j])
 
 
-@pytest.mark.parametrize("g,v", [(0, 0), (4, 2), (8, 1), (32, 1)])
-def test_engine_matches_oracle(cuda_lib, oracle_mod, g, v):
+@pytest.mark.parametrize("g,v,direct", [(0, 0, 0), (4, 2, 0), (8, 1, 0), (32, 1, 0), (0, 0, 1), (4, 2, 1)])
+def test_engine_matches_oracle(cuda_lib, oracle_mod, g, v, direct):
     wl = W.batched_workload(48, 6, 11, seed=31)
     tables, ops, vout, codes = _setup(cuda_lib, wl)
     plan = cuda_lib.Plan(ops)
-    plan.set_config(group_width=g, lane_cells=v)
+    plan.set_config(group_width=g, lane_cells=v, direct_io=direct)
     plan.launch()
     assert plan.status() == 0
     otabs, keys, ovout, ocodes = _oracle(oracle_mod, wl)

@@ -83,6 +83,12 @@ def test_server_mix_equals_alone(cuda_lib, inflight, stage):
     assert (lat > 0).all() and makespan > 0
     steps, done = srv.stats()
     assert done == len(reqs) and steps >= 2
+    prof = srv.profile()
+    assert prof["steps"] == steps and prof["completed"] == done
+    assert prof["parts"] >= len(reqs) and prof["chunks"] >= prof["parts"]
+    assert steps <= prof["rounds"] <= prof["parts"]
+    assert 0 < prof["engine_ms"] <= prof["gpu_step_ms"] <= makespan * 1e3
+    assert prof["migrations"] > 0  # the 64-cell tables had to grow
     alone_tabs, a_vout, a_codes = _single_calls(cuda_lib, wl, keys, vals, caps)
     _compare(wl, keys, tables, vout, codes, alone_tabs, a_vout, a_codes)
     srv.destroy()
