@@ -227,7 +227,13 @@ typedef struct cht_plan *cht_plan_handle;
  * direct_io: 0 = each warp copies its work item's keys and values into
  * shared memory with one coalesced pass and writes results back with one
  * (the default), 1 = the probe loops read and write the batch arrays in
- * place. */
+ * place; chunk_ops: operations per work item, 32 / 64 / 128 / 256, or 0 =
+ * per table: 256 unless the table's chain of dependent batches would
+ * outlast the plan's other work, then smaller (more warps per batch);
+ * poll_ns: longest sleep of a waiting work item between two polls of its
+ * table's completion counter (0 = 8192 ns; the sleep is 16 ns per item still
+ * awaited, at least 128 ns; longer = less traffic on that counter, later
+ * wake-up). */
 typedef struct {
     int group_width;
     int lane_cells;
@@ -235,13 +241,18 @@ typedef struct {
     int spin_limit_us;
     int fault_inject;
     int direct_io;
+    int chunk_ops;
+    int poll_ns;
 } cht_plan_config;
 
 #define CHT_PLAN_TIMEOUT 0x1u
 
 /* Build a plan from n_ops batch descriptors (copied; the arrays they point to
  * are not).  Validates every descriptor (host arrays are rejected with
- * CHT_ERR_INVALID_ARG).  Allocates the plan's device buffers. */
+ * CHT_ERR_INVALID_ARG).  The engine reads a work item's keys and values
+ * before the work it depends on has finished, so no batch's keys / vals may
+ * overlap any batch's vals_out / codes (CHT_ERR_INVALID_ARG otherwise).
+ * Allocates the plan's device buffers. */
 cht_status cht_plan_create(const cht_batch_op *ops, uint64_t n_ops, cht_plan_handle *out);
 cht_status cht_plan_set_config(cht_plan_handle p, const cht_plan_config *cfg);
 cht_status cht_plan_get_config(cht_plan_handle p, cht_plan_config *cfg);
@@ -291,6 +302,9 @@ typedef struct {
                                     arena; 1: stage every request through the arena */
 } cht_server_config;
 
+/* A request's arrays must stay alive and unchanged until it completes, and
+ * its keys / vals must not overlap the vals_out / codes of any request in
+ * flight (the engine reads inputs ahead of the work they wait for). */
 typedef struct {
     uint32_t table;          /* index into the server's table list */
     int op;                  /* cht_op_kind */

@@ -78,7 +78,8 @@ class ServerProfile(ctypes.Structure):
 
 class PlanConfig(ctypes.Structure):
     _fields_ = [("group_width", ctypes.c_int), ("lane_cells", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("spin_limit_us", ctypes.c_int), ("fault_inject", ctypes.c_int), ("direct_io", ctypes.c_int)]
+                ("spin_limit_us", ctypes.c_int), ("fault_inject", ctypes.c_int), ("direct_io", ctypes.c_int),
+                ("chunk_ops", ctypes.c_int), ("poll_ns", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -321,7 +322,8 @@ class Plan:
 
     `ops` is a list of (table, op, keys, vals, vals_out, codes) tuples with CUDA
     tensors (vals / vals_out / codes may be None where unused).  Batches on the
-    same table run in list order; the arrays must stay alive with the plan.
+    same table run in list order; the arrays must stay alive with the plan,
+    and no keys / vals array may overlap a vals_out / codes array.
     """
 
     def __init__(self, ops):

@@ -20,16 +20,30 @@
 // Coherence: a later chunk of a table may run on another SM right after an
 // earlier one modified the table, so every table read in the engine goes
 // through L2 (finds included); writers fence before they count a chunk done
-// and waiters load the counter with acquire semantics.
+// and a waiter fences after it has seen the count it needs.
 //
-// Staged I/O (the default): a warp copies its chunk's keys and values, in
-// windows of kStageOps operations, into its own shared-memory area with one
-// coalesced pass, runs the probe loop from there and writes the found values
-// and result codes back with one coalesced pass.  The probe loop itself
-// touches the request arrays one scattered element at a time; when those
-// arrays are in host memory (a serving loop reading requests in place across
-// NVLink-C2C) every such access is a separate round trip, and staging turns
-// them into a few full-width transfers per window.
+// Staged I/O (the default): a warp copies its chunk's keys and values into
+// its own shared-memory area with one coalesced pass, runs the probe loop
+// from there and writes the found values and result codes back with one
+// coalesced pass.  The probe loop itself touches the request arrays one
+// scattered element at a time; when those arrays are in host memory (a
+// serving loop reading requests in place across NVLink-C2C) every such
+// access is a separate round trip, and staging turns them into a few
+// full-width transfers.  The copy-in happens before the dependency wait
+// (inputs are never written by the plan), so on a chain of dependent
+// batches -- one hot table's requests in arrival order -- its latency is off
+// the critical path.
+//
+// Waiting: many warps can wait on the same table's counter (they take items
+// far ahead of the level in progress).  Each polls with a plain relaxed load
+// and sleeps in between for 16 ns per item it still waits for (at least
+// 128 ns, at most max_backoff_ns): warps whose turn is near poll often, the
+// many far behind them rarely, so the counter's L2 line is not flooded
+// while the warps it waits for are updating it.
+//
+// Groups: a chain of small dependent batches (levels of one item each) is
+// run by one warp in order -- no hand-off through the counter between them,
+// which costs a few microseconds per level.
 #include <atomic>
 
 #include "cht_ops.cuh"
@@ -40,22 +54,21 @@ namespace {
 constexpr u32 kEngineTimeout = 1u;
 constexpr u32 kEngineAbort = 2u;
 
-__device__ __forceinline__ u64 ld_acquire_u64(const unsigned long long* p) {
+__device__ __forceinline__ u64 ld_relaxed_u64(const unsigned long long* p) {
     u64 v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ void red_release_add(unsigned long long* p, u64 v) {
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Operations per staging window and the shared memory one warp uses for it:
-// keys, values (find results reuse this array: finds read no values) and
-// one result byte per operation.
-constexpr u32 kStageOps = 128;
-constexpr u32 kStageWarpBytes = kStageOps * (8 + 8 + 1);
-static_assert(kChunkOps % kStageOps == 0, "a chunk is a whole number of windows");
+// Shared memory one warp uses to stage a chunk: keys, values (find results
+// reuse this array: finds read no values) and one result byte per operation.
+constexpr u32 kStageWarpBytes = kChunkOps * (8 + 8 + 1);
 static_assert(kStageWarpBytes % 8 == 0, "warp areas stay 8-byte aligned");
 
 template <int G, int V, int MODE, bool kStaged>
@@ -78,6 +91,58 @@ __device__ __forceinline__ void engine_run(int mode, const OpArgs& a, u64 first,
     }
 }
 
+// Copy one item's keys (and values) into the warp's staging area.
+__device__ __forceinline__ void stage_in(const EngineChunk& ch, const EngineBatch& b, const WarpStage& sg, int lane) {
+    const bool has_vals = b.mode == kInsert || b.mode == kIouAdd || b.mode == kIouOverwrite;
+    for (u32 j = lane; j < ch.count; j += 32) {
+        sg.keys[j] = ld_stream(b.keys + ch.start + j);
+        if (has_vals) sg.vals[j] = ld_stream(b.vals + ch.start + j);
+    }
+}
+
+// Run one item whose dependencies are met and write its results.  With
+// `count` > 0 the item then counts itself and the `count` - 1 items before
+// it in its group done for its table; with 0 (an item inside a group) the
+// next item of the group, run by this same warp, only needs this warp's
+// lanes to agree on memory order, which __syncwarp gives.
+template <int G, int V, bool kStaged>
+__device__ __forceinline__ void run_item(const EngineArgs& e, const EngineChunk& ch, const EngineBatch& b,
+                                         const EngineTable& t, WarpStage& sg, int lane, u32 count) {
+    OpArgs a;
+    a.cells = t.cells;
+    a.log2c = t.log2c;
+    a.keys = b.keys;
+    a.vals = b.vals;
+    a.vals_out = b.vals_out;
+    a.codes = b.codes;
+    a.n = b.n;
+    a.st = t.st;
+    const u64 end = ch.start + ch.count;
+    u64 n_ins = 0, n_del = 0;
+    u32 sbits = 0;
+    if (kStaged) {
+        sg.base = ch.start;
+        engine_run<G, V, true>(b.mode, a, ch.start, end, n_ins, n_del, sbits, sg);
+    } else {
+        engine_run<G, V, false>(b.mode, a, ch.start, end, n_ins, n_del, sbits, sg);
+    }
+    // Count the items done as soon as the table writes are ordered: the
+    // results (found values, codes -- possibly in host memory) and the
+    // table's counters are read only after the launch, so they are written
+    // after the release and stay out of the fence's wait.
+    if (count) fence_acq_rel_gpu();  // this lane's table writes before the items are counted
+    __syncwarp();
+    if (count && lane == 0) red_release_add(e.done + b.table, u64(count));
+    if (kStaged) {
+        for (u32 j = lane; j < ch.count; j += 32) {
+            if (b.mode == kFind) b.vals_out[ch.start + j] = sg.vout[j];
+            if (b.codes) b.codes[ch.start + j] = sg.codes[j];
+        }
+    }
+    warp_flush_counters(t.st, n_ins, n_del, sbits);
+    __syncwarp();  // the next item overwrites this one's staging area
+}
+
 template <int G, int V, bool kStaged>
 __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
     constexpr u32 FULL = 0xffffffffu;
@@ -87,9 +152,9 @@ __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
     if (kStaged) {
         unsigned char* w = engine_smem + (threadIdx.x >> 5) * kStageWarpBytes;
         sg.keys = reinterpret_cast<u64*>(w);
-        sg.vals = sg.keys + kStageOps;
+        sg.vals = sg.keys + kChunkOps;
         sg.vout = sg.vals;
-        sg.codes = reinterpret_cast<unsigned char*>(sg.vals + kStageOps);
+        sg.codes = reinterpret_cast<unsigned char*>(sg.vals + kChunkOps);
     }
     for (;;) {
         u64 c = 0;
@@ -100,23 +165,27 @@ __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
         const EngineChunk ch = e.chunks[c];
         const EngineBatch b = e.batches[ch.batch];
         const EngineTable t = e.tables[b.table];
-        // wait for every chunk of this table's earlier batches
+        if (kStaged) stage_in(ch, b, sg, lane);
+        // wait for every item of this table's earlier levels; the sleep
+        // between polls grows with the number of items still missing
         int ok = 1;
         if (lane == 0) {
             u64 need = ch.need;
             if (e.inject_stall && c == 0) need = ~0ull;  // testing: a count nothing reaches
-            if (ld_acquire_u64(e.done + b.table) < need) {
+            u64 seen = ld_relaxed_u64(e.done + b.table);
+            if (seen < need) {
                 const long long t0 = clock64();
-                while (ld_acquire_u64(e.done + b.table) < need) {
-                    if (clock64() - t0 > e.spin_limit) {
+                for (;;) {
+                    const u64 gap = need - seen;
+                    const u64 ns = gap > e.max_backoff_ns / 16 ? e.max_backoff_ns : gap * 16 < 128 ? 128 : gap * 16;
+                    __nanosleep(unsigned(ns));
+                    seen = ld_relaxed_u64(e.done + b.table);
+                    if (seen >= need) break;
+                    if (clock64() - t0 > e.spin_limit ||
+                        (*reinterpret_cast<volatile u32*>(e.status) & kEngineAbort)) {
                         ok = 0;
                         break;
                     }
-                    if (*reinterpret_cast<volatile u32*>(e.status) & kEngineAbort) {
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(64);
                 }
             }
         }
@@ -125,44 +194,20 @@ __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
             if (lane == 0) atomicOr(e.status, kEngineTimeout | kEngineAbort);
             break;
         }
-        __threadfence();  // order this warp's table reads after the acquire
-        OpArgs a;
-        a.cells = t.cells;
-        a.log2c = t.log2c;
-        a.keys = b.keys;
-        a.vals = b.vals;
-        a.vals_out = b.vals_out;
-        a.codes = b.codes;
-        a.n = b.n;
-        a.st = t.st;
-        const u64 end = ch.start + ch.count;
-        const bool has_vals = b.mode == kInsert || b.mode == kIouAdd || b.mode == kIouOverwrite;
-        u64 n_ins = 0, n_del = 0;
-        u32 sbits = 0;
-        if (kStaged) {
-            for (u64 w0 = ch.start; w0 < end; w0 += kStageOps) {
-                const u32 cnt = u32(end - w0 < kStageOps ? end - w0 : kStageOps);
-                sg.base = w0;
-                for (u32 j = lane; j < cnt; j += 32) {
-                    sg.keys[j] = ld_stream(b.keys + w0 + j);
-                    if (has_vals) sg.vals[j] = ld_stream(b.vals + w0 + j);
-                }
+        fence_acq_rel_gpu();  // lane 0: table reads after the count it saw ...
+        __syncwarp();         // ... and the other lanes' reads after lane 0's fence
+        run_item<G, V, kStaged>(e, ch, b, t, sg, lane, ch.nfollow ? 0u : 1u);
+        // the group this item leads: later levels of the same table, in
+        // order; the whole group is counted done by its last item
+        for (u32 f = 0; f < ch.nfollow; ++f) {
+            const EngineChunk fc = e.chunks[ch.follow_first + f];
+            const EngineBatch fb = e.batches[fc.batch];
+            if (kStaged) {
+                stage_in(fc, fb, sg, lane);
                 __syncwarp();
-                engine_run<G, V, true>(b.mode, a, w0, w0 + cnt, n_ins, n_del, sbits, sg);
-                __syncwarp();
-                for (u32 j = lane; j < cnt; j += 32) {
-                    if (b.mode == kFind) b.vals_out[w0 + j] = sg.vout[j];
-                    if (b.codes) b.codes[w0 + j] = sg.codes[j];
-                }
-                __syncwarp();  // the next window overwrites this one's area
             }
-        } else {
-            engine_run<G, V, false>(b.mode, a, ch.start, end, n_ins, n_del, sbits, sg);
+            run_item<G, V, kStaged>(e, fc, fb, t, sg, lane, f + 1 == ch.nfollow ? ch.nfollow + 1u : 0u);
         }
-        warp_flush_counters(t.st, n_ins, n_del, sbits);
-        __threadfence();  // this lane's table writes before the chunk is counted
-        __syncwarp();
-        if (lane == 0) red_release_add(e.done + b.table, 1ull);
     }
 }
 

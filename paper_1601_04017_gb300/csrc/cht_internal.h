@@ -68,22 +68,32 @@ struct EngineBatch {
     u32 mode;   // Mode
 };
 
+// One work item: operations [start, start + count) of one batch.  A queue
+// item may lead a group: the warp that runs it then runs `nfollow` more
+// items of the same table, chunks[follow_first ..], in order and without
+// waiting (each is a later dependency level of that table, so program order
+// is the ordering it needs).  Followers sit after the queue in the array.
 struct EngineChunk {
     u64 start;  // first operation of the batch in this chunk
-    u64 need;   // chunks of the table's earlier batches that must be done first
+    u64 need;   // items of the table's earlier levels that must be done first
     u32 batch;
-    u32 count;
+    uint16_t count;
+    uint16_t nfollow;
+    u32 follow_first;
+    u32 pad;
 };
+static_assert(sizeof(EngineChunk) == 32, "work items are 32 bytes");
 
 struct EngineArgs {
     const EngineTable* tables;
     const EngineBatch* batches;
     const EngineChunk* chunks;
-    u64 n_chunks;
+    u64 n_chunks;  // queue items (followers come after them)
     unsigned long long* next;  // work-queue cursor (zero before a launch)
     unsigned long long* done;  // per table: completed chunks (zero before a launch)
     u32* status;               // engine status bits (zero before a launch)
     long long spin_limit;      // bound of one dependency wait, in clock cycles
+    unsigned max_backoff_ns;   // longest sleep between two polls of a dependency counter
     int inject_stall;          // testing: the first chunk waits for a count nothing reaches
 };
 
@@ -101,8 +111,15 @@ cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, 
 namespace cht {
 
 // Order batches into engine work items round by round (round r = every
-// table's r-th batch); `need` of an item = its table's items in earlier rounds.
-void plan_order(const std::vector<EngineBatch>& batches, size_t n_tables, std::vector<EngineChunk>& chunks);
+// table's r-th batch).  `need` of an item = its table's items in earlier
+// dependency levels (a run of consecutive finds on a table is one level).
+// Consecutive levels of one table that are one item each are grouped: the
+// first is a queue item that leads the rest.  chunk_ops: operations per
+// item (32..256, a power of two), 0 = sized per table from the length of
+// its chain of levels.  Returns the number of queue items; `chunks` holds
+// them followed by the followers.
+u64 plan_order(const std::vector<EngineBatch>& batches, size_t n_tables, int chunk_ops,
+               std::vector<EngineChunk>& chunks);
 
 // Runtime services for translation units outside the runtime.
 struct TableInfo {

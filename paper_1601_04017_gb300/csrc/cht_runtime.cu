@@ -401,31 +401,147 @@ int sm_count() {
     return v;
 }
 
-void plan_order(const std::vector<EngineBatch>& batches, size_t n_tables, std::vector<EngineChunk>& chunks) {
+namespace {
+
+// Latency model of the engine used to size work items (chunk_ops = 0):
+// a chain of dependent batches (one table's batches in order) costs per
+// batch about kRoundUs (hand-off between warps, fences, the wait's
+// back-off) plus kLaneOpUs per operation a lane handles in sequence
+// (ceil(chunk / 32) with one lane per key); independent work runs at about
+// kOpsPerUs.  A table whose chain at 256-operation items would outlast the
+// whole plan's work gets smaller items (more warps per batch, fewer
+// operations in sequence per lane) -- as small as needed, at least 32.
+constexpr double kRoundUs = 4.0;
+constexpr double kLaneOpUs = 0.8;
+constexpr double kOpsPerUs = 30000.0;
+// Longest run of one-item levels one warp runs in sequence.
+constexpr u32 kMaxGroup = 4096;
+
+double chain_us(const std::vector<u64>& sizes, u32 chunk) {
+    double t = 0;
+    for (u64 n : sizes) t += kRoundUs + kLaneOpUs * double((std::min<u64>(n, chunk) + 31) / 32);
+    return t;
+}
+
+}  // namespace
+
+u64 plan_order(const std::vector<EngineBatch>& batches, size_t n_tables, int chunk_ops,
+               std::vector<EngineChunk>& chunks) {
+    // Per table: a batch's dependency level.  A find right after a find of
+    // the same table does not wait for it (finds do not modify the table, so
+    // both see the state after the last modifying batch): it joins the
+    // level of the run of finds it belongs to.
     std::vector<u32> rounds(n_tables, 0), round_of(batches.size());
-    for (size_t b = 0; b < batches.size(); ++b) round_of[b] = rounds[batches[b].table]++;
+    std::vector<u32> level_of(batches.size()), levels(n_tables, 0);
+    std::vector<char> last_find(n_tables, 0);
+    std::vector<std::vector<u64>> level_ops(n_tables);     // largest batch per level
+    std::vector<std::vector<u32>> level_first(n_tables);   // first batch of each level
+    std::vector<std::vector<u32>> level_batches(n_tables); // batches per level
+    for (size_t b = 0; b < batches.size(); ++b) {
+        const u32 t = batches[b].table;
+        round_of[b] = rounds[t]++;
+        const bool find = batches[b].mode == kFind;
+        if (!(find && last_find[t])) {
+            ++levels[t];
+            level_ops[t].push_back(0);
+            level_first[t].push_back(u32(b));
+            level_batches[t].push_back(0);
+        }
+        level_of[b] = levels[t] - 1;
+        level_ops[t].back() = std::max(level_ops[t].back(), batches[b].n);
+        ++level_batches[t].back();
+        last_find[t] = find;
+    }
+    // work-item size per table
+    std::vector<u32> chunk_of(n_tables, kChunkOps);
+    if (chunk_ops > 0) {
+        std::fill(chunk_of.begin(), chunk_of.end(), u32(chunk_ops));
+    } else {
+        u64 total = 0;
+        for (const EngineBatch& eb : batches) total += eb.n;
+        const double work_us = double(total) / kOpsPerUs;
+        for (size_t t = 0; t < n_tables; ++t) {
+            u32 c = kChunkOps;
+            while (c > 32 && chain_us(level_ops[t], c) > work_us) c /= 2;
+            chunk_of[t] = c;
+        }
+    }
+    // Groups: runs of consecutive one-item levels (one batch of at most one
+    // item).  group_len[t][l] = levels in the group that starts at level l
+    // (0 for the other levels of a group, 1 for a level on its own).
+    std::vector<std::vector<u32>> group_len(n_tables);
+    for (size_t t = 0; t < n_tables; ++t) {
+        const u32 nl = levels[t];
+        group_len[t].assign(nl, 1);
+        u32 l = 0;
+        while (l < nl) {
+            auto single = [&](u32 k) { return level_batches[t][k] == 1 && level_ops[t][k] <= chunk_of[t]; };
+            if (!single(l)) {
+                ++l;
+                continue;
+            }
+            u32 e = l + 1;
+            while (e < nl && single(e) && e - l < kMaxGroup) ++e;
+            group_len[t][l] = e - l;
+            for (u32 k = l + 1; k < e; ++k) group_len[t][k] = 0;
+            l = e;
+        }
+    }
     const u32 n_rounds = n_tables ? *std::max_element(rounds.begin(), rounds.end()) : 0;
     std::vector<std::vector<u32>> by_round(n_rounds);
     for (u32 b = 0; b < batches.size(); ++b) by_round[round_of[b]].push_back(b);
-    std::vector<u64> items_so_far(n_tables, 0);
+    // items of each table, counted as they are emitted (followers when their
+    // leader is); the items before a level are what its batches need
+    std::vector<u64> items_so_far(n_tables, 0), level_need(n_tables, 0);
+    std::vector<u32> cur_level(n_tables, ~0u);
+    std::vector<EngineChunk> followers;
     chunks.clear();
+    auto item = [](u64 start, u64 need, u32 b, u64 count) {
+        EngineChunk ch;
+        ch.start = start;
+        ch.need = need;
+        ch.batch = b;
+        ch.count = uint16_t(count);
+        ch.nfollow = 0;
+        ch.follow_first = 0;
+        ch.pad = 0;
+        return ch;
+    };
     for (u32 r = 0; r < n_rounds; ++r) {
-        std::vector<u64> need_now(by_round[r].size());
-        for (size_t k = 0; k < by_round[r].size(); ++k) need_now[k] = items_so_far[batches[by_round[r][k]].table];
-        for (size_t k = 0; k < by_round[r].size(); ++k) {
-            const u32 b = by_round[r][k];
+        for (const u32 b : by_round[r]) {
             const EngineBatch& eb = batches[b];
-            for (u64 s0 = 0; s0 < eb.n; s0 += kChunkOps) {
-                EngineChunk ch;
-                ch.start = s0;
-                ch.need = need_now[k];
-                ch.batch = b;
-                ch.count = u32(eb.n - s0 < kChunkOps ? eb.n - s0 : kChunkOps);
-                chunks.push_back(ch);
-                ++items_so_far[eb.table];
+            const u32 t = eb.table;
+            const u32 lv = level_of[b];
+            const u32 glen = group_len[t][lv];
+            if (glen == 0) continue;  // runs as a follower of its group's leader
+            if (lv != cur_level[t]) {  // a new level: wait for all earlier items
+                cur_level[t] = lv;
+                level_need[t] = items_so_far[t];
             }
+            if (glen > 1) {
+                EngineChunk lead = item(0, level_need[t], b, eb.n);
+                lead.nfollow = uint16_t(glen - 1);
+                lead.follow_first = u32(followers.size());  // made absolute below
+                chunks.push_back(lead);
+                ++items_so_far[t];
+                for (u32 k = 1; k < glen; ++k) {
+                    const u32 fb = level_first[t][lv + k];
+                    followers.push_back(item(0, 0, fb, batches[fb].n));
+                    ++items_so_far[t];
+                }
+                continue;
+            }
+            const u32 c = chunk_of[t];
+            for (u64 s0 = 0; s0 < eb.n; s0 += c)
+                chunks.push_back(item(s0, level_need[t], b, eb.n - s0 < c ? eb.n - s0 : c));
+            items_so_far[t] += (eb.n + c - 1) / c;
         }
     }
+    const u64 n_queue = chunks.size();
+    for (EngineChunk& ch : chunks)
+        if (ch.nfollow) ch.follow_first += u32(n_queue);
+    chunks.insert(chunks.end(), followers.begin(), followers.end());
+    return n_queue;
 }
 
 TableInfo table_info(const cht_table* h) {
@@ -748,7 +864,8 @@ struct cht_plan {
     u32* d_status = nullptr;
     u64 n_batches = 0, n_chunks = 0;
     u64 bytes_tables = 0, bytes_batches = 0, bytes_chunks = 0, bytes_counters = 0;
-    cht_plan_config cfg{0, 0, 0, 0, 0, 0};
+    std::vector<cht::EngineBatch> batches;  // host copy: work items are rebuilt when chunk_ops changes
+    cht_plan_config cfg{0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -780,6 +897,7 @@ cht::EngineArgs plan_args(const cht_plan* p) {
     e.status = p->d_status;
     e.spin_limit = (p->cfg.spin_limit_us > 0 ? (long long)p->cfg.spin_limit_us : 1000000ll) * 2000;  // ~2 GHz
     e.inject_stall = p->cfg.fault_inject & 1;
+    e.max_backoff_ns = p->cfg.poll_ns > 0 ? unsigned(p->cfg.poll_ns) : 8192u;
     return e;
 }
 
@@ -793,6 +911,33 @@ cht_status plan_run(cht_plan* p, cudaStream_t s) {
 }  // namespace
 
 extern "C" {
+
+// True if no batch's keys / vals range overlaps any batch's vals_out /
+// codes range (byte intervals; sort the outputs, binary-search each input).
+static bool inputs_disjoint_from_outputs(const std::vector<cht::EngineBatch>& batches) {
+    std::vector<std::pair<uintptr_t, uintptr_t>> outs;
+    for (const cht::EngineBatch& b : batches) {
+        if (b.vals_out) outs.emplace_back(uintptr_t(b.vals_out), uintptr_t(b.vals_out) + b.n * 8);
+        if (b.codes) outs.emplace_back(uintptr_t(b.codes), uintptr_t(b.codes) + b.n);
+    }
+    if (outs.empty()) return true;
+    std::sort(outs.begin(), outs.end());
+    // prefix maximum of the ends, so one search answers "any output overlaps"
+    std::vector<uintptr_t> max_end(outs.size());
+    uintptr_t m = 0;
+    for (size_t i = 0; i < outs.size(); ++i) max_end[i] = m = std::max(m, outs[i].second);
+    auto overlaps = [&](uintptr_t lo, uintptr_t hi) {
+        // outputs starting before hi; the one with the largest end decides
+        const size_t k = size_t(std::lower_bound(outs.begin(), outs.end(), std::make_pair(hi, uintptr_t(0))) -
+                                outs.begin());
+        return k > 0 && max_end[k - 1] > lo;
+    };
+    for (const cht::EngineBatch& b : batches) {
+        if (overlaps(uintptr_t(b.keys), uintptr_t(b.keys) + b.n * 8)) return false;
+        if (b.vals && overlaps(uintptr_t(b.vals), uintptr_t(b.vals) + b.n * 8)) return false;
+    }
+    return true;
+}
 
 cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_handle* out) {
     if (!out || (n_ops > 0 && !ops)) return CHT_ERR_INVALID_ARG;
@@ -839,9 +984,15 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
         batches.push_back(b);
         if (has_vals) p->new_cells[t] += o.n;
     }
-    // work items, round by round; need = the table's items in earlier rounds
+    // The engine may read a work item's inputs before the items it depends
+    // on have run, so no input array may overlap any output array.
+    if (!inputs_disjoint_from_outputs(batches)) {
+        delete p;
+        return CHT_ERR_INVALID_ARG;
+    }
+    // work items, round by round; need = the table's items in earlier levels
     std::vector<cht::EngineChunk> chunks;
-    cht::plan_order(batches, p->tables.size(), chunks);
+    const u64 n_queue = cht::plan_order(batches, p->tables.size(), 0, chunks);
     std::vector<cht::EngineTable> tabs(p->tables.size());
     for (size_t t = 0; t < p->tables.size(); ++t) {
         tabs[t].cells = p->tables[t]->cells;
@@ -851,7 +1002,7 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
     }
     DeviceGuard g(p->tables.empty() ? current_device() : p->device);
     p->n_batches = batches.size();
-    p->n_chunks = chunks.size();
+    p->n_chunks = n_queue;
     cht_status r = upload(reinterpret_cast<void**>(&p->d_tables), &p->bytes_tables, tabs.data(),
                           tabs.size() * sizeof(cht::EngineTable));
     if (r == CHT_OK)
@@ -872,19 +1023,40 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
         delete p;
         return r;
     }
+    p->batches = std::move(batches);
     *out = p;
     return CHT_OK;
 }
 
 cht_status cht_plan_set_config(cht_plan_handle p, const cht_plan_config* cfg) {
     if (!p) return CHT_ERR_INVALID_ARG;
-    cht_plan_config c = cfg ? *cfg : cht_plan_config{0, 0, 0, 0, 0, 0};
+    cht_plan_config c = cfg ? *cfg : cht_plan_config{0, 0, 0, 0, 0, 0, 0, 0};
     const int g = c.group_width;
     if (!(g == 0 || g == 1 || g == 4 || g == 8 || g == 16 || g == 32)) return CHT_ERR_INVALID_ARG;
     if (c.lane_cells < 0 || c.lane_cells > 2 || (g == 32 && c.lane_cells == 2)) return CHT_ERR_INVALID_ARG;
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64 || c.spin_limit_us < 0 || c.fault_inject < 0 || c.fault_inject > 1 ||
         c.direct_io < 0 || c.direct_io > 1)
         return CHT_ERR_INVALID_ARG;
+    if (c.poll_ns < 0 || c.poll_ns > 1000000) return CHT_ERR_INVALID_ARG;
+    if (!(c.chunk_ops == 0 || c.chunk_ops == 32 || c.chunk_ops == 64 || c.chunk_ops == 128 || c.chunk_ops == 256))
+        return CHT_ERR_INVALID_ARG;
+    if (c.chunk_ops != p->cfg.chunk_ops && p->n_chunks > 0) {  // rebuild the work items
+        std::vector<cht::EngineChunk> chunks;
+        const u64 n_queue = cht::plan_order(p->batches, p->tables.size(), c.chunk_ops, chunks);
+        DeviceGuard g(p->device);
+        cht::EngineChunk* d = nullptr;
+        u64 bytes = 0;
+        cht_status r = upload(reinterpret_cast<void**>(&d), &bytes, chunks.data(), chunks.size() * sizeof(cht::EngineChunk));
+        if (r == CHT_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) r = CHT_ERR_CUDA;
+        if (r != CHT_OK) {
+            lib_free(d, bytes, nullptr);
+            return r;
+        }
+        lib_free(p->d_chunks, p->bytes_chunks, nullptr);
+        p->d_chunks = d;
+        p->bytes_chunks = bytes;
+        p->n_chunks = n_queue;
+    }
     p->cfg = c;
     return CHT_OK;
 }

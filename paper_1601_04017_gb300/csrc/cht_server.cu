@@ -120,6 +120,7 @@ struct cht_server {
     unsigned char* dmeta = nullptr;  // device: step metadata
     Ring dring;
     u64 meta_bytes = 0;
+    u64 max_step_items = 0;  // engine work items one step may use
     std::vector<Req> reqs;
     std::list<u64> queue;
     std::deque<Step> inflight;
@@ -352,8 +353,12 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
         batches[i].table = rq.r.table;
         batches[i].mode = u32(rq.r.op);
     }
+    // work items sized per table from its chain of dependent requests; if
+    // that needs more metadata than a step of 256-operation items may use,
+    // take 256-operation items
     std::vector<cht::EngineChunk> chunks;
-    cht::plan_order(batches, nt, chunks);
+    u64 n_queue = cht::plan_order(batches, nt, 0, chunks);
+    if (chunks.size() > s->max_step_items) n_queue = cht::plan_order(batches, nt, int(cht::kChunkOps), chunks);
     std::vector<u32> touched;
     std::vector<u64> tnew;
     {
@@ -383,11 +388,12 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
     e.tables = reinterpret_cast<const cht::EngineTable*>(dm);
     e.batches = reinterpret_cast<const cht::EngineBatch*>(dm + o_bat);
     e.chunks = reinterpret_cast<const cht::EngineChunk*>(dm + o_chk);
-    e.n_chunks = chunks.size();
+    e.n_chunks = n_queue;
     e.next = reinterpret_cast<unsigned long long*>(dm + o_cnt);
     e.done = e.next + 1;
     e.status = reinterpret_cast<u32*>(e.done + nt);
     e.spin_limit = 2000000000ll;
+    e.max_backoff_ns = 8192;
     e.inject_stall = 0;
     if (cudaEventRecord(st.t_eng0, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
     if (cht::launch_engine(e, 1, 2, 0, true, s->stream) != cudaSuccess) {
@@ -425,7 +431,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
     if (!s->spare_events.empty()) {
         st.ev = s->spare_events.back();
         s->spare_events.pop_back();
-    } else if (cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming) != cudaSuccess) {
+    } else if (cudaEventCreate(&st.ev) != cudaSuccess) {
         return CHT_ERR_CUDA;
     }
     if (cudaEventRecord(st.ev, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
@@ -501,10 +507,12 @@ cht_status cht_server_create(const cht_handle* tables, uint32_t n_tables, const 
     // exact starting counts of every table
     cht_status r = CHT_OK;
     for (size_t t = 0; t < nt && r == CHT_OK; ++t) r = cht::table_read_counts(s->tables[t], &s->known_I[t], &s->known_D[t], s->stream);
-    // metadata rings: room for several steps of the largest size
-    s->meta_bytes = (s->cfg.max_step_ops / cht::kChunkOps + s->cfg.max_step_requests + 1) * 48 +
+    // metadata rings: room for several steps of the largest size (twice
+    // over, so a step also fits when the free space is split at the ring end)
+    s->max_step_items = s->cfg.max_step_ops / cht::kChunkOps + s->cfg.max_step_requests;
+    s->meta_bytes = (s->max_step_items + s->cfg.max_step_requests + 1) * 48 +
                     nt * (sizeof(cht::EngineTable) + 40) + (1u << 20);
-    s->meta_bytes *= (s->cfg.max_inflight_steps + 1);
+    s->meta_bytes *= 2 * (s->cfg.max_inflight_steps + 1);
     s->aring.cap = s->cfg.arena_bytes;
     s->mring.cap = s->meta_bytes;
     s->dring.cap = s->meta_bytes;

@@ -75,12 +75,13 @@ def _check(wl, keys, tables, vout, codes, otabs, ovout, ocodes):
         assert np.array_equal(gk[i], ok[j]) and np.array_equal(gv[i], ov[j])
 
 
-@pytest.mark.parametrize("g,v,direct", [(0, 0, 0), (4, 2, 0), (8, 1, 0), (32, 1, 0), (0, 0, 1), (4, 2, 1)])
-def test_engine_matches_oracle(cuda_lib, oracle_mod, g, v, direct):
+@pytest.mark.parametrize("g,v,direct,chunk", [(0, 0, 0, 0), (4, 2, 0, 0), (8, 1, 0, 0), (32, 1, 0, 0), (0, 0, 1, 0),
+                                               (4, 2, 1, 0), (0, 0, 0, 32), (0, 0, 1, 64), (8, 1, 0, 128)])
+def test_engine_matches_oracle(cuda_lib, oracle_mod, g, v, direct, chunk):
     wl = W.batched_workload(48, 6, 11, seed=31)
     tables, ops, vout, codes = _setup(cuda_lib, wl)
     plan = cuda_lib.Plan(ops)
-    plan.set_config(group_width=g, lane_cells=v, direct_io=direct)
+    plan.set_config(group_width=g, lane_cells=v, direct_io=direct, chunk_ops=chunk)
     plan.launch()
     assert plan.status() == 0
     otabs, keys, ovout, ocodes = _oracle(oracle_mod, wl)
@@ -140,3 +141,84 @@ def test_plan_rejects_host_arrays(cuda_lib):
     with pytest.raises(cuda_lib.ChtError):
         cuda_lib.Plan([(t, cuda_lib.OP_INSERT, keys, keys, None, None)])
     torch.cuda.synchronize()
+
+
+def test_plan_rejects_inputs_overlapping_outputs(cuda_lib):
+    import torch
+
+    t = cuda_lib.Table(1024)
+    buf = torch.arange(1, 65, dtype=torch.int64, device="cuda")
+    vout = torch.zeros(32, dtype=torch.int64, device="cuda")
+    # a find whose found values land where a later insert reads its keys
+    with pytest.raises(cuda_lib.ChtError):
+        cuda_lib.Plan([(t, cuda_lib.OP_FIND, buf[:32], None, buf[16:48], None),
+                       (t, cuda_lib.OP_INSERT, buf[40:64], buf[40:64], None, None)])
+    # codes inside a key array
+    codes = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(cuda_lib.ChtError):
+        cuda_lib.Plan([(t, cuda_lib.OP_INSERT, buf[:32], buf[:32], None, buf.view(torch.uint8)[8:40])])
+    # disjoint arrays are fine
+    cuda_lib.Plan([(t, cuda_lib.OP_FIND, buf[:32], None, vout, codes[:32])]).destroy()
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("chunk", [0, 32, 256])
+def test_engine_chain_of_small_batches(cuda_lib, oracle_mod, chunk):
+    """One table, a long chain of small dependent batches of every kind (the
+    engine runs runs of one-item levels in one warp) plus a second table with
+    larger batches interleaved; results and final contents vs the oracle."""
+    import torch
+
+    rng = np.random.default_rng(77)
+    universe = W.uniform_keys(3000, seed=78)
+    specs = []
+    for i in range(400):
+        t = 0 if i % 5 else 1
+        n = int(rng.integers(1, 200)) if t == 0 else int(rng.integers(100, 2000))
+        op = int(rng.choice([W.OP_FIND, W.OP_INSERT, W.OP_IOU_ADD, W.OP_ERASE], p=[0.4, 0.3, 0.2, 0.1]))
+        k = universe[rng.integers(0, universe.size, n)]
+        # an insert's value is a function of its key: whichever copy of a
+        # repeated key wins, the stored value is the same
+        v = k ^ np.uint64(0x5DEECE66D) if op == W.OP_INSERT else W.uniform_keys(n, seed=1000 + i)
+        specs.append((t, op, k, v))
+    total = sum(k.size for _, _, k, _ in specs)
+    keys_d = torch.empty(total, dtype=torch.int64, device="cuda")
+    vals_d = torch.empty(total, dtype=torch.int64, device="cuda")
+    vout = torch.full((total,), -1, dtype=torch.int64, device="cuda")
+    codes = torch.full((total,), 255, dtype=torch.uint8, device="cuda")
+    tables = [cuda_lib.Table(1 << 12), cuda_lib.Table(1 << 13)]
+    otabs = [oracle_mod.OracleTable(1 << 12), oracle_mod.OracleTable(1 << 13)]
+    ops, spans, o = [], [], 0
+    for t, op, k, v in specs:
+        n = k.size
+        keys_d[o:o + n] = torch.from_numpy(k.view(np.int64))
+        vals_d[o:o + n] = torch.from_numpy(v.view(np.int64))
+        ops.append((tables[t], op, keys_d[o:o + n], vals_d[o:o + n] if op in (W.OP_INSERT, W.OP_IOU_ADD) else None,
+                    vout[o:o + n] if op == W.OP_FIND else None, codes[o:o + n]))
+        spans.append((o, o + n))
+        o += n
+    plan = cuda_lib.Plan(ops)
+    plan.set_config(chunk_ops=chunk)
+    plan.launch()
+    assert plan.status() == 0
+    g_v, g_c = to_np_u64(vout), to_np_u8(codes)
+    for (t, op, k, v), (lo, hi) in zip(specs, spans):
+        ot = otabs[t]
+        if op == W.OP_FIND:
+            ov, oc = ot.find(k)
+            assert np.array_equal(g_v[lo:hi], ov) and np.array_equal(g_c[lo:hi], oc)
+            continue
+        if op == W.OP_INSERT:
+            oc = ot.insert(k, v)
+        elif op == W.OP_IOU_ADD:
+            oc = ot.insert_or_update(k, v, oracle_mod.ADD)
+        else:
+            oc = ot.erase(k)
+        for kk in np.unique(k):  # equal keys in one batch: which one wins is free
+            m = k == kk
+            assert int(g_c[lo:hi][m].astype(np.int64).sum()) == int(oc[m].astype(np.int64).sum())
+    for t, ot in zip(tables, otabs):
+        gk, gv = map(to_np_u64, t.export())
+        ok, ov = ot.export()
+        i, j = np.argsort(gk), np.argsort(ok)
+        assert gk.size == ok.size and np.array_equal(gk[i], ok[j]) and np.array_equal(gv[i], ov[j])
