@@ -53,6 +53,7 @@ typedef struct {
     double alpha;      /* fill threshold for growth (Sec. 4.3.2) */
     uint64_t probes;   /* cells inspected by all operations so far (statistics) */
     uint64_t migrations;
+    int reuse_tombstones; /* inserts may take the first tombstone on their path */
 } or_table;
 
 /* 64-bit finalizer of MurmurHash3 (Appleby, public domain): the paper hashes
@@ -121,6 +122,14 @@ void or_destroy(or_table *t)
     free(t->cells);
     free(t);
 }
+
+/* Tombstone reuse (off by default, which is the paper's rule: a deleted cell
+ * is never used again, Sec. 3 "Deletions").  Under phase semantics no erase
+ * runs while an insert batch does, so an insert that finds its key absent may
+ * put it into the first tombstone on its probe path instead of the first
+ * empty cell: the cell stays non-empty (I unchanged, D - 1), every key stays
+ * reachable from its home, and every result is the same as without reuse. */
+void or_set_reuse(or_table *t, int on) { t->reuse_tombstones = on; }
 
 uint64_t or_capacity(const or_table *t) { return t->cap; }
 uint64_t or_nonempty(const or_table *t) { return t->I; }
@@ -201,18 +210,27 @@ static void grow_if_needed(or_table *t)
 /* insertOrUpdate (Algorithm 1), sequential: probe from the home cell; at the
  * first empty cell store <k, d> and report an insertion; at a cell holding k
  * apply the update and report an update.  Tombstones are passed over like any
- * other non-empty cell and never reused (Sec. 3 "Deletions").  Mode 0 is the
- * plain insert of Sec. 3 (a present key is left untouched). */
+ * other non-empty cell and never reused (Sec. 3 "Deletions") -- unless reuse
+ * is on: then the key goes into the first tombstone the probe passed, once
+ * the probe has shown the key absent (an empty cell, or all c cells seen).
+ * Mode 0 is the plain insert of Sec. 3 (a present key is left untouched). */
 static int or_modify1(or_table *t, uint64_t k, uint64_t d, int mode, int op)
 {
     if (is_reserved(k)) return OR_RESERVED;
     grow_if_needed(t);
     uint64_t mask = t->cap - 1;
     uint64_t i = home_of(k, t->log2c);
+    or_cell *tomb = NULL;
     for (uint64_t step = 0; step < t->cap; ++step, i = (i + 1) & mask) {
         or_cell *c = &t->cells[i];
         t->probes++;
         if (c->key == OR_EMPTY) {
+            if (tomb) {
+                tomb->key = k;
+                tomb->val = d;
+                t->D--;
+                return OR_YES;
+            }
             c->key = k;
             c->val = d;
             t->I++;
@@ -222,6 +240,13 @@ static int or_modify1(or_table *t, uint64_t k, uint64_t d, int mode, int op)
             if (mode == 1) c->val = (op == OR_ADD) ? c->val + d : d;
             return OR_NO;
         }
+        if (c->key == OR_TOMB && t->reuse_tombstones && !tomb) tomb = c;
+    }
+    if (tomb) {  /* no empty cell anywhere, the key is absent */
+        tomb->key = k;
+        tomb->val = d;
+        t->D--;
+        return OR_YES;
     }
     return OR_FULL;
 }

@@ -78,12 +78,13 @@ def _random_batch(rng, pool, n):
 
 @pytest.mark.parametrize("log2c", [6, 7, 8, 10])
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_oracle_matches_dictionary(oracle_mod, log2c, seed):
+@pytest.mark.parametrize("reuse", [False, True])
+def test_oracle_matches_dictionary(oracle_mod, log2c, seed, reuse):
     c = 1 << log2c
     rng = np.random.default_rng(1000 * log2c + seed)
     pool = np.concatenate([W.uniform_keys(c // 2, start=seed * 4096, seed=5),
                            _wrap_keys(oracle_mod, log2c, 6, seed)])
-    t = oracle_mod.OracleTable(c)
+    t = oracle_mod.OracleTable(c, reuse_tombstones=reuse)
     m = DictModel()
     for step in range(40):
         kind = rng.choice(["insert", "iou_add", "iou_ow", "find", "erase"])
@@ -180,6 +181,57 @@ def test_tombstones_are_not_reused(oracle_mod):
     # re-inserting an erased key occupies a fresh cell: I grows
     assert (t.insert(ks[:10], ks[:10]) == 1).all()
     assert t.nonempty == 30 and t.live == 20
+    t.assert_invariants()
+
+
+def test_reused_tombstones_keep_counts_and_reachability(oracle_mod):
+    """With reuse, re-inserting erased keys takes their tombstones back: the
+    non-empty count stays, the tombstone count drops to zero, and every key is
+    still found from its home."""
+    c = 64
+    t = oracle_mod.OracleTable(c, reuse_tombstones=True)
+    ks = W.uniform_keys(20, seed=12)
+    t.insert(ks, ks)
+    assert (t.erase(ks[:10]) == 1).all()
+    assert t.nonempty == 20 and t.live == 10
+    assert (t.insert(ks[:10], ks[:10] + np.uint64(1)) == 1).all()
+    assert t.nonempty == 20 and t.live == 20
+    v, f = t.find(ks)
+    assert (f == 1).all() and (v[:10] == ks[:10] + np.uint64(1)).all() and (v[10:] == ks[10:]).all()
+    t.assert_invariants()
+
+
+def test_reused_tombstone_fills_a_table_without_empty_cells(oracle_mod):
+    """A table with no empty cell but a tombstone still takes a new key."""
+    c = 64
+    t = oracle_mod.OracleTable(c, reuse_tombstones=True)
+    ks = W.uniform_keys(c + 1, seed=13)
+    assert (t.insert(ks[:c], ks[:c]) == 1).all()
+    assert t.erase(ks[:1])[0] == 1
+    assert t.insert(ks[c:], ks[c:])[0] == 1
+    assert t.insert(ks[:1], ks[:1])[0] == 2  # now full again
+    t.assert_invariants()
+
+
+@pytest.mark.parametrize("reuse", [False, True])
+def test_erase_reinsert_cycles_and_probe_length(oracle_mod, reuse):
+    """Erasing and re-inserting the same keys again and again: without reuse
+    every cycle leaves a tombstone on the keys' probe paths, so an insert of
+    cycle r walks past ~r of them (linear probing, Sec. 2); with reuse each
+    key goes back into its own tombstone and the walk stays one cell."""
+    c = 1 << 12
+    t = oracle_mod.OracleTable(c, reuse_tombstones=reuse)
+    ks = W.uniform_keys(4, seed=14)
+    t.insert(ks, ks)
+    for _ in range(200):
+        assert (t.erase(ks) == 1).all()
+        t.reset_probes()
+        assert (t.insert(ks, ks) == 1).all()
+    per_insert = t.probes / ks.size
+    if reuse:
+        assert per_insert <= 2.0 and t.nonempty == 4
+    else:
+        assert per_insert >= 150 and t.nonempty == 4 + 4 * 200
     t.assert_invariants()
 
 
