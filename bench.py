@@ -834,12 +834,16 @@ def run_serving(args):
 
     cht.load_library()
     nreq = args.serving_requests
-    wl = W.serving_workload(nreq, n_tables=256, log2_min=10, log2_max=24, size_log2_max=16, table_s=1.0)
+    wl = W.serving_workload(nreq, n_tables=256, log2_min=10, log2_max=24, size_log2_max=16, table_s=1.0,
+                            mix=tuple(args.serving_mix))
     total = int(wl["offsets"][-1])
-    keys_h = torch.empty(total, dtype=torch.int64).pin_memory()
-    vals_h = torch.empty(total, dtype=torch.int64).pin_memory()
-    vout_h = torch.zeros(total, dtype=torch.int64).pin_memory()
-    codes_h = torch.zeros(total, dtype=torch.uint8).pin_memory()
+    on_dev = args.serving_arrays == "device"
+
+    def buf(dtype):
+        return torch.zeros(total, dtype=dtype, device="cuda") if on_dev else \
+            torch.zeros(total, dtype=dtype).pin_memory()
+
+    keys_h, vals_h, vout_h, codes_h = buf(torch.int64), buf(torch.int64), buf(torch.int64), buf(torch.uint8)
     r0 = 0
     while r0 < nreq:
         r1 = int(np.searchsorted(wl["offsets"], wl["offsets"][r0] + (1 << 27), side="right")) - 1
@@ -865,6 +869,7 @@ def run_serving(args):
         lat, mk = srv.replay(reqs, arrivals)
         steps, done = srv.stats()
         prof = srv.profile()
+        prof["trace"] = srv.trace()
         grown = sum(t.size()[2] for t in tables) * 16
         srv.destroy()
         for t in tables:
@@ -872,18 +877,25 @@ def run_serving(args):
         torch.cuda.synchronize()
         return lat, mk, steps, done, grown, prof
 
-    def breakdown(prof, mk):
+    def breakdown(prof, mk, name):
+        tr = prof["trace"]
+        if args.serving_trace:
+            np.save(f"{args.serving_trace}_{name}.npy", tr)
+        per_round = tr["engine_ms"] * 1e3 / np.maximum(tr["rounds"], 1)
         return {"gpu_busy_s": round(prof["gpu_step_ms"] / 1e3, 4), "engine_s": round(prof["engine_ms"] / 1e3, 4),
                 "host_admit_s": round(prof["host_admit_ms"] / 1e3, 4), "makespan_s": round(mk, 4),
                 "dependent_rounds": prof["rounds"], "parts": prof["parts"], "work_items": prof["chunks"],
-                "migrations": prof["migrations"]}
+                "migrations": prof["migrations"],
+                "engine_us_per_round_p50_p90": [round(float(np.percentile(per_round, q)), 2) for q in (50, 90)],
+                "recut_steps": int(tr["recut"].sum()), "largest_table_log2": int(tr["max_table_log2"].max())}
 
     lat0, mk0, steps0, done0, grown, prof0 = run(np.zeros(nreq))
     assert done0 == nreq
     cap_rps = nreq / mk0
     out = {"workload": "serving: 256 growable tables (key universes log-uniform 2^10..2^24), requests of 1..65536 "
-                       "ops (log-uniform), table ~ Zipf(1.0), find/insert/insertOrUpdate(add)/erase 50/30/15/5, "
-                       "request arrays in pinned host memory, memory cap 64 GiB",
+                       "ops (log-uniform), table ~ Zipf(1.0), find/insert/insertOrUpdate(add)/erase "
+                       f"{'/'.join(str(round(100 * x)) for x in args.serving_mix)}, "
+                       f"request arrays in {'device' if on_dev else 'pinned host'} memory, memory cap 64 GiB",
            "request_arrays": "copied through the device arena" if args.serving_stage_inputs else
                              "read and written in place (zero-copy)",
            "requests": nreq, "ops": total, "final_table_bytes": grown,
@@ -891,7 +903,7 @@ def run_serving(args):
                         "mops": round(total / mk0 / 1e6, 1), "steps": steps0,
                         "p50_ms": round(float(np.percentile(lat0, 50)) * 1e3, 3),
                         "p99_ms": round(float(np.percentile(lat0, 99)) * 1e3, 3),
-                        "time": breakdown(prof0, mk0)}}
+                        "time": breakdown(prof0, mk0, "capacity")}}
     for frac in args.serving_loads:
         arr = W.poisson_arrivals(nreq, frac * cap_rps)
         lat, mk, steps, done, _, prof = run(arr)
@@ -899,7 +911,8 @@ def run_serving(args):
                                "mops": round(total / mk / 1e6, 1), "steps": steps,
                                "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
-                               "max_ms": round(float(lat.max()) * 1e3, 3), "time": breakdown(prof, mk)}
+                               "max_ms": round(float(lat.max()) * 1e3, 3),
+                               "time": breakdown(prof, mk, f"load_{frac}")}
     print(json.dumps(out), flush=True)
 
 
@@ -930,6 +943,12 @@ def main():
     ap.add_argument("--no-graph-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=100_000)
     ap.add_argument("--serving-loads", type=float, nargs="*", default=[0.5, 0.7, 0.9])
+    ap.add_argument("--serving-mix", type=float, nargs=4, default=[0.5, 0.3, 0.15, 0.05],
+                    help="find / insert / insertOrUpdate(add) / erase fractions of the requests")
+    ap.add_argument("--serving-trace", default="",
+                    help="save each run's per-step server trace to <prefix>_<run>.npy")
+    ap.add_argument("--serving-arrays", default="pinned", choices=["pinned", "device"],
+                    help="where the request arrays live: pinned host memory or device memory")
     ap.add_argument("--serving-stage-inputs", type=int, default=0, choices=[0, 1],
                     help="1: copy every request through the device arena instead of reading it in place")
     args = ap.parse_args()

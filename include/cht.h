@@ -363,6 +363,26 @@ typedef struct {
     double host_admit_ms;
 } cht_server_profile;
 cht_status cht_server_get_profile(cht_server_handle s, cht_server_profile *out);
+
+/* One record per completed step, in completion order.  gpu_ms / engine_ms
+ * as in cht_server_profile; ops: operations launched; rounds: longest chain
+ * of dependent batches; max_table_log2: log2 cells of the largest table of
+ * the server at launch; recut: 1 if the step's work items were cut at 256
+ * operations because the per-table sizing needed more metadata than a step
+ * may use. */
+typedef struct {
+    double gpu_ms;
+    double engine_ms;
+    uint64_t parts;
+    uint64_t items;
+    uint64_t ops;
+    uint64_t rounds;
+    uint64_t migrations;
+    uint32_t max_table_log2;
+    uint32_t recut;
+} cht_server_step_record;
+/* Copy up to max records (from the first step) into out; *n = records kept. */
+cht_status cht_server_get_trace(cht_server_handle s, cht_server_step_record *out, uint64_t max, uint64_t *n);
 cht_status cht_server_destroy(cht_server_handle s);
 
 /* Cap, in bytes, on the device memory this library allocates at any time for

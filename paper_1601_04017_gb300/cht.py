@@ -76,6 +76,12 @@ class ServerProfile(ctypes.Structure):
                 ("gpu_step_ms", ctypes.c_double), ("engine_ms", ctypes.c_double), ("host_admit_ms", ctypes.c_double)]
 
 
+class ServerStepRecord(ctypes.Structure):
+    _fields_ = [("gpu_ms", ctypes.c_double), ("engine_ms", ctypes.c_double), ("parts", ctypes.c_uint64),
+                ("items", ctypes.c_uint64), ("ops", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
+                ("migrations", ctypes.c_uint64), ("max_table_log2", ctypes.c_uint32), ("recut", ctypes.c_uint32)]
+
+
 class PlanConfig(ctypes.Structure):
     _fields_ = [("group_width", ctypes.c_int), ("lane_cells", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("spin_limit_us", ctypes.c_int), ("fault_inject", ctypes.c_int), ("direct_io", ctypes.c_int),
@@ -133,6 +139,7 @@ def load_library(build: bool = True):
             "cht_server_replay": (i32, [p, p, p, u64, p, ctypes.POINTER(ctypes.c_double)]),
             "cht_server_stats": (i32, [p, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
             "cht_server_get_profile": (i32, [p, ctypes.POINTER(ServerProfile)]),
+            "cht_server_get_trace": (i32, [p, ctypes.POINTER(ServerStepRecord), u64, ctypes.POINTER(u64)]),
             "cht_server_destroy": (i32, [p]),
         }
         for name, (res, args) in sigs.items():
@@ -448,6 +455,19 @@ class Server:
         pr = ServerProfile()
         _check(self._lib.cht_server_get_profile(self._h, ctypes.byref(pr)), "cht_server_get_profile")
         return {f: getattr(pr, f) for f, _ in ServerProfile._fields_}
+
+    def trace(self) -> np.ndarray:
+        """Per-step records (cht_server_get_trace) as a structured array."""
+        n = ctypes.c_uint64()
+        _check(self._lib.cht_server_get_trace(self._h, None, 0, ctypes.byref(n)), "cht_server_get_trace")
+        recs = (ServerStepRecord * max(int(n.value), 1))()
+        _check(self._lib.cht_server_get_trace(self._h, recs, n.value, ctypes.byref(n)), "cht_server_get_trace")
+        dt = np.dtype([(f, np.float64 if t is ctypes.c_double else np.uint64 if t is ctypes.c_uint64 else np.uint32)
+                       for f, t in ServerStepRecord._fields_])
+        out = np.zeros(int(n.value), dt)
+        for i in range(int(n.value)):
+            out[i] = tuple(getattr(recs[i], f) for f, _ in ServerStepRecord._fields_)
+        return out
 
     def destroy(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -131,17 +131,45 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
     bool active = false;
     u64 idx = 0, key = 0, d = 0, pos = 0, probed = 0;
 
+    // Unstaged: the warp's next 64 keys (and values) are held in registers,
+    // two windows of 32 -- lane j holds operation wbase + j of `cur` and
+    // wbase + 32 + j of `nxt` -- loaded with coalesced 256-byte reads one
+    // window ahead, so a refill takes its key by shuffle instead of a
+    // dependent load from memory.  Invariant: next - wbase < 32 between
+    // refills (a refill takes at most 32 operations).
+    u64 wbase = next, k_cur = 0, v_cur = 0, k_nxt = 0, v_nxt = 0;
+    if (!kStaged) {
+        if (wbase + lane < end) {
+            k_cur = ld_stream(a.keys + wbase + lane);
+            if (kHasVals) v_cur = ld_stream(a.vals + wbase + lane);
+        }
+        if (wbase + 32 + lane < end) {
+            k_nxt = ld_stream(a.keys + wbase + 32 + lane);
+            if (kHasVals) v_nxt = ld_stream(a.vals + wbase + 32 + lane);
+        }
+    }
+
     for (;;) {
         // ---- refill idle groups from this warp's slice
         bool fresh = false;
         const u32 idle = __ballot_sync(FULL, !active) & GroupConsts<G>::leaders;
         if (idle != 0 && next < end) {
+            const u64 my = next + __popc(idle & below_group);
+            u64 wk = 0, wv = 0;
+            if (!kStaged) {  // every lane shuffles; only idle groups use the result
+                const u32 o = u32(my - wbase);
+                const u64 xk = __shfl_sync(FULL, k_cur, o & 31), yk = __shfl_sync(FULL, k_nxt, o & 31);
+                wk = o < 32 ? xk : yk;
+                if (kHasVals) {
+                    const u64 xv = __shfl_sync(FULL, v_cur, o & 31), yv = __shfl_sync(FULL, v_nxt, o & 31);
+                    wv = o < 32 ? xv : yv;
+                }
+            }
             if (!active) {
-                const u64 my = next + __popc(idle & below_group);
                 if (my < end) {
                     idx = my;
-                    key = op_key<kStaged>(a, sg, idx);
-                    if (kHasVals) d = op_val<kStaged>(a, sg, idx);
+                    key = kStaged ? op_key<kStaged>(a, sg, idx) : wk;
+                    if (kHasVals) d = kStaged ? op_val<kStaged>(a, sg, idx) : wv;
                     if (is_reserved(key)) {
                         if (gl == 0) {
                             op_code<kStaged>(a, sg, idx, kCodeReserved);
@@ -157,6 +185,15 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                 }
             }
             next += __popc(idle);
+            if (!kStaged && next - wbase >= 32) {  // slide: nxt becomes cur, load the one after
+                wbase += 32;
+                k_cur = k_nxt;
+                v_cur = v_nxt;
+                if (wbase + 32 + lane < end) {
+                    k_nxt = ld_stream(a.keys + wbase + 32 + lane);
+                    if (kHasVals) v_nxt = ld_stream(a.vals + wbase + 32 + lane);
+                }
+            }
         }
 
         // ---- pre-reduce equal keys loaded in this step (modifying modes)

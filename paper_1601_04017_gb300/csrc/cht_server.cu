@@ -88,6 +88,7 @@ struct Step {
     std::vector<u32> touched;
     std::vector<u64> new_cells;          // per touched table
     unsigned long long* snap = nullptr;  // pinned: (I, D) per touched table
+    cht_server_step_record rec{};        // completed by poll() with the times
 };
 
 struct Req {
@@ -130,6 +131,7 @@ struct cht_server {
     std::vector<cudaEvent_t> spare_timers;
     u64 steps = 0, completed = 0;
     cht_server_profile prof{};
+    std::vector<cht_server_step_record> trace;  // one record per completed step
     bool pageable_ok = false;  // device can address pageable host memory
 };
 
@@ -174,6 +176,9 @@ cht_status poll(cht_server* s, u32* completed_now) {
         if (cudaEventElapsedTime(&ms_step, st.t_begin, st.ev) == cudaSuccess) s->prof.gpu_step_ms += ms_step;
         if (cudaEventElapsedTime(&ms_eng, st.t_eng0, st.t_eng1) == cudaSuccess) s->prof.engine_ms += ms_eng;
         cudaGetLastError();
+        st.rec.gpu_ms = ms_step;
+        st.rec.engine_ms = ms_eng;
+        s->trace.push_back(st.rec);
         s->aring.tail = st.arena_end;
         s->mring.tail = st.meta_end;
         s->dring.tail = st.dmeta_end;
@@ -272,6 +277,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
                 cht_status r = cht::table_migrate_to(h, nl, ~0ull, s->stream);
                 if (r != CHT_OK) return r;
                 ++s->prof.migrations;
+                ++st.rec.migrations;
             }
         }
         if (rq.direct) {  // the engine reads / writes the request's arrays in place
@@ -358,7 +364,10 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
     // take 256-operation items
     std::vector<cht::EngineChunk> chunks;
     u64 n_queue = cht::plan_order(batches, nt, 0, chunks);
-    if (chunks.size() > s->max_step_items) n_queue = cht::plan_order(batches, nt, int(cht::kChunkOps), chunks);
+    if (chunks.size() > s->max_step_items) {
+        n_queue = cht::plan_order(batches, nt, int(cht::kChunkOps), chunks);
+        st.rec.recut = 1;
+    }
     std::vector<u32> touched;
     std::vector<u64> tnew;
     {
@@ -409,6 +418,11 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
         s->prof.rounds += rounds;
         s->prof.chunks += chunks.size();
         s->prof.parts += batches.size();
+        st.rec.rounds = rounds;
+        st.rec.items = chunks.size();
+        st.rec.parts = batches.size();
+        for (const cht::EngineBatch& b : batches) st.rec.ops += b.n;
+        for (const cht::EngineTable& et : tabs) st.rec.max_table_log2 = std::max(st.rec.max_table_log2, et.log2c);
     }
     // staged results back to the caller's arrays
     for (const Part& p : parts) {
@@ -622,6 +636,14 @@ cht_status cht_server_get_profile(cht_server_handle s, cht_server_profile* out) 
     *out = s->prof;
     out->steps = s->steps;
     out->completed = s->completed;
+    return CHT_OK;
+}
+
+cht_status cht_server_get_trace(cht_server_handle s, cht_server_step_record* out, uint64_t max, uint64_t* n) {
+    if (!s || !n || (max > 0 && !out)) return CHT_ERR_INVALID_ARG;
+    const u64 k = std::min<u64>(max, s->trace.size());
+    for (u64 i = 0; i < k; ++i) out[i] = s->trace[i];
+    *n = s->trace.size();
     return CHT_OK;
 }
 

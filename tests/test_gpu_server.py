@@ -89,6 +89,11 @@ def test_server_mix_equals_alone(cuda_lib, inflight, stage):
     assert steps <= prof["rounds"] <= prof["parts"]
     assert 0 < prof["engine_ms"] <= prof["gpu_step_ms"] <= makespan * 1e3
     assert prof["migrations"] > 0  # the 64-cell tables had to grow
+    tr = srv.trace()
+    assert tr.size == steps and int(tr["parts"].sum()) == prof["parts"] and int(tr["items"].sum()) == prof["chunks"]
+    assert int(tr["rounds"].sum()) == prof["rounds"] and int(tr["migrations"].sum()) == prof["migrations"]
+    assert int(tr["ops"].sum()) == int(wl["offsets"][-1])
+    assert abs(float(tr["engine_ms"].sum()) - prof["engine_ms"]) < 1e-6 * max(1.0, prof["engine_ms"]) + 1e-3
     alone_tabs, a_vout, a_codes = _single_calls(cuda_lib, wl, keys, vals, caps)
     _compare(wl, keys, tables, vout, codes, alone_tabs, a_vout, a_codes)
     srv.destroy()
