@@ -864,6 +864,8 @@ def run_serving(args):
 
     def run(arrivals):
         tables = [cht.Table(1024, growable=True) for _ in range(256)]
+        for t in tables:
+            t.set_config(reuse_tombstones=args.serving_reuse_tombstones)
         srv = cht.Server(tables, memory_cap_bytes=64 << 30, arena_bytes=1 << 30, max_inflight_steps=2,
                          stage_inputs=args.serving_stage_inputs)
         lat, mk = srv.replay(reqs, arrivals)
@@ -898,6 +900,7 @@ def run_serving(args):
                        f"request arrays in {'device' if on_dev else 'pinned host'} memory, memory cap 64 GiB",
            "request_arrays": "copied through the device arena" if args.serving_stage_inputs else
                              "read and written in place (zero-copy)",
+           "table_config": {"growable": True, "alpha": 0.5, "reuse_tombstones": args.serving_reuse_tombstones},
            "requests": nreq, "ops": total, "final_table_bytes": grown,
            "capacity": {"makespan_s": round(mk0, 4), "requests_per_s": round(cap_rps, 1),
                         "mops": round(total / mk0 / 1e6, 1), "steps": steps0,
@@ -943,6 +946,8 @@ def main():
     ap.add_argument("--no-graph-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=100_000)
     ap.add_argument("--serving-loads", type=float, nargs="*", default=[0.5, 0.7, 0.9])
+    ap.add_argument("--serving-reuse-tombstones", type=int, default=1, choices=[0, 1],
+                    help="table option: inserts take the first tombstone on their path")
     ap.add_argument("--serving-mix", type=float, nargs=4, default=[0.5, 0.3, 0.15, 0.05],
                     help="find / insert / insertOrUpdate(add) / erase fractions of the requests")
     ap.add_argument("--serving-trace", default="",

@@ -93,7 +93,14 @@ typedef enum {
  * insertOrUpdate operations in shared memory first (one table operation per
  * distinct key and window); 2 also combines equal keys within each warp step
  * before that (faster only under extreme skew); 0 probes every operation
- * with the group kernel. */
+ * with the group kernel.  reuse_tombstones: 0 (default) = the paper's rule,
+ * an erased cell is never used again until a migration drops it (Sec. 3
+ * "Deletions"); 1 = an insert / insert-or-update that finds its key absent
+ * puts it into the first tombstone on its probe path (safe under phase
+ * semantics: no erase runs during an insert batch).  Results are the same
+ * either way; reuse keeps probes short when keys are erased and inserted
+ * again and again, where without it every cycle leaves a tombstone on the
+ * key's probe path. */
 typedef struct {
     int group_width;
     int lane_cells;
@@ -101,6 +108,7 @@ typedef struct {
     int migrate_tile;
     double alpha;
     int iou_aggregate;
+    int reuse_tombstones;
 } cht_config;
 
 /* Create a table of at least `capacity` cells (rounded up to a power of two,

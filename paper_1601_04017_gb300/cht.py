@@ -45,7 +45,7 @@ class ChtError(RuntimeError):
 class ChtConfig(ctypes.Structure):
     _fields_ = [("group_width", ctypes.c_int), ("lane_cells", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("migrate_tile", ctypes.c_int), ("alpha", ctypes.c_double),
-                ("iou_aggregate", ctypes.c_int)]
+                ("iou_aggregate", ctypes.c_int), ("reuse_tombstones", ctypes.c_int)]
 
 
 OP_FIND, OP_INSERT, OP_IOU_ADD, OP_IOU_OVERWRITE, OP_ERASE = 0, 1, 2, 3, 4
@@ -242,8 +242,7 @@ class Table:
     def set_config(self, **kw):
         cur = self.config()
         cur.update(kw)
-        c = ChtConfig(int(cur["group_width"]), int(cur["lane_cells"]), int(cur["ctas_per_sm"]),
-                      int(cur["migrate_tile"]), float(cur["alpha"]), int(cur["iou_aggregate"]))
+        c = ChtConfig(*(float(cur[f]) if t is ctypes.c_double else int(cur[f]) for f, t in ChtConfig._fields_))
         _check(self._lib.cht_set_config(self._h, ctypes.byref(c)), "cht_set_config")
 
     # -- operations ----------------------------------------------------------

@@ -15,6 +15,7 @@ enum Mode : int { kFind = 0, kInsert = 1, kIouAdd = 2, kIouOverwrite = 3, kErase
 struct OpArgs {
     Cell* cells;
     u32 log2c;
+    u32 reuse;            // inserts may take the first tombstone on their path
     const u64* keys;
     const u64* vals;      // insert / insert_or_update input values (else NULL)
     u64* vals_out;        // find output values (else NULL)
@@ -54,7 +55,7 @@ constexpr u32 kChunkOps = 256;  // operations per engine work item
 struct EngineTable {
     Cell* cells;
     u32 log2c;
-    u32 pad;
+    u32 reuse;  // tombstone reuse by inserts (table configuration)
     DevState* st;
 };
 
@@ -94,6 +95,7 @@ struct EngineArgs {
     u32* status;               // engine status bits (zero before a launch)
     long long spin_limit;      // bound of one dependency wait, in clock cycles
     unsigned max_backoff_ns;   // longest sleep between two polls of a dependency counter
+    int any_reuse;             // some table of the launch reuses tombstones
     int inject_stall;          // testing: the first chunk waits for a count nothing reaches
 };
 
@@ -130,6 +132,7 @@ struct TableInfo {
     int growable;
     double alpha;
     u64 bound;  // upper bound on the number of non-empty cells
+    int reuse;  // tombstone reuse by inserts
 };
 TableInfo table_info(const cht_table* h);
 void table_set_bound(cht_table* h, u64 bound, bool exact);

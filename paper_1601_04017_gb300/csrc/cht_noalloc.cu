@@ -80,6 +80,7 @@ extern "C" cht_status cht_find_noalloc(cht_handle h, const uint64_t* keys, uint6
             cht::OpArgs a;
             a.cells = cells;
             a.log2c = log2c;
+            a.reuse = 0;  // finds never take cells
             a.keys = s_keys;
             a.vals = nullptr;
             a.vals_out = s_vals;

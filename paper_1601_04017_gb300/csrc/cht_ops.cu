@@ -6,13 +6,13 @@
 namespace cht {
 namespace {
 
-template <int G, int V, int MODE>
+template <int G, int V, int MODE, bool kReuse = false>
 cudaError_t launch_one(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     static std::atomic<int> occ{0};
     int per_sm = occ.load(std::memory_order_relaxed);
     if (per_sm == 0) {
         cudaError_t e =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, op_kernel<G, V, MODE>, kOpBlock, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, op_kernel<G, V, MODE, kReuse>, kOpBlock, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         occ.store(per_sm, std::memory_order_relaxed);
@@ -22,14 +22,27 @@ cudaError_t launch_one(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     const u64 need = (a.n + kOpBlock - 1) / kOpBlock;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    op_kernel<G, V, MODE><<<unsigned(grid), kOpBlock, 0, s>>>(a);
+    op_kernel<G, V, MODE, kReuse><<<unsigned(grid), kOpBlock, 0, s>>>(a);
     count_launch();
     return cudaGetLastError();
+}
+
+// Tombstone reuse (insert modes of a table that has it on): kernels exist for
+// the automatic windows only -- 1, 4 or 8 lanes of one 32-byte sector; any
+// other configured window takes the one of these with the nearest width.
+template <int MODE>
+cudaError_t launch_reuse(const OpArgs& a, int g, int ctas_per_sm, cudaStream_t s) {
+    if (g <= 2) return launch_one<1, 2, MODE, true>(a, ctas_per_sm, s);
+    if (g == 4) return launch_one<4, 2, MODE, true>(a, ctas_per_sm, s);
+    return launch_one<8, 2, MODE, true>(a, ctas_per_sm, s);
 }
 
 // (group width G, cells per lane V): G = 1 always loads a whole sector.
 template <int MODE>
 cudaError_t launch_mode(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStream_t s) {
+    if constexpr (MODE == kInsert || MODE == kIouAdd || MODE == kIouOverwrite) {
+        if (a.reuse) return launch_reuse<MODE>(a, g, ctas_per_sm, s);
+    }
     if (v == 2) {
         switch (g) {
             case 1: return launch_one<1, 2, MODE>(a, ctas_per_sm, s);
@@ -51,16 +64,16 @@ cudaError_t launch_mode(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStre
     }
 }
 
-template <int MODE, bool WD>
+template <int MODE, bool WD, bool RE>
 cudaError_t launch_agg(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     constexpr size_t smem = size_t(kAggSlots) * (8 + 8 + 4);
     static std::atomic<int> occ{0};
     int per_sm = occ.load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(iou_agg_kernel<MODE, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(iou_agg_kernel<MODE, WD, RE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smem));
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iou_agg_kernel<MODE, WD>, kAggBlock, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iou_agg_kernel<MODE, WD, RE>, kAggBlock, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         occ.store(per_sm, std::memory_order_relaxed);
@@ -70,7 +83,7 @@ cudaError_t launch_agg(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     const u64 nwin = (a.n + kAggWindow - 1) / kAggWindow;
     if (grid > nwin) grid = nwin;
     if (grid < 1) grid = 1;
-    iou_agg_kernel<MODE, WD><<<unsigned(grid), kAggBlock, smem, s>>>(a);
+    iou_agg_kernel<MODE, WD, RE><<<unsigned(grid), kAggBlock, smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
@@ -79,11 +92,21 @@ cudaError_t launch_agg(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
 
 cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, bool warp_dedup, int ctas_per_sm, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    if (mode == kIouAdd)
-        return warp_dedup ? launch_agg<kIouAdd, true>(a, ctas_per_sm, s) : launch_agg<kIouAdd, false>(a, ctas_per_sm, s);
-    if (mode == kIouOverwrite)
-        return warp_dedup ? launch_agg<kIouOverwrite, true>(a, ctas_per_sm, s)
-                          : launch_agg<kIouOverwrite, false>(a, ctas_per_sm, s);
+    const bool re = a.reuse != 0;
+    if (mode == kIouAdd) {
+        if (re)
+            return warp_dedup ? launch_agg<kIouAdd, true, true>(a, ctas_per_sm, s)
+                              : launch_agg<kIouAdd, false, true>(a, ctas_per_sm, s);
+        return warp_dedup ? launch_agg<kIouAdd, true, false>(a, ctas_per_sm, s)
+                          : launch_agg<kIouAdd, false, false>(a, ctas_per_sm, s);
+    }
+    if (mode == kIouOverwrite) {
+        if (re)
+            return warp_dedup ? launch_agg<kIouOverwrite, true, true>(a, ctas_per_sm, s)
+                              : launch_agg<kIouOverwrite, false, true>(a, ctas_per_sm, s);
+        return warp_dedup ? launch_agg<kIouOverwrite, true, false>(a, ctas_per_sm, s)
+                          : launch_agg<kIouOverwrite, false, false>(a, ctas_per_sm, s);
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -43,8 +43,12 @@ struct GroupConsts {
                                            : 0x00000001u;
 };
 
-// Outcome of a leader's atomic step.
-enum : int { kStepDoneNo = 0, kStepDoneYes = 1, kStepContinue = 2 };
+// Outcome of a leader's atomic step.  kStepRestart: a tombstone the probe
+// meant to reuse was taken by another key first -- probe again from the cell
+// after it; kStepDoneReused: inserted into a reused tombstone.
+enum : int { kStepDoneNo = 0, kStepDoneYes = 1, kStepContinue = 2, kStepRestart = 3, kStepDoneReused = 4 };
+
+constexpr u64 kNoPos = ~0ull;
 
 template <int MODE>
 __device__ __forceinline__ int modify_at(Cell* cp, bool is_key, u64 key, u64 d) {
@@ -72,6 +76,38 @@ __device__ __forceinline__ int modify_at(Cell* cp, bool is_key, u64 key, u64 d) 
         return kStepDoneNo;
     }
     return kStepContinue;
+}
+
+// Tombstone reuse (insert modes, reuse on): the probe has shown `key`
+// absent (it reached an empty cell or saw every cell) after passing the
+// tombstone at cp.  Claim it with a 16-byte CAS on the content read now.
+// Under phase semantics tombstones only change by such claims, so a cell that
+// is no longer a tombstone, or a failed CAS, means another key took the cell
+// (start again after it) or the same key did (then it is present: update it).
+template <int MODE>
+__device__ __forceinline__ int claim_tomb(Cell* cp, u64 key, u64 d) {
+    u64 ck, cv;
+    ld_cell_cg(cp, ck, cv);
+    if (ck != kTomb) {
+        if (ck != key) return kStepRestart;
+        if (MODE == kIouAdd) atomicAdd(&cp->val, d);
+        if (MODE == kIouOverwrite) atomicExch(&cp->val, d);
+        return kStepDoneNo;
+    }
+    Cell expect;
+    expect.key = kTomb;
+    expect.val = cv;
+    Cell desired;
+    desired.key = key;
+    desired.val = d;
+    const Cell old = cas_cell(cp, expect, desired);
+    if (old.key == kTomb && old.val == cv) return kStepDoneReused;
+    if (old.key == key) {
+        if (MODE == kIouAdd) atomicAdd(&cp->val, d);
+        if (MODE == kIouOverwrite) atomicExch(&cp->val, d);
+        return kStepDoneNo;
+    }
+    return kStepRestart;
 }
 
 // One warp runs the operations [next, end) of the batch with the group
@@ -111,13 +147,14 @@ __device__ __forceinline__ void op_vout(const OpArgs& a, const WarpStage& sg, u6
     else a.vals_out[idx] = v;
 }
 
-template <int G, int V, int MODE, bool kCoherent = false, bool kStaged = false>
+template <int G, int V, int MODE, bool kCoherent = false, bool kStaged = false, bool kReuse = false>
 __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 end, u64& n_ins, u64& n_del,
                                          u32& sbits, const WarpStage& sg = WarpStage{}) {
     constexpr u32 W = G * V;
     constexpr u32 FULL = 0xffffffffu;
     constexpr bool kModify = MODE != kFind;
     constexpr bool kHasVals = MODE == kInsert || MODE == kIouAdd || MODE == kIouOverwrite;
+    constexpr bool kInsLike = kHasVals;  // modes that may fill a cell
 
     const u64 cap = 1ull << a.log2c;
     const u64 cmask = cap - 1;
@@ -130,6 +167,10 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
 
     bool active = false;
     u64 idx = 0, key = 0, d = 0, pos = 0, probed = 0;
+    // tombstone reuse: tdist = 1 + the distance from the current key's home
+    // to the first tombstone on its path (0: none yet)
+    constexpr bool reuse = kInsLike && kReuse;
+    u64 tdist = 0;
 
     // Unstaged: the warp's next 64 keys (and values) are held in registers,
     // two windows of 32 -- lane j holds operation wbase + j of `cur` and
@@ -181,6 +222,7 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                         active = true;
                         pos = home_of(key, shift);
                         probed = 0;
+                        tdist = 0;
                     }
                 }
             }
@@ -272,6 +314,25 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
             gmatch = __shfl_sync(FULL, int(match), src) != 0;
             if (MODE == kFind) gval = __shfl_sync(FULL, hv, src);
         }
+        if (kInsLike && reuse) {
+            // first tombstone of the window at or after `first` (lanes hold
+            // the window's cells in order, so the lowest lane has it)
+            int toff = -1;
+            if (active) {
+                const u32 o0 = u32(gl) * V;
+                if (o0 >= first && k0 == kTomb) toff = int(o0);
+                else if (V == 2 && o0 + 1 >= first && k1 == kTomb) toff = int(o0 + 1);
+            }
+            if (G > 1) {
+                const u32 b = __ballot_sync(FULL, toff >= 0) & group_lanes;
+                const int src = b ? __ffs(b) - 1 : lane;
+                const int t2 = __shfl_sync(FULL, toff, src);
+                toff = b ? t2 : -1;
+            }
+            // only a tombstone before the deciding cell is on the path
+            if (active && tdist == 0 && toff >= 0 && (ghit < 0 || toff < ghit))
+                tdist = probed + u32(toff) - first + 1;
+        }
 
         int outcome = kStepContinue;
         if (active && ghit >= 0) {
@@ -282,7 +343,10 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                 }
                 active = false;
             } else if (gl == 0) {
-                outcome = modify_at<MODE>(a.cells + base + u32(ghit), gmatch, key, d);
+                if (kInsLike && !gmatch && tdist != 0)
+                    outcome = claim_tomb<MODE>(a.cells + ((home_of(key, shift) + tdist - 1) & cmask), key, d);
+                else
+                    outcome = modify_at<MODE>(a.cells + base + u32(ghit), gmatch, key, d);
             }
         }
         if (kModify && G > 1) outcome = __shfl_sync(FULL, outcome, g0);
@@ -295,13 +359,36 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                 if (outcome == kStepContinue) {
                     probed += u32(ghit) - first + 1;
                     pos = (base + u32(ghit) + 1) & cmask;
+                } else if (kInsLike && outcome == kStepRestart) {
+                    pos = (home_of(key, shift) + tdist) & cmask;
+                    probed = tdist;
+                    tdist = 0;
                 } else {
                     if (gl == 0) {
-                        op_code<kStaged>(a, sg, idx, (unsigned char)outcome);
+                        op_code<kStaged>(a, sg, idx, outcome == kStepDoneReused ? kYes : (unsigned char)outcome);
                         if (outcome == kStepDoneYes) {
                             if (MODE == kErase) ++n_del;
                             else ++n_ins;
                         }
+                        if (kInsLike && outcome == kStepDoneReused) --n_del;  // one tombstone fewer (mod 2^64)
+                    }
+                    active = false;
+                }
+            }
+            if (kInsLike && reuse && active && probed >= cap && tdist != 0) {
+                // every cell seen, no empty one and no key: take the tombstone
+                // (group-uniform branch: shuffle within the group only)
+                int fo = kStepContinue;
+                if (gl == 0) fo = claim_tomb<MODE>(a.cells + ((home_of(key, shift) + tdist - 1) & cmask), key, d);
+                if (G > 1) fo = __shfl_sync(group_lanes, fo, g0);
+                if (fo == kStepRestart) {
+                    pos = (home_of(key, shift) + tdist) & cmask;
+                    probed = tdist;
+                    tdist = 0;
+                } else {
+                    if (gl == 0) {
+                        op_code<kStaged>(a, sg, idx, fo == kStepDoneReused ? kYes : (unsigned char)fo);
+                        if (fo == kStepDoneReused) --n_del;
                     }
                     active = false;
                 }
@@ -341,7 +428,7 @@ __device__ __forceinline__ void warp_flush_counters(DevState* st, u64 n_ins, u64
     }
 }
 
-template <int G, int V, int MODE>
+template <int G, int V, int MODE, bool kReuse>
 __global__ void __launch_bounds__(kOpBlock) op_kernel(OpArgs a) {
     // each warp owns a contiguous slice of the batch
     const u64 warp = (u64(blockIdx.x) * kOpBlock + threadIdx.x) >> 5;
@@ -351,7 +438,7 @@ __global__ void __launch_bounds__(kOpBlock) op_kernel(OpArgs a) {
     const u64 end = begin + per < a.n ? begin + per : a.n;
     u64 n_ins = 0, n_del = 0;
     u32 sbits = 0;
-    warp_ops<G, V, MODE>(a, begin, end, n_ins, n_del, sbits);
+    warp_ops<G, V, MODE, false, false, kReuse>(a, begin, end, n_ins, n_del, sbits);
     warp_flush_counters(a.st, n_ins, n_del, sbits);
 }
 
@@ -380,44 +467,81 @@ constexpr int kAggWindow = 1024;
 constexpr int kAggSlots = 2048;
 
 // One operation on the global table by one thread (sector-wise probe).
-template <int MODE>
+template <int MODE, bool kReuse>
 __device__ __forceinline__ unsigned char global_modify(const OpArgs& a, u64 key, u64 d, u64 cap, u32 shift,
-                                                       u64& n_ins, u32& sbits) {
+                                                       u64& n_ins, u64& n_reused, u32& sbits) {
     const u64 cmask = cap - 1;
     u64 pos = home_of(key, shift), probed = 0;
-    while (probed < cap) {
-        const u64 base = pos & ~1ull;
-        const u32 first = u32(pos - base);
-        u64 k0, v0, k1, v1;
-        ld_pair_cg(a.cells + base, k0, v0, k1, v1);
-        int hit = -1;
-        bool match = false;
-        if (first == 0 && (k0 == key || k0 == kEmpty)) {
-            hit = 0;
-            match = k0 == key;
-        } else if (k1 == key || k1 == kEmpty) {
-            hit = 1;
-            match = k1 == key;
+    u64 tpos = kNoPos, tprobed = 0;  // tombstone reuse (a.reuse): first one on the path
+    for (;;) {
+        while (probed < cap) {
+            const u64 base = pos & ~1ull;
+            const u32 first = u32(pos - base);
+            u64 k0, v0, k1, v1;
+            ld_pair_cg(a.cells + base, k0, v0, k1, v1);
+            int hit = -1;
+            bool match = false;
+            if (first == 0 && (k0 == key || k0 == kEmpty)) {
+                hit = 0;
+                match = k0 == key;
+            } else if (k1 == key || k1 == kEmpty) {
+                hit = 1;
+                match = k1 == key;
+            }
+            if (kReuse && tpos == kNoPos) {  // first tombstone before the deciding cell
+                if (first == 0 && k0 == kTomb) {
+                    tpos = base & cmask;
+                    tprobed = probed + 1;
+                } else if (k1 == kTomb && hit < 0) {
+                    tpos = (base + 1) & cmask;
+                    tprobed = probed + 2 - first;
+                }
+            }
+            if (hit < 0) {
+                probed += 2 - first;
+                pos = (base + 2) & cmask;
+                continue;
+            }
+            const int out = (!match && tpos != kNoPos) ? claim_tomb<MODE>(a.cells + tpos, key, d)
+                                                       : modify_at<MODE>(a.cells + base + hit, match, key, d);
+            if (out == kStepContinue) {
+                probed += u32(hit) - first + 1;
+                pos = (base + u32(hit) + 1) & cmask;
+                continue;
+            }
+            if (out == kStepRestart) {
+                pos = (tpos + 1) & cmask;
+                probed = tprobed;
+                tpos = kNoPos;
+                continue;
+            }
+            if (out == kStepDoneYes) ++n_ins;
+            if (out == kStepDoneReused) {
+                ++n_reused;
+                return kYes;
+            }
+            return (unsigned char)out;
         }
-        if (hit < 0) {
-            probed += 2 - first;
-            pos = (base + 2) & cmask;
+        if (tpos == kNoPos) break;
+        // every cell seen, no empty one and no key: take the tombstone
+        const int out = claim_tomb<MODE>(a.cells + tpos, key, d);
+        if (out == kStepRestart) {
+            pos = (tpos + 1) & cmask;
+            probed = tprobed;
+            tpos = kNoPos;
             continue;
         }
-        const int out = modify_at<MODE>(a.cells + base + hit, match, key, d);
-        if (out == kStepContinue) {
-            probed += u32(hit) - first + 1;
-            pos = (base + u32(hit) + 1) & cmask;
-            continue;
+        if (out == kStepDoneReused) {
+            ++n_reused;
+            return kYes;
         }
-        if (out == kStepDoneYes) ++n_ins;
         return (unsigned char)out;
     }
     sbits |= kFull;
     return kCodeFull;
 }
 
-template <int MODE, bool WARP_DEDUP>
+template <int MODE, bool WARP_DEDUP, bool kReuse>
 __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
     extern __shared__ __align__(16) unsigned char agg_smem[];
     u64* const skey = reinterpret_cast<u64*>(agg_smem);
@@ -426,7 +550,7 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
     const u64 cap = 1ull << a.log2c;
     const u32 shift = 64u - a.log2c;
     const int tid = threadIdx.x;
-    u64 n_ins = 0;
+    u64 n_ins = 0, n_reused = 0;
     u32 sbits = 0;
     for (int s = tid; s < kAggSlots; s += kAggBlock) {
         skey[s] = kEmpty;
@@ -504,7 +628,7 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
         for (int s = tid; s < kAggSlots; s += kAggBlock) {
             const u64 k = skey[s];
             if (k == kEmpty) continue;
-            const unsigned char r = global_modify<MODE>(a, k, sval[s], cap, shift, n_ins, sbits);
+            const unsigned char r = global_modify<MODE, kReuse>(a, k, sval[s], cap, shift, n_ins, n_reused, sbits);
             if (a.codes) a.codes[w0 + slead[s]] = r;
             skey[s] = kEmpty;
             sval[s] = 0;
@@ -512,10 +636,14 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
         __syncthreads();
     }
     constexpr u32 FULL = 0xffffffffu;
-    for (int o = 16; o > 0; o >>= 1) n_ins += __shfl_xor_sync(FULL, n_ins, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        n_ins += __shfl_xor_sync(FULL, n_ins, o);
+        n_reused += __shfl_xor_sync(FULL, n_reused, o);
+    }
     const u32 any_status = __reduce_or_sync(FULL, sbits);
     if ((tid & 31) == 0) {
         if (n_ins) atomicAdd(&a.st->I, n_ins);
+        if (n_reused) atomicAdd(&a.st->D, 0ull - n_reused);  // reused tombstones: D falls
         if (any_status) atomicOr(&a.st->status, any_status);
     }
 }

@@ -168,6 +168,7 @@ cht_config default_config() {
     c.migrate_tile = 0;
     c.alpha = 0.5;
     c.iou_aggregate = 1;
+    c.reuse_tombstones = 0;
     return c;
 }
 
@@ -180,6 +181,7 @@ bool valid_config(const cht_config& c) {
     if (t != 0 && (t < 64 || t > 8192 || (t & (t - 1)) != 0)) return false;
     if (!(c.alpha > 0.0 && c.alpha < 1.0)) return false;
     if (c.iou_aggregate < 0 || c.iou_aggregate > 2) return false;
+    if (c.reuse_tombstones < 0 || c.reuse_tombstones > 1) return false;
     return true;
 }
 
@@ -311,6 +313,7 @@ cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals
     cht::OpArgs a;
     a.cells = h->cells;
     a.log2c = h->log2c;
+    a.reuse = u32(h->cfg.reuse_tombstones);
     a.keys = keys;
     a.vals = vals;
     a.vals_out = vals_out;
@@ -553,6 +556,7 @@ TableInfo table_info(const cht_table* h) {
     i.growable = h->growable;
     i.alpha = h->cfg.alpha;
     i.bound = h->i_bound;
+    i.reuse = h->cfg.reuse_tombstones;
     return i;
 }
 
@@ -898,6 +902,8 @@ cht::EngineArgs plan_args(const cht_plan* p) {
     e.spin_limit = (p->cfg.spin_limit_us > 0 ? (long long)p->cfg.spin_limit_us : 1000000ll) * 2000;  // ~2 GHz
     e.inject_stall = p->cfg.fault_inject & 1;
     e.max_backoff_ns = p->cfg.poll_ns > 0 ? unsigned(p->cfg.poll_ns) : 8192u;
+    e.any_reuse = 0;
+    for (const cht_table* h : p->tables) e.any_reuse |= h->cfg.reuse_tombstones;
     return e;
 }
 
@@ -997,7 +1003,7 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
     for (size_t t = 0; t < p->tables.size(); ++t) {
         tabs[t].cells = p->tables[t]->cells;
         tabs[t].log2c = p->tables[t]->log2c;
-        tabs[t].pad = 0;
+        tabs[t].reuse = u32(p->tables[t]->cfg.reuse_tombstones);
         tabs[t].st = p->tables[t]->st;
     }
     DeviceGuard g(p->tables.empty() ? current_device() : p->device);

@@ -162,8 +162,8 @@ def test_plan_rejects_inputs_overlapping_outputs(cuda_lib):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("chunk", [0, 32, 256])
-def test_engine_chain_of_small_batches(cuda_lib, oracle_mod, chunk):
+@pytest.mark.parametrize("chunk,reuse", [(0, 0), (32, 0), (256, 0), (0, 1), (32, 1)])
+def test_engine_chain_of_small_batches(cuda_lib, oracle_mod, chunk, reuse):
     """One table, a long chain of small dependent batches of every kind (the
     engine runs runs of one-item levels in one warp) plus a second table with
     larger batches interleaved; results and final contents vs the oracle."""
@@ -187,7 +187,9 @@ def test_engine_chain_of_small_batches(cuda_lib, oracle_mod, chunk):
     vout = torch.full((total,), -1, dtype=torch.int64, device="cuda")
     codes = torch.full((total,), 255, dtype=torch.uint8, device="cuda")
     tables = [cuda_lib.Table(1 << 12), cuda_lib.Table(1 << 13)]
-    otabs = [oracle_mod.OracleTable(1 << 12), oracle_mod.OracleTable(1 << 13)]
+    if reuse:
+        tables[0].set_config(reuse_tombstones=1)  # one table with reuse, one without, in one launch
+    otabs = [oracle_mod.OracleTable(1 << 12, reuse_tombstones=bool(reuse)), oracle_mod.OracleTable(1 << 13)]
     ops, spans, o = [], [], 0
     for t, op, k, v in specs:
         n = k.size
