@@ -251,7 +251,23 @@ cudaError_t launch_engine_gv(const EngineArgs& e, bool staged, int ctas_per_sm, 
                   : launch_engine_gvs<G, V, false>(e, ctas_per_sm, s);
 }
 
+__global__ void snapshot_kernel(const EngineTable* tables, const u32* touched, u32 n, unsigned long long* out) {
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const DevState* st = tables[touched[i]].st;
+        out[2 * i] = st->I;
+        out[2 * i + 1] = st->D;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_snapshot(const EngineTable* tables, const u32* touched, u32 n, unsigned long long* out,
+                            cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    snapshot_kernel<<<(n + 255) / 256, 256, 0, s>>>(tables, touched, n, out);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, bool staged,
                           cudaStream_t s) {

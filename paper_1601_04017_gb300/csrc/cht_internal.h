@@ -104,6 +104,11 @@ struct EngineArgs {
 cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, bool staged,
                           cudaStream_t s);
 
+// out[2i], out[2i+1] = I, D of tables[touched[i]] (i < n), read after the
+// work before it on the stream.
+cudaError_t launch_snapshot(const EngineTable* tables, const u32* touched, u32 n, unsigned long long* out,
+                            cudaStream_t s);
+
 }  // namespace cht
 
 #include <vector>

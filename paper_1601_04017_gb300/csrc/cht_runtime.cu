@@ -420,41 +420,49 @@ constexpr double kOpsPerUs = 30000.0;
 // Longest run of one-item levels one warp runs in sequence.
 constexpr u32 kMaxGroup = 4096;
 
-double chain_us(const std::vector<u64>& sizes, u32 chunk) {
-    double t = 0;
-    for (u64 n : sizes) t += kRoundUs + kLaneOpUs * double((std::min<u64>(n, chunk) + 31) / 32);
-    return t;
-}
 
 }  // namespace
 
 u64 plan_order(const std::vector<EngineBatch>& batches, size_t n_tables, int chunk_ops,
                std::vector<EngineChunk>& chunks) {
-    // Per table: a batch's dependency level.  A find right after a find of
-    // the same table does not wait for it (finds do not modify the table, so
-    // both see the state after the last modifying batch): it joins the
-    // level of the run of finds it belongs to.
-    std::vector<u32> rounds(n_tables, 0), round_of(batches.size());
-    std::vector<u32> level_of(batches.size()), levels(n_tables, 0);
+    const size_t nb = batches.size();
+    constexpr u32 kNone = ~0u;
+    // Dependency levels.  A find right after a find of the same table does
+    // not wait for it (finds do not modify the table, so both see the state
+    // after the last modifying batch): it joins the level of the run of finds
+    // it belongs to.  Levels get global ids in batch order; per level: its
+    // table, first batch, number of batches, largest batch, and the next
+    // level of the same table.
+    std::vector<u32> round_of(nb), level_of(nb), rounds(n_tables, 0), cur_level(n_tables, kNone);
     std::vector<char> last_find(n_tables, 0);
-    std::vector<std::vector<u64>> level_ops(n_tables);     // largest batch per level
-    std::vector<std::vector<u32>> level_first(n_tables);   // first batch of each level
-    std::vector<std::vector<u32>> level_batches(n_tables); // batches per level
-    for (size_t b = 0; b < batches.size(); ++b) {
+    std::vector<u32> lv_table, lv_first, lv_count, lv_next;
+    std::vector<u64> lv_ops;
+    lv_table.reserve(nb);
+    lv_first.reserve(nb);
+    lv_count.reserve(nb);
+    lv_next.reserve(nb);
+    lv_ops.reserve(nb);
+    for (size_t b = 0; b < nb; ++b) {
         const u32 t = batches[b].table;
         round_of[b] = rounds[t]++;
         const bool find = batches[b].mode == kFind;
         if (!(find && last_find[t])) {
-            ++levels[t];
-            level_ops[t].push_back(0);
-            level_first[t].push_back(u32(b));
-            level_batches[t].push_back(0);
+            const u32 L = u32(lv_table.size());
+            if (cur_level[t] != kNone) lv_next[cur_level[t]] = L;
+            lv_table.push_back(t);
+            lv_first.push_back(u32(b));
+            lv_count.push_back(0);
+            lv_next.push_back(kNone);
+            lv_ops.push_back(0);
+            cur_level[t] = L;
         }
-        level_of[b] = levels[t] - 1;
-        level_ops[t].back() = std::max(level_ops[t].back(), batches[b].n);
-        ++level_batches[t].back();
+        const u32 L = cur_level[t];
+        level_of[b] = L;
+        ++lv_count[L];
+        lv_ops[L] = std::max(lv_ops[L], batches[b].n);
         last_find[t] = find;
     }
+    const size_t nl = lv_table.size();
     // work-item size per table
     std::vector<u32> chunk_of(n_tables, kChunkOps);
     if (chunk_ops > 0) {
@@ -463,45 +471,51 @@ u64 plan_order(const std::vector<EngineBatch>& batches, size_t n_tables, int chu
         u64 total = 0;
         for (const EngineBatch& eb : batches) total += eb.n;
         const double work_us = double(total) / kOpsPerUs;
-        for (size_t t = 0; t < n_tables; ++t) {
-            u32 c = kChunkOps;
-            while (c > 32 && chain_us(level_ops[t], c) > work_us) c /= 2;
-            chunk_of[t] = c;
-        }
-    }
-    // Groups: runs of consecutive one-item levels (one batch of at most one
-    // item).  group_len[t][l] = levels in the group that starts at level l
-    // (0 for the other levels of a group, 1 for a level on its own).
-    std::vector<std::vector<u32>> group_len(n_tables);
-    for (size_t t = 0; t < n_tables; ++t) {
-        const u32 nl = levels[t];
-        group_len[t].assign(nl, 1);
-        u32 l = 0;
-        while (l < nl) {
-            auto single = [&](u32 k) { return level_batches[t][k] == 1 && level_ops[t][k] <= chunk_of[t]; };
-            if (!single(l)) {
-                ++l;
-                continue;
+        // chain length per table at items of 256 / 128 / 64 / 32 operations
+        std::vector<double> chain(4 * n_tables, 0.0);
+        for (size_t L = 0; L < nl; ++L)
+            for (int j = 0; j < 4; ++j) {
+                const u64 c = u64(kChunkOps) >> j;
+                chain[4 * lv_table[L] + j] += kRoundUs + kLaneOpUs * double((std::min<u64>(lv_ops[L], c) + 31) / 32);
             }
-            u32 e = l + 1;
-            while (e < nl && single(e) && e - l < kMaxGroup) ++e;
-            group_len[t][l] = e - l;
-            for (u32 k = l + 1; k < e; ++k) group_len[t][k] = 0;
-            l = e;
+        for (size_t t = 0; t < n_tables; ++t) {
+            int j = 0;
+            while (j < 3 && chain[4 * t + j] > work_us) ++j;
+            chunk_of[t] = kChunkOps >> j;
         }
     }
+    // Groups: runs of consecutive one-item levels of a table (one batch of at
+    // most one item).  group_len[L] = levels in the group led by L, 0 for the
+    // other levels of a group, 1 for a level on its own.
+    std::vector<u32> group_len(nl, 1), open(n_tables, kNone);
+    for (size_t L = 0; L < nl; ++L) {
+        const u32 t = lv_table[L];
+        const bool single = lv_count[L] == 1 && lv_ops[L] <= chunk_of[t];
+        if (!single) {
+            open[t] = kNone;
+        } else if (open[t] != kNone && group_len[open[t]] < kMaxGroup) {
+            ++group_len[open[t]];
+            group_len[L] = 0;
+        } else {
+            open[t] = u32(L);
+        }
+    }
+    // batches in round order (stable counting sort)
     const u32 n_rounds = n_tables ? *std::max_element(rounds.begin(), rounds.end()) : 0;
-    std::vector<std::vector<u32>> by_round(n_rounds);
-    for (u32 b = 0; b < batches.size(); ++b) by_round[round_of[b]].push_back(b);
-    // items of each table, counted as they are emitted (followers when their
-    // leader is); the items before a level are what its batches need
+    std::vector<u32> start(size_t(n_rounds) + 1, 0), order(nb);
+    for (size_t b = 0; b < nb; ++b) ++start[round_of[b] + 1];
+    for (u32 r = 0; r < n_rounds; ++r) start[r + 1] += start[r];
+    for (size_t b = 0; b < nb; ++b) order[start[round_of[b]]++] = u32(b);
+    // Emit.  Items of each table are counted as they are emitted (followers
+    // when their leader is); the items before a level are what it needs.
     std::vector<u64> items_so_far(n_tables, 0), level_need(n_tables, 0);
-    std::vector<u32> cur_level(n_tables, ~0u);
+    std::vector<u32> emit_level(n_tables, kNone);
     std::vector<EngineChunk> followers;
     chunks.clear();
-    auto item = [](u64 start, u64 need, u32 b, u64 count) {
+    chunks.reserve(nb);
+    auto item = [](u64 first, u64 need, u32 b, u64 count) {
         EngineChunk ch;
-        ch.start = start;
+        ch.start = first;
         ch.need = need;
         ch.batch = b;
         ch.count = uint16_t(count);
@@ -510,35 +524,34 @@ u64 plan_order(const std::vector<EngineBatch>& batches, size_t n_tables, int chu
         ch.pad = 0;
         return ch;
     };
-    for (u32 r = 0; r < n_rounds; ++r) {
-        for (const u32 b : by_round[r]) {
-            const EngineBatch& eb = batches[b];
-            const u32 t = eb.table;
-            const u32 lv = level_of[b];
-            const u32 glen = group_len[t][lv];
-            if (glen == 0) continue;  // runs as a follower of its group's leader
-            if (lv != cur_level[t]) {  // a new level: wait for all earlier items
-                cur_level[t] = lv;
-                level_need[t] = items_so_far[t];
-            }
-            if (glen > 1) {
-                EngineChunk lead = item(0, level_need[t], b, eb.n);
-                lead.nfollow = uint16_t(glen - 1);
-                lead.follow_first = u32(followers.size());  // made absolute below
-                chunks.push_back(lead);
-                ++items_so_far[t];
-                for (u32 k = 1; k < glen; ++k) {
-                    const u32 fb = level_first[t][lv + k];
-                    followers.push_back(item(0, 0, fb, batches[fb].n));
-                    ++items_so_far[t];
-                }
-                continue;
-            }
-            const u32 c = chunk_of[t];
-            for (u64 s0 = 0; s0 < eb.n; s0 += c)
-                chunks.push_back(item(s0, level_need[t], b, eb.n - s0 < c ? eb.n - s0 : c));
-            items_so_far[t] += (eb.n + c - 1) / c;
+    for (const u32 b : order) {
+        const EngineBatch& eb = batches[b];
+        const u32 t = eb.table;
+        const u32 L = level_of[b];
+        const u32 glen = group_len[L];
+        if (glen == 0) continue;  // runs as a follower of its group's leader
+        if (L != emit_level[t]) {  // a new level: wait for all earlier items
+            emit_level[t] = L;
+            level_need[t] = items_so_far[t];
         }
+        if (glen > 1) {
+            EngineChunk lead = item(0, level_need[t], b, eb.n);
+            lead.nfollow = uint16_t(glen - 1);
+            lead.follow_first = u32(followers.size());  // made absolute below
+            chunks.push_back(lead);
+            ++items_so_far[t];
+            u32 f = L;
+            for (u32 k = 1; k < glen; ++k) {
+                f = lv_next[f];
+                const u32 fb = lv_first[f];
+                followers.push_back(item(0, 0, fb, batches[fb].n));
+                ++items_so_far[t];
+            }
+            continue;
+        }
+        const u32 c = chunk_of[t];
+        for (u64 s0 = 0; s0 < eb.n; s0 += c) chunks.push_back(item(s0, level_need[t], b, eb.n - s0 < c ? eb.n - s0 : c));
+        items_so_far[t] += (eb.n + c - 1) / c;
     }
     const u64 n_queue = chunks.size();
     for (EngineChunk& ch : chunks)

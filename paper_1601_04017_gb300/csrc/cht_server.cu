@@ -379,20 +379,28 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
                 tnew.push_back(step_new[b.table]);
             }
     }
+    // One upload holds the step's metadata: tables, batches, work items, the
+    // engine's counters (zero), the touched tables' indices; the snapshot of
+    // their counts is gathered on the device after the engine and read back
+    // with one copy.
     const u64 b_tabs = nt * sizeof(cht::EngineTable), b_bat = batches.size() * sizeof(cht::EngineBatch);
     const u64 b_chk = chunks.size() * sizeof(cht::EngineChunk), b_cnt = (2 + nt) * sizeof(unsigned long long);
+    const u64 b_tch = touched.size() * sizeof(u32), b_snap = touched.size() * 16;
     const u64 o_bat = (b_tabs + 255) & ~255ull, o_chk = o_bat + ((b_bat + 255) & ~255ull);
-    const u64 o_cnt = o_chk + ((b_chk + 255) & ~255ull), o_snap = o_cnt + ((b_cnt + 255) & ~255ull);
-    const u64 total_meta = o_snap + touched.size() * 16;
+    const u64 o_cnt = o_chk + ((b_chk + 255) & ~255ull), o_tch = o_cnt + ((b_cnt + 255) & ~255ull);
+    const u64 o_snap = o_tch + ((b_tch + 255) & ~255ull);
+    const u64 total_meta = o_snap + b_snap;
     u64 hoff = 0, doff = 0;
-    if (!s->mring.alloc(total_meta, &hoff) || !s->dring.alloc(o_snap, &doff)) return CHT_ERR_OOM;
+    if (!s->mring.alloc(total_meta, &hoff) || !s->dring.alloc(total_meta, &doff)) return CHT_ERR_OOM;
     unsigned char* hm = s->meta + hoff;
     unsigned char* dm = s->dmeta + doff;
     memcpy(hm, tabs.data(), b_tabs);
     memcpy(hm + o_bat, batches.data(), b_bat);
     memcpy(hm + o_chk, chunks.data(), b_chk);
-    if (cudaMemcpyAsync(dm, hm, o_cnt, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
-    if (cudaMemsetAsync(dm + o_cnt, 0, b_cnt, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
+    memset(hm + o_cnt, 0, b_cnt);
+    memcpy(hm + o_tch, touched.data(), b_tch);
+    if (cudaMemcpyAsync(dm, hm, o_tch + b_tch, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        return CHT_ERR_CUDA;
     cht::EngineArgs e;
     e.tables = reinterpret_cast<const cht::EngineTable*>(dm);
     e.batches = reinterpret_cast<const cht::EngineBatch*>(dm + o_bat);
@@ -438,12 +446,14 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
             return CHT_ERR_CUDA;
     }
     st.snap = reinterpret_cast<unsigned long long*>(hm + o_snap);
-    for (size_t k = 0; k < touched.size(); ++k) {
-        // DevState starts with I then D
-        if (cudaMemcpyAsync(st.snap + 2 * k, tabs[touched[k]].st, 16, cudaMemcpyDeviceToHost, s->stream) !=
-            cudaSuccess)
-            return CHT_ERR_CUDA;
+    if (cht::launch_snapshot(reinterpret_cast<const cht::EngineTable*>(dm), reinterpret_cast<const u32*>(dm + o_tch),
+                             u32(touched.size()), reinterpret_cast<unsigned long long*>(dm + o_snap),
+                             s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CHT_ERR_CUDA;
     }
+    if (cudaMemcpyAsync(st.snap, dm + o_snap, b_snap, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+        return CHT_ERR_CUDA;
     if (!s->spare_events.empty()) {
         st.ev = s->spare_events.back();
         s->spare_events.pop_back();
