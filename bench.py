@@ -623,8 +623,11 @@ extern "C" float run_rr(const void* buf, u64 bytes, u64 n, int width, u64* out, 
   if (width == 32) rr<32><<<grid, 256>>>((const unsigned char*)buf, mask, n, out);
   if (width == 64) rr<64><<<grid, 256>>>((const unsigned char*)buf, mask, n, out);
   if (width == 128) rr<128><<<grid, 256>>>((const unsigned char*)buf, mask, n, out);
+  if (width == 256) rr<256><<<grid, 256>>>((const unsigned char*)buf, mask, n, out);
+  if (width == 512) rr<512><<<grid, 256>>>((const unsigned char*)buf, mask, n, out);
   cudaEventRecord(b); cudaEventSynchronize(b); float ms = 0; cudaEventElapsedTime(&ms, a, b);
-  cudaEventDestroy(a); cudaEventDestroy(b); return cudaGetLastError() == cudaSuccess ? ms : -1.0f;
+  cudaEventDestroy(a); cudaEventDestroy(b);
+  return cudaGetLastError() == cudaSuccess ? ms : -1.0f;
 }
 """
 
@@ -657,7 +660,7 @@ def probe_random_access():
     for log2b in (24, 32):
         nbytes = 1 << log2b
         buf = torch.randint(0, 1 << 62, (nbytes // 8,), dtype=torch.int64, device="cuda")
-        for width in (16, 32, 64, 128):
+        for width in (16, 32, 64, 128, 256, 512):
             n = (1 << 32) // width
             lib.run_rr(buf.data_ptr(), nbytes, n, width, out.data_ptr(), grid)
             ms = lib.run_rr(buf.data_ptr(), nbytes, n, width, out.data_ptr(), grid)
@@ -745,11 +748,11 @@ def run_batched(args):
     # sampled tables against the oracle (the whole plan's results)
     verified = verify_batched_sample(wl, tables, keys, vout, codes, args.batched_verify)
     percall = []
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(0 if args.batched_engine_only else max(1, min(args.steps, 2))):
         clear_all()
         percall.append(timed(per_call))
     graph_ms = None
-    if not args.no_graph_baseline:
+    if not args.no_graph_baseline and not args.batched_engine_only:
         try:
             clear_all()
             g = torch.cuda.CUDAGraph()
@@ -768,7 +771,8 @@ def run_batched(args):
         "table_bytes": int(wl["capacity"].sum()) * 16,
         "engine": {"ms": round(ms, 3), "mops": round(total / (ms * 1e-3) / 1e6, 1), "launches_per_run": 1,
                    "autotuned": cfg, "autotune_best_ms": round(tuned_ms, 3), "plan_build_s": round(plan_build_s, 2)},
-        "per_call": {"ms": round(statistics.median(percall), 3),
+        "per_call": None if not percall else
+                    {"ms": round(statistics.median(percall), 3),
                      "mops": round(total / (statistics.median(percall) * 1e-3) / 1e6, 1), "launches_per_run": nb},
         "per_call_graph": (graph_ms if not isinstance(graph_ms, float) else
                            {"ms": round(graph_ms, 3), "mops": round(total / (graph_ms * 1e-3) / 1e6, 1)}),
@@ -944,6 +948,8 @@ def main():
     ap.add_argument("--batched-log2-max", type=int, default=20)
     ap.add_argument("--batched-verify", type=int, default=16)
     ap.add_argument("--no-graph-baseline", action="store_true")
+    ap.add_argument("--batched-engine-only", action="store_true",
+                    help="time the engine only (no per-batch launch baselines), e.g. for profiling")
     ap.add_argument("--serving-requests", type=int, default=100_000)
     ap.add_argument("--serving-loads", type=float, nargs="*", default=[0.5, 0.7, 0.9])
     ap.add_argument("--serving-reuse-tombstones", type=int, default=1, choices=[0, 1],
