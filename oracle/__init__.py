@@ -63,6 +63,7 @@ def _load():
             "or_migrate": (ctypes.c_int, [p, u64]),
             "or_insert": (None, [p, p, p, u64, p]),
             "or_insert_or_update": (None, [p, p, p, u64, ctypes.c_int, p]),
+            "or_update": (None, [p, p, p, u64, ctypes.c_int, p]),
             "or_find": (None, [p, p, u64, p, p]),
             "or_erase": (None, [p, p, u64, p]),
             "or_export": (u64, [p, p, p, u64]),
@@ -172,6 +173,14 @@ class OracleTable:
         assert k.shape == v.shape
         f = np.zeros(k.size, dtype=np.uint8)
         self._lib.or_insert_or_update(self._t, _ptr(k), _ptr(v), k.size, int(op), _ptr(f))
+        return f
+
+    def update(self, keys, vals, op: int = ADD) -> np.ndarray:
+        """update (Sec. 3): change the value of present keys; 1 = updated, 0 = absent."""
+        k, v = _u64(keys), _u64(vals)
+        assert k.shape == v.shape
+        f = np.zeros(k.size, dtype=np.uint8)
+        self._lib.or_update(self._t, _ptr(k), _ptr(v), k.size, int(op), _ptr(f))
         return f
 
     def find(self, keys):

@@ -268,6 +268,35 @@ void or_insert_or_update(or_table *t, const uint64_t *keys, const uint64_t *vals
     }
 }
 
+/* update (Sec. 3 interface: update(x, d, up)): probe from home like find; at
+ * the cell holding k set value <- up(value, d) (overwrite: d; add: value + d
+ * mod 2^64) and report 1; reaching an empty cell (or seeing every cell)
+ * means k is absent: report 0 and change nothing.  Never fills a cell. */
+void or_update(or_table *t, const uint64_t *keys, const uint64_t *vals, uint64_t n, int op, uint8_t *flags)
+{
+    uint64_t mask = t->cap - 1;
+    for (uint64_t j = 0; j < n; ++j) {
+        uint64_t k = keys[j];
+        int r = OR_NO;
+        if (is_reserved(k)) {
+            r = OR_RESERVED;
+        } else {
+            uint64_t i = home_of(k, t->log2c);
+            for (uint64_t step = 0; step < t->cap; ++step, i = (i + 1) & mask) {
+                or_cell *c = &t->cells[i];
+                t->probes++;
+                if (c->key == OR_EMPTY) break;
+                if (c->key == k) {
+                    c->val = (op == OR_ADD) ? c->val + vals[j] : vals[j];
+                    r = OR_YES;
+                    break;
+                }
+            }
+        }
+        if (flags) flags[j] = (uint8_t)r;
+    }
+}
+
 /* find (Sec. 3 "Lookup"): probe from home until the key (hit, copy of the
  * value) or an empty cell (miss; value 0).  Writes nothing to the table. */
 void or_find(or_table *t, const uint64_t *keys, uint64_t n, uint64_t *vals_out, uint8_t *flags)

@@ -41,6 +41,14 @@ class DictModel:
         self.d[k] = v
         return 1
 
+    def update(self, k, v, op):
+        if self.reserved(k):
+            return 3
+        if k in self.d:
+            self.d[k] = (self.d[k] + v) & MASK if op == 1 else v
+            return 1
+        return 0
+
     def find(self, k):
         if self.reserved(k):
             return 0, 3
@@ -87,7 +95,7 @@ def test_oracle_matches_dictionary(oracle_mod, log2c, seed, reuse):
     t = oracle_mod.OracleTable(c, reuse_tombstones=reuse)
     m = DictModel()
     for step in range(40):
-        kind = rng.choice(["insert", "iou_add", "iou_ow", "find", "erase"])
+        kind = rng.choice(["insert", "iou_add", "iou_ow", "find", "erase", "upd_add", "upd_ow"])
         # keep the number of inserted cells (tombstones count) below c
         if kind in ("insert", "iou_add", "iou_ow") and t.nonempty > c - len(pool):
             kind = "find"
@@ -100,6 +108,11 @@ def test_oracle_matches_dictionary(oracle_mod, log2c, seed, reuse):
             op = 1 if kind == "iou_add" else 0
             f = t.insert_or_update(ks, vs, op)
             exp = [m.iou(int(k), int(v), op) for k, v in zip(ks, vs)]
+            assert f.tolist() == exp
+        elif kind in ("upd_add", "upd_ow"):
+            op = 1 if kind == "upd_add" else 0
+            f = t.update(ks, vs, op)
+            exp = [m.update(int(k), int(v), op) for k, v in zip(ks, vs)]
             assert f.tolist() == exp
         elif kind == "find":
             v, f = t.find(ks)
@@ -114,6 +127,34 @@ def test_oracle_matches_dictionary(oracle_mod, log2c, seed, reuse):
         ek, ev = t.export()
         assert dict(zip((int(x) for x in ek), (int(x) for x in ev))) == m.d
         assert t.live == len(m.d)
+
+
+def test_update_add_equals_sorted_reduction_over_present_keys(oracle_mod):
+    """update(add) of a batch with repeats: every present key gains the sum of
+    its batch values (sort + run-length sums), absent keys stay absent."""
+    c = 1 << 10
+    t = oracle_mod.OracleTable(c)
+    present = W.uniform_keys(200, seed=21)
+    t.insert(present, np.zeros(200, np.uint64))
+    rng = np.random.default_rng(22)
+    pool = np.concatenate([present, W.uniform_keys(100, start=5000, seed=21)])
+    ks = pool[rng.integers(0, pool.size, 3000)]
+    vs = rng.integers(0, 1 << 40, ks.size).astype(np.uint64)
+    f = t.update(ks, vs, oracle_mod.ADD)
+    pset = set(present.tolist())
+    assert [int(x) for x in f] == [1 if int(k) in pset else 0 for k in ks]
+    order = np.argsort(ks, kind="stable")
+    sk, sv = ks[order], vs[order]
+    starts = np.flatnonzero(np.r_[True, sk[1:] != sk[:-1]])
+    sums = np.add.reduceat(sv, starts)
+    got_v, got_f = t.find(sk[starts])
+    for k, sm, gv, gf in zip(sk[starts], sums, got_v, got_f):
+        if int(k) in pset:
+            assert gf == 1 and int(gv) == int(sm)
+        else:
+            assert gf == 0
+    assert t.live == 200 and t.nonempty == 200
+    t.assert_invariants()
 
 
 def test_wraparound_cluster_is_used(oracle_mod):
