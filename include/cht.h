@@ -150,6 +150,16 @@ cht_status cht_insert_or_update(cht_handle h, const uint64_t *keys, const uint64
                                 uint64_t n, cht_update_op op, uint8_t *inserted,
                                 cht_stream_t stream);
 
+/* update (Sec. 3, update(x, d, up)): if keys[i] is present, change its value
+ * by `op` (CHT_ADD: fetch-and-add d; CHT_OVERWRITE: store d) and report 1;
+ * if absent, report 0 and change nothing (3 for a reserved key).  Never fills
+ * a cell, so it never grows the table.  Every operation on a present key
+ * reports 1; with CHT_ADD the final value is the previous one plus the sum
+ * of the batch's d for that key, mod 2^64; with CHT_OVERWRITE it is one of
+ * those d.  keys/vals: n u64 each; updated: n u8 result codes or NULL. */
+cht_status cht_update(cht_handle h, const uint64_t *keys, const uint64_t *vals, uint64_t n,
+                      cht_update_op op, uint8_t *updated, cht_stream_t stream);
+
 /* erase (Sec. 4.4): replace the key of the cell holding keys[i] by the
  * tombstone (value kept).  For a present key exactly one of the batch's
  * operations on it reports 1.  Tombstones keep occupying their cells until
@@ -212,7 +222,9 @@ typedef enum {
     CHT_OP_INSERT = 1,
     CHT_OP_IOU_ADD = 2,
     CHT_OP_IOU_OVERWRITE = 3,
-    CHT_OP_ERASE = 4
+    CHT_OP_ERASE = 4,
+    CHT_OP_UPDATE_ADD = 5,
+    CHT_OP_UPDATE_OVERWRITE = 6
 } cht_op_kind;
 
 typedef struct {

@@ -49,6 +49,7 @@ class ChtConfig(ctypes.Structure):
 
 
 OP_FIND, OP_INSERT, OP_IOU_ADD, OP_IOU_OVERWRITE, OP_ERASE = 0, 1, 2, 3, 4
+OP_UPDATE_ADD, OP_UPDATE_OVERWRITE = 5, 6
 PLAN_TIMEOUT = 0x1
 
 
@@ -111,6 +112,7 @@ def load_library(build: bool = True):
             "cht_insert": (i32, [p, p, p, u64, p, p]),
             "cht_find": (i32, [p, p, u64, p, p, p]),
             "cht_insert_or_update": (i32, [p, p, p, u64, i32, p, p]),
+            "cht_update": (i32, [p, p, p, u64, i32, p, p]),
             "cht_erase": (i32, [p, p, u64, p, p]),
             "cht_migrate": (i32, [p, u64, p]),
             "cht_size": (i32, [p, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64), p]),
@@ -267,6 +269,14 @@ class Table:
         _check(self._lib.cht_insert_or_update(self._h, kp, vp, n, int(op), cp, _stream(stream)),
                "cht_insert_or_update")
         return inserted
+
+    def update(self, keys, vals, op: int = ADD, updated=None, stream=None):
+        """cht_update: change the values of present keys (1 = updated, 0 = absent)."""
+        kp, n, _ = _ptr(keys, 8, what="keys")
+        vp, _, _ = _ptr(vals, 8, n, "vals")
+        cp, _, _ = _ptr(updated, 1, n, "updated")
+        _check(self._lib.cht_update(self._h, kp, vp, n, int(op), cp, _stream(stream)), "cht_update")
+        return updated
 
     def erase(self, keys, erased=None, stream=None):
         kp, n, _ = _ptr(keys, 8, what="keys")

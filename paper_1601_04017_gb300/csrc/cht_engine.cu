@@ -97,13 +97,17 @@ __device__ __forceinline__ void engine_run(int mode, const OpArgs& a, u64 first,
             if (re) engine_window<G, V, kIouOverwrite, kStaged, true>(a, first, end, n_ins, n_del, sbits, sg);
             else engine_window<G, V, kIouOverwrite, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg);
             break;
+        case kUpdAdd: engine_window<G, V, kUpdAdd, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg); break;
+        case kUpdOverwrite:
+            engine_window<G, V, kUpdOverwrite, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg);
+            break;
         default: engine_window<G, V, kErase, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg); break;
     }
 }
 
 // Copy one item's keys (and values) into the warp's staging area.
 __device__ __forceinline__ void stage_in(const EngineChunk& ch, const EngineBatch& b, const WarpStage& sg, int lane) {
-    const bool has_vals = b.mode == kInsert || b.mode == kIouAdd || b.mode == kIouOverwrite;
+    const bool has_vals = mode_has_vals(int(b.mode));
     for (u32 j = lane; j < ch.count; j += 32) {
         sg.keys[j] = ld_stream(b.keys + ch.start + j);
         if (has_vals) sg.vals[j] = ld_stream(b.vals + ch.start + j);

@@ -9,7 +9,13 @@
 
 namespace cht {
 
-enum Mode : int { kFind = 0, kInsert = 1, kIouAdd = 2, kIouOverwrite = 3, kErase = 4 };
+enum Mode : int { kFind = 0, kInsert = 1, kIouAdd = 2, kIouOverwrite = 3, kErase = 4, kUpdAdd = 5, kUpdOverwrite = 6 };
+
+// Modes that read a value per operation / that may fill an empty cell.
+__host__ __device__ constexpr bool mode_has_vals(int m) {
+    return m == kInsert || m == kIouAdd || m == kIouOverwrite || m == kUpdAdd || m == kUpdOverwrite;
+}
+__host__ __device__ constexpr bool mode_fills(int m) { return m == kInsert || m == kIouAdd || m == kIouOverwrite; }
 
 // One batched operation over a table of 2^log2c cells.
 struct OpArgs {

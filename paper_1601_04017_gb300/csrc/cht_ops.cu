@@ -120,6 +120,8 @@ cudaError_t launch_op(Mode mode, const OpArgs& a, int group_width, int lane_cell
         case kIouAdd: return launch_mode<kIouAdd>(a, group_width, v, ctas_per_sm, s);
         case kIouOverwrite: return launch_mode<kIouOverwrite>(a, group_width, v, ctas_per_sm, s);
         case kErase: return launch_mode<kErase>(a, group_width, v, ctas_per_sm, s);
+        case kUpdAdd: return launch_mode<kUpdAdd>(a, group_width, v, ctas_per_sm, s);
+        case kUpdOverwrite: return launch_mode<kUpdOverwrite>(a, group_width, v, ctas_per_sm, s);
     }
     return cudaErrorInvalidValue;
 }

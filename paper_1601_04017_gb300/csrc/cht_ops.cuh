@@ -52,6 +52,12 @@ constexpr u64 kNoPos = ~0ull;
 
 template <int MODE>
 __device__ __forceinline__ int modify_at(Cell* cp, bool is_key, u64 key, u64 d) {
+    if (MODE == kUpdAdd || MODE == kUpdOverwrite) {  // update: present keys only
+        if (!is_key) return kStepDoneNo;
+        if (MODE == kUpdAdd) atomicAdd(&cp->val, d);
+        else atomicExch(&cp->val, d);
+        return kStepDoneYes;
+    }
     if (is_key) {
         if (MODE == kInsert) return kStepDoneNo;
         if (MODE == kIouAdd) { atomicAdd(&cp->val, d); return kStepDoneNo; }
@@ -153,8 +159,9 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
     constexpr u32 W = G * V;
     constexpr u32 FULL = 0xffffffffu;
     constexpr bool kModify = MODE != kFind;
-    constexpr bool kHasVals = MODE == kInsert || MODE == kIouAdd || MODE == kIouOverwrite;
-    constexpr bool kInsLike = kHasVals;  // modes that may fill a cell
+    constexpr bool kHasVals = mode_has_vals(MODE);
+    constexpr bool kInsLike = mode_fills(MODE);  // modes that may fill a cell
+    constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
 
     const u64 cap = 1ull << a.log2c;
     const u64 cmask = cap - 1;
@@ -238,8 +245,9 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
             }
         }
 
-        // ---- pre-reduce equal keys loaded in this step (modifying modes)
-        if (kModify) {
+        // ---- pre-reduce equal keys loaded in this step (modifying modes; an
+        // update reports presence per operation, so each one probes itself)
+        if (kModify && !kUpdate) {
             const u32 fm = __ballot_sync(FULL, fresh && gl == 0);
             if (fm & (fm - 1u)) {
                 bool dup = false;
@@ -368,7 +376,7 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                         op_code<kStaged>(a, sg, idx, outcome == kStepDoneReused ? kYes : (unsigned char)outcome);
                         if (outcome == kStepDoneYes) {
                             if (MODE == kErase) ++n_del;
-                            else ++n_ins;
+                            else if (kInsLike) ++n_ins;
                         }
                         if (kInsLike && outcome == kStepDoneReused) --n_del;  // one tombstone fewer (mod 2^64)
                     }
@@ -399,13 +407,13 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                     if (MODE == kFind) {
                         op_vout<kStaged>(a, sg, idx, 0);
                         op_code<kStaged>(a, sg, idx, kNo);
-                    } else if (MODE == kErase) {
+                    } else if (MODE == kErase || kUpdate) {
                         op_code<kStaged>(a, sg, idx, kNo);
                     } else {
                         op_code<kStaged>(a, sg, idx, kCodeFull);
                     }
                 }
-                if (MODE != kFind && MODE != kErase) sbits |= kFull;
+                if (kInsLike) sbits |= kFull;
                 active = false;
             }
         }

@@ -702,6 +702,28 @@ cht_status cht_insert_or_update(cht_handle h, const uint64_t* keys, const uint64
                        stream);
 }
 
+cht_status cht_update(cht_handle h, const uint64_t* keys, const uint64_t* vals, uint64_t n, cht_update_op op,
+                      uint8_t* updated, cht_stream_t stream) {
+    if (op != CHT_ADD && op != CHT_OVERWRITE) return CHT_ERR_INVALID_ARG;
+    if (!h || (n > 0 && (!keys || !vals))) return CHT_ERR_INVALID_ARG;
+    if (n == 0) return CHT_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last = s;
+    Staging stg(s);
+    const void *dk, *dv;
+    void* dc;
+    cht_status r = stg.in(keys, n * 8, &dk);
+    if (r == CHT_OK) r = stg.in(vals, n * 8, &dv);
+    if (r == CHT_OK) r = stg.out(updated, n, &dc);
+    if (r != CHT_OK) return r;
+    // no cell is filled: neither growth nor the bound on I is involved
+    r = launch(h, op == CHT_ADD ? cht::kUpdAdd : cht::kUpdOverwrite, static_cast<const u64*>(dk),
+               static_cast<const u64*>(dv), nullptr, static_cast<unsigned char*>(dc), n, s);
+    cht_status f = stg.finish();
+    return r != CHT_OK ? r : f;
+}
+
 cht_status cht_find(cht_handle h, const uint64_t* keys, uint64_t n, uint64_t* vals_out, uint8_t* found,
                     cht_stream_t stream) {
     if (!h || (n > 0 && (!keys || !vals_out))) return CHT_ERR_INVALID_ARG;
@@ -968,8 +990,8 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
     batches.reserve(n_ops);
     for (u64 i = 0; i < n_ops; ++i) {
         const cht_batch_op& o = ops[i];
-        const bool has_vals = o.op == CHT_OP_INSERT || o.op == CHT_OP_IOU_ADD || o.op == CHT_OP_IOU_OVERWRITE;
-        bool ok = o.table && o.op >= CHT_OP_FIND && o.op <= CHT_OP_ERASE;
+        const bool has_vals = cht::mode_has_vals(o.op);
+        bool ok = o.table && o.op >= CHT_OP_FIND && o.op <= CHT_OP_UPDATE_OVERWRITE;
         if (ok && o.n > 0) {
             ok = o.keys && !is_host_pointer(o.keys) && (!has_vals || (o.vals && !is_host_pointer(o.vals))) &&
                  (o.op != CHT_OP_FIND || (o.vals_out && !is_host_pointer(o.vals_out))) &&
@@ -1001,7 +1023,7 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
         b.table = t;
         b.mode = u32(o.op);
         batches.push_back(b);
-        if (has_vals) p->new_cells[t] += o.n;
+        if (cht::mode_fills(o.op)) p->new_cells[t] += o.n;
     }
     // The engine may read a work item's inputs before the items it depends
     // on have run, so no input array may overlap any output array.

@@ -101,7 +101,8 @@ struct Req {
     cht_status status = CHT_OK;
 };
 
-bool has_vals(int op) { return op == CHT_OP_INSERT || op == CHT_OP_IOU_ADD || op == CHT_OP_IOU_OVERWRITE; }
+bool has_vals(int op) { return cht::mode_has_vals(op); }
+bool fills(int op) { return cht::mode_fills(op); }
 
 u64 per_op_bytes(const cht_request& r) {
     return 8 + (has_vals(r.op) ? 8 : 0) + (r.op == CHT_OP_FIND ? 8 : 0) + (r.codes ? 1 : 0);
@@ -247,7 +248,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
         u64 m = rq.r.n - rq.admitted;
         if (m > s->cfg.max_step_ops - ops) m = s->cfg.max_step_ops - ops;
         const cht::TableInfo ti = cht::table_info(h);
-        if (has_vals(rq.r.op) && ti.growable) {
+        if (fills(rq.r.op) && ti.growable) {
             // Room check with an upper bound of the non-empty cells (every
             // admitted insert counted as new).  If the part does not fit, grow
             // now to the smallest capacity whose alpha-limit holds the bound
@@ -327,7 +328,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
         rq.admitted += m;
         ++rq.parts_inflight;
         ++s->parts_inflight[t];
-        if (has_vals(rq.r.op)) step_new[t] += m;
+        if (fills(rq.r.op)) step_new[t] += m;
         ops += m;
         if (rq.admitted == rq.r.n) {
             rq.state = 1;
@@ -557,7 +558,7 @@ cht_status cht_server_create(const cht_handle* tables, uint32_t n_tables, const 
 }
 
 cht_status cht_server_submit(cht_server_handle s, const cht_request* req, uint64_t* id) {
-    if (!s || !req || req->table >= s->tables.size() || req->op < CHT_OP_FIND || req->op > CHT_OP_ERASE ||
+    if (!s || !req || req->table >= s->tables.size() || req->op < CHT_OP_FIND || req->op > CHT_OP_UPDATE_OVERWRITE ||
         req->n == 0 || !req->keys || (has_vals(req->op) && !req->vals) || (req->op == CHT_OP_FIND && !req->vals_out))
         return CHT_ERR_INVALID_ARG;
     Req rq;

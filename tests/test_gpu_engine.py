@@ -175,7 +175,8 @@ def test_engine_chain_of_small_batches(cuda_lib, oracle_mod, chunk, reuse):
     for i in range(400):
         t = 0 if i % 5 else 1
         n = int(rng.integers(1, 200)) if t == 0 else int(rng.integers(100, 2000))
-        op = int(rng.choice([W.OP_FIND, W.OP_INSERT, W.OP_IOU_ADD, W.OP_ERASE], p=[0.4, 0.3, 0.2, 0.1]))
+        op = int(rng.choice([W.OP_FIND, W.OP_INSERT, W.OP_IOU_ADD, W.OP_ERASE, W.OP_UPDATE_ADD],
+                            p=[0.35, 0.3, 0.15, 0.1, 0.1]))
         k = universe[rng.integers(0, universe.size, n)]
         # an insert's value is a function of its key: whichever copy of a
         # repeated key wins, the stored value is the same
@@ -186,16 +187,19 @@ def test_engine_chain_of_small_batches(cuda_lib, oracle_mod, chunk, reuse):
     vals_d = torch.empty(total, dtype=torch.int64, device="cuda")
     vout = torch.full((total,), -1, dtype=torch.int64, device="cuda")
     codes = torch.full((total,), 255, dtype=torch.uint8, device="cuda")
-    tables = [cuda_lib.Table(1 << 12), cuda_lib.Table(1 << 13)]
+    # large enough never to fill (which operations fail on a full table depends
+    # on their order), small enough to keep long clusters and tombstone runs
+    tables = [cuda_lib.Table(1 << 14), cuda_lib.Table(1 << 14)]
     if reuse:
         tables[0].set_config(reuse_tombstones=1)  # one table with reuse, one without, in one launch
-    otabs = [oracle_mod.OracleTable(1 << 12, reuse_tombstones=bool(reuse)), oracle_mod.OracleTable(1 << 13)]
+    otabs = [oracle_mod.OracleTable(1 << 14, reuse_tombstones=bool(reuse)), oracle_mod.OracleTable(1 << 14)]
     ops, spans, o = [], [], 0
     for t, op, k, v in specs:
         n = k.size
         keys_d[o:o + n] = torch.from_numpy(k.view(np.int64))
         vals_d[o:o + n] = torch.from_numpy(v.view(np.int64))
-        ops.append((tables[t], op, keys_d[o:o + n], vals_d[o:o + n] if op in (W.OP_INSERT, W.OP_IOU_ADD) else None,
+        ops.append((tables[t], op, keys_d[o:o + n],
+                    vals_d[o:o + n] if op in (W.OP_INSERT, W.OP_IOU_ADD, W.OP_UPDATE_ADD) else None,
                     vout[o:o + n] if op == W.OP_FIND else None, codes[o:o + n]))
         spans.append((o, o + n))
         o += n
@@ -204,6 +208,7 @@ def test_engine_chain_of_small_batches(cuda_lib, oracle_mod, chunk, reuse):
     plan.launch()
     assert plan.status() == 0
     g_v, g_c = to_np_u64(vout), to_np_u8(codes)
+    assert (g_c != 2).all()  # no table filled up
     for (t, op, k, v), (lo, hi) in zip(specs, spans):
         ot = otabs[t]
         if op == W.OP_FIND:
@@ -214,6 +219,10 @@ def test_engine_chain_of_small_batches(cuda_lib, oracle_mod, chunk, reuse):
             oc = ot.insert(k, v)
         elif op == W.OP_IOU_ADD:
             oc = ot.insert_or_update(k, v, oracle_mod.ADD)
+        elif op == W.OP_UPDATE_ADD:
+            oc = ot.update(k, v, oracle_mod.ADD)
+            assert np.array_equal(g_c[lo:hi], oc)  # presence per operation is unique
+            continue
         else:
             oc = ot.erase(k)
         for kk in np.unique(k):  # equal keys in one batch: which one wins is free

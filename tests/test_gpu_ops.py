@@ -302,3 +302,40 @@ def test_reuse_tombstones_matches_oracle(cuda_lib, oracle_mod, g, agg, mode):
     # reuse keeps the table from filling with tombstones: never more non-empty
     # cells than the keys ever inserted
     assert t.size()[1] <= universe.size
+
+
+@pytest.mark.parametrize("g,v", [(0, 0), (1, 0), (4, 2), (8, 2), (2, 1), (32, 1)])
+@pytest.mark.parametrize("mode", ["add", "overwrite"])
+def test_update_matches_oracle(cuda_lib, oracle_mod, g, v, mode):
+    """update (Sec. 3): present keys change, absent and erased ones do not; the
+    presence code of every operation is exact, add sums are exact, overwrite
+    keeps one of the batch's values; nothing is inserted."""
+    c = 1 << 15
+    rng = np.random.default_rng(9)
+    keys = W.uniform_keys(12_000, seed=58)
+    t = _table(cuda_lib, c, g, v=v)
+    o = oracle_mod.OracleTable(c)
+    t.insert(to_dev(keys), to_dev(keys))
+    o.insert(keys, keys)
+    gone = keys[:2000]
+    t.erase(to_dev(gone))
+    o.erase(gone)
+    pool = np.concatenate([keys, W.uniform_keys(3000, start=10**7, seed=58)])
+    ks = pool[rng.integers(0, pool.size, 40_001)]
+    vs = rng.integers(1, 1 << 40, ks.size).astype(np.uint64)
+    op = cuda_lib.ADD if mode == "add" else cuda_lib.OVERWRITE
+    codes = codes_buf(ks.size)
+    t.update(to_dev(ks), to_dev(vs), op, codes)
+    oc = o.update(ks, vs, oracle_mod.ADD if mode == "add" else oracle_mod.OVERWRITE)
+    assert np.array_equal(to_np_u8(codes), oc)
+    live, ne, _ = t.size(check=True)
+    assert (live, ne) == (o.live, o.nonempty)
+    if mode == "add":
+        assert_same_live_set(t, o)
+    else:
+        uk = np.unique(ks[oc == 1])
+        vo = vals_buf(uk.size)
+        t.find(to_dev(uk), vo)
+        got = to_np_u64(vo)
+        for k, gv in zip(uk, got):
+            assert gv in set(vs[ks == k].tolist())

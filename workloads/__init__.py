@@ -463,6 +463,7 @@ def _batched_keys_t(wl, first, last, device):
 # serving: requests over resident growing tables
 # ----------------------------------------------------------------------------
 OP_ERASE = 4
+OP_UPDATE_ADD, OP_UPDATE_OVERWRITE = 5, 6  # update of present keys only (no insertion)
 STREAM_UNIVERSE = 3
 SEED_SERVING = 5
 
