@@ -141,3 +141,26 @@ def test_full_table_migration_starts_at_zero(oracle_mod):
     t.migrate(2 * c)
     assert np.array_equal(t.cells(), want)
     t.assert_invariants()
+
+
+@pytest.mark.parametrize("shrink_log2", [1, 2, 5])
+def test_shrinking_migration_matches_bruteforce(oracle_mod, shrink_log2):
+    """Shrinking (Sec. 4.3.1): the sequential migration into c / 2^k cells equals
+    brute-force re-insertion of the live elements in cluster order, keeps the
+    live set and the invariants, and its occupancy equals any insertion order's."""
+    log2c = 12
+    # leave about 0.45 c' live elements: load 0.45 in the smaller table
+    t, _ = _filled(oracle_mod, log2c, 0.5, 6 + shrink_log2, erase_frac=1.0 - 0.9 / (1 << shrink_log2))
+    live_k, live_v = t.export()
+    assert live_k.size < (1 << (log2c - shrink_log2))
+    expect = _bruteforce_migrate(oracle_mod, t.cells(), log2c - shrink_log2)
+    t.migrate(t.capacity >> shrink_log2)
+    assert t.capacity == 1 << (log2c - shrink_log2)
+    assert np.array_equal(t.cells(), expect)
+    k1, v1 = t.export()
+    assert sorted(zip(live_k.tolist(), live_v.tolist())) == sorted(zip(k1.tolist(), v1.tolist()))
+    order = np.random.default_rng(7).permutation(live_k.size)
+    ref = oracle_mod.OracleTable(t.capacity)
+    ref.insert(live_k[order], live_v[order])
+    assert np.array_equal(t.cells()[:, 0] != 0, ref.cells()[:, 0] != 0)
+    t.assert_invariants()
