@@ -168,14 +168,19 @@ cht_status cht_erase(cht_handle h, const uint64_t *keys, uint64_t n, uint8_t *er
                      cht_stream_t stream);
 
 /* Migrate into a new table of new_capacity cells (rounded up to a power of
- * two; must be a power-of-two multiple gamma >= 1 of the current capacity and
- * hold every live element), dropping tombstones (Sec. 4.3.1, Sec. 4.4).
+ * two, minimum 64), dropping tombstones (Sec. 4.3.1, Sec. 4.4).
  * new_capacity = 0 applies the growth policy: double if more than alpha*c/2
- * elements are live, else keep the size.  The resulting cell layout equals the
- * sequential migration that visits the old cells in index order from a
- * cluster start (Lemma 1).  The new table is allocated before the old one is
+ * elements are live, else keep the size.  Growing or keeping the size
+ * (gamma >= 1): the cell layout equals the sequential migration that visits
+ * the old cells in index order from a cluster start (Lemma 1).  Shrinking
+ * (Sec. 4.3.1 "Shrinking"; the live elements must be fewer than the new
+ * capacity, else CHT_ERR_INVALID_ARG and no change): each block of the target
+ * takes the elements that land in it, the rest are inserted concurrently;
+ * the occupied cells equal those of the sequential migration, which key sits
+ * where may differ.  The new table is allocated before the old one is
  * released: on CHT_ERR_OOM the table is unchanged.  Reads the live count
- * back from the device (synchronizes `stream`). */
+ * back from the device when the policy or a shrink needs it (synchronizes
+ * `stream`). */
 cht_status cht_migrate(cht_handle h, uint64_t new_capacity, cht_stream_t stream);
 
 /* Synchronize `stream` and report: live elements (I - D), non-empty cells

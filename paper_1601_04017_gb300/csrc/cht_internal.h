@@ -50,6 +50,13 @@ u64 migrate_border_count(u32 src_log2, int tile);
 cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log2, DevState* st,
                            int tile, u64* border, cudaStream_t s);
 
+// Shrinking migration (Sec. 4.3.1 "Shrinking") of `src` into `dst` (2^dst_log2
+// cells, dst_log2 < src_log2, more cells than live elements; no
+// initialisation needed).  `st` receives the new I (zero on entry).  spill:
+// scratch of 2^dst_log2 cells; nspill: one counter, zero on entry.
+cudaError_t launch_shrink(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log2, DevState* st, Cell* spill,
+                          unsigned long long* nspill, cudaStream_t s);
+
 // Compact the live cells into keys_out / vals_out (max_n entries); the count
 // lands in st->export_pos, which must be zero on entry.
 cudaError_t launch_export(const Cell* cells, u32 log2c, u64* keys_out, u64* vals_out, u64 max_n,

@@ -290,7 +290,163 @@ __global__ void __launch_bounds__(256) export_kernel(const Cell* __restrict__ ce
     }
 }
 
+// ---------------------------------------------------------------------------
+// Shrinking (Sec. 4.3.1 "Shrinking"): Lemma 1 does not hold for gamma < 1, so
+// the paper cuts the source into blocks, maps each block a..b to a disjoint
+// target block a'..b' with the scaling function, and migrates in two phases:
+// first every element whose new home lies in its block's target block and
+// whose probe stays inside it is placed there (no other thread touches that
+// target block), then, after a barrier (here: the kernel boundary), the
+// elements that did not fit are inserted concurrently with atomic operations.
+//
+// Here a warp owns one target block of kShrinkBlock cells, staged in shared
+// memory, and the 2^k * kShrinkBlock source cells that map onto it (the new
+// home is the top bits of the hash, so it is the old home >> k).  Lanes read
+// the source coalesced and place their elements into the shared block by
+// linear probing with shared-memory CAS; an element whose new home lies in
+// another block (a cluster that began in the previous source block, or
+// wrapped around), or whose probe would run past the block's end, goes to a
+// spill list.  The block is then written whole, empties included.  Every
+// placement is one a sequential insertion could make (it only looked at cells
+// of its own block), so the occupied cells equal those of the sequential
+// migration of the same elements (linear probing's occupancy does not depend
+// on the insertion order); which key sits where may differ.
+constexpr u32 kShrinkBlock = 256;
+
+struct ShrinkArgs {
+    const Cell* src;
+    u32 slog2;
+    Cell* dst;
+    u32 dlog2;
+    DevState* st;
+    Cell* spill;                // capacity: 2^dlog2 cells (more than the live count)
+    unsigned long long* nspill; // zero before the launch
+    u32 block;                  // target cells per warp (kShrinkBlock, or c' if smaller)
+};
+
+__global__ void __launch_bounds__(kMigBlock) shrink_kernel(ShrinkArgs a) {
+    extern __shared__ __align__(16) unsigned char shrink_smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned long long* skey = reinterpret_cast<unsigned long long*>(shrink_smem) + size_t(wib) * 2 * a.block;
+    u64* sval = reinterpret_cast<u64*>(skey + a.block);
+    const u32 k = a.slog2 - a.dlog2;
+    const u64 nblocks = (1ull << a.dlog2) / a.block;
+    const u64 span = u64(a.block) << k;  // source cells per block
+    const u32 dshift = 64u - a.dlog2;
+    u64 moved = 0;
+    for (u64 blk = (u64(blockIdx.x) * kMigWarps + wib); blk < nblocks; blk += u64(gridDim.x) * kMigWarps) {
+        const u64 t0 = blk * a.block;  // first target cell of the block
+        for (u32 j = lane; j < a.block; j += 32) {
+            skey[j] = kEmpty;
+            sval[j] = 0;
+        }
+        __syncwarp();
+        const u64 s0 = blk * span;
+        for (u64 i = lane; i < span; i += 32) {
+            u64 key, val;
+            ld_cell_nc(a.src + s0 + i, key, val);
+            const bool live = key != kEmpty && key != kTomb;
+            bool spill = false;
+            if (live) {
+                const u64 h = home_of(key, dshift);
+                spill = true;
+                if (h >= t0 && h < t0 + a.block) {
+                    for (u32 q = u32(h - t0); q < a.block; ++q) {
+                        if (atomicCAS(&skey[q], kEmpty, key) == kEmpty) {
+                            sval[q] = val;
+                            spill = false;
+                            ++moved;
+                            break;
+                        }
+                    }
+                }
+            }
+            // warp-aggregated append to the spill list
+            const u32 m = __ballot_sync(0xffffffffu, spill);
+            if (m) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.nspill, u64(__popc(m)));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (spill) {
+                    Cell c;
+                    c.key = key;
+                    c.val = val;
+                    a.spill[base + __popc(m & ((1u << lane) - 1u))] = c;
+                }
+            }
+        }
+        __syncwarp();
+        for (u32 j = lane; j < a.block; j += 32) {
+            Cell c;
+            c.key = skey[j];
+            c.val = sval[j];
+            a.dst[t0 + j] = c;
+        }
+        __syncwarp();  // the next block reuses the shared area
+    }
+    for (int o = 16; o > 0; o >>= 1) moved += __shfl_xor_sync(0xffffffffu, moved, o);
+    if (lane == 0 && moved) atomicAdd(&a.st->I, moved);
+}
+
+// Second phase: insert the spilled elements concurrently (16-byte CAS into
+// an empty cell, linear probing from the new home).  Keys are distinct, so a
+// failed CAS only means another element took the cell.  The target holds
+// fewer elements than cells, so every probe ends; it is still bounded by c'.
+__global__ void __launch_bounds__(256) shrink_spill_kernel(ShrinkArgs a) {
+    const u64 n = *a.nspill;
+    const u64 cap = 1ull << a.dlog2, mask = cap - 1;
+    const u32 dshift = 64u - a.dlog2;
+    u64 moved = 0;
+    for (u64 i = u64(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += u64(gridDim.x) * blockDim.x) {
+        const Cell e = a.spill[i];
+        u64 pos = home_of(e.key, dshift);
+        for (u64 probed = 0; probed < cap; ++probed, pos = (pos + 1) & mask) {
+            u64 ck, cv;
+            ld_cell_cg(a.dst + pos, ck, cv);
+            if (ck != kEmpty) continue;
+            Cell expect;
+            expect.key = kEmpty;
+            expect.val = 0;
+            const Cell old = cas_cell(a.dst + pos, expect, e);
+            if (old.key == kEmpty && old.val == 0) {
+                ++moved;
+                break;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) moved += __shfl_xor_sync(0xffffffffu, moved, o);
+    if ((threadIdx.x & 31) == 0 && moved) atomicAdd(&a.st->I, moved);
+}
+
 }  // namespace
+
+cudaError_t launch_shrink(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log2, DevState* st, Cell* spill,
+                          unsigned long long* nspill, cudaStream_t s) {
+    if (dst_log2 >= src_log2) return cudaErrorInvalidValue;
+    ShrinkArgs a;
+    a.src = src;
+    a.slog2 = src_log2;
+    a.dst = dst;
+    a.dlog2 = dst_log2;
+    a.st = st;
+    a.spill = spill;
+    a.nspill = nspill;
+    const u64 cnew = 1ull << dst_log2;
+    a.block = cnew < kShrinkBlock ? u32(cnew) : kShrinkBlock;
+    const size_t smem = size_t(kMigWarps) * 2 * a.block * sizeof(u64);
+    const u64 nblocks = cnew / a.block;
+    u64 grid = (nblocks + kMigWarps - 1) / kMigWarps;
+    const u64 gcap = u64(sm_count()) * 8;
+    if (grid > gcap) grid = gcap;
+    shrink_kernel<<<unsigned(grid), kMigBlock, smem, s>>>(a);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    shrink_spill_kernel<<<unsigned(sm_count() * 4), 256, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
 
 u64 migrate_border_count(u32 src_log2, int tile) {
     const u64 c = 1ull << src_log2;

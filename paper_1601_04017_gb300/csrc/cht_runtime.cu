@@ -237,30 +237,40 @@ cht_status read_state(cht_table* h, DevState* out, cudaStream_t s) {
 // Migrate h into 2^new_log2 cells (new_log2 >= log2c).  `live` is the exact
 // live count if known (else ~0).  Allocates first: on failure h is unchanged.
 cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
+    // everything is allocated before the table's counters are touched: on
+    // CHT_ERR_OOM the table is unchanged
+    const bool shrink = new_log2 < h->log2c;
+    if (shrink && live == ~0ull) return CHT_ERR_INVALID_ARG;  // shrinking needs the exact live count
     Cell* dst = nullptr;
     const u64 bytes = (1ull << new_log2) * sizeof(Cell);
     cht_status r = lib_alloc(reinterpret_cast<void**>(&dst), bytes, s);
     if (r != CHT_OK) return r;
-    // I and D restart (the kernel accumulates the moved count into I)
-    if (cudaMemsetAsync(&h->st->I, 0, 2 * sizeof(u64), s) != cudaSuccess ||
-        cudaMemsetAsync(&h->st->mig_fail, 0, sizeof(u32), s) != cudaSuccess) {
-        lib_free(dst, bytes, s);
-        return CHT_ERR_CUDA;
-    }
     // tile: short clusters (load below 0.6) want small tiles for parallelism,
     // long ones want large tiles so few clusters straddle tile borders
     int tile = h->cfg.migrate_tile;
     if (tile == 0) tile = double(h->i_bound) < 0.6 * double(h->cap()) ? 256 : 1024;
-    // scratch: the moved border of every migration tile
-    const u64 nb = cht::migrate_border_count(h->log2c, tile);
-    u64* border = nullptr;
-    r = lib_alloc(reinterpret_cast<void**>(&border), nb * sizeof(u64), s);
+    // scratch: the moved border of every migration tile (growing), or the
+    // spill list of c' cells plus its counter (shrinking)
+    const u64 sbytes = shrink ? bytes + 256 : cht::migrate_border_count(h->log2c, tile) * sizeof(u64);
+    unsigned char* scratch = nullptr;
+    r = lib_alloc(reinterpret_cast<void**>(&scratch), sbytes, s);
     if (r != CHT_OK) {
         lib_free(dst, bytes, s);
         return r;
     }
-    cudaError_t e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, tile, border, s);
-    lib_free(border, nb * sizeof(u64), s);
+    // I and D restart (the kernels accumulate the moved count into I)
+    cudaError_t e = cudaMemsetAsync(&h->st->I, 0, 2 * sizeof(u64), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&h->st->mig_fail, 0, sizeof(u32), s);
+    if (shrink) {
+        unsigned long long* nspill = reinterpret_cast<unsigned long long*>(scratch + bytes);
+        if (e == cudaSuccess) e = cudaMemsetAsync(nspill, 0, sizeof(unsigned long long), s);
+        if (e == cudaSuccess)
+            e = cht::launch_shrink(h->cells, h->log2c, dst, new_log2, h->st, reinterpret_cast<Cell*>(scratch),
+                                   nspill, s);
+    } else if (e == cudaSuccess) {
+        e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, tile, reinterpret_cast<u64*>(scratch), s);
+    }
+    lib_free(scratch, sbytes, s);
     if (e != cudaSuccess) {
         lib_free(dst, bytes, s);
         return cuda_status(e);
@@ -780,7 +790,16 @@ cht_status cht_migrate(cht_handle h, uint64_t new_capacity, cht_stream_t stream)
         if (new_capacity > (1ull << kMaxLog2)) return CHT_ERR_INVALID_ARG;
         nl = log2_ceil_cap(new_capacity);
     }
-    if (nl < h->log2c || nl > kMaxLog2) return CHT_ERR_INVALID_ARG;
+    if (nl > kMaxLog2) return CHT_ERR_INVALID_ARG;
+    if (nl < h->log2c) {  // shrinking: the live elements must leave an empty cell
+        if (live == ~0ull) {
+            DevState ds;
+            cht_status r = read_state(h, &ds, s);
+            if (r != CHT_OK) return r;
+            live = ds.I - ds.D;
+        }
+        if (live >= (1ull << nl)) return CHT_ERR_INVALID_ARG;
+    }
     return do_migrate(h, nl, live, s);
 }
 

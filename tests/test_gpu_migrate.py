@@ -106,7 +106,46 @@ def test_migrate_policy_and_bad_capacity(cuda_lib):
     t.migrate(0)  # 100 live: same size, tombstones purged
     assert t.size() == (100, 100, 2048)
     with pytest.raises(cuda_lib.ChtError):
-        t.migrate(512)  # shrinking is not supported
+        t.migrate(64)  # shrinking below the live count: no empty cell would remain
+    assert t.size() == (100, 100, 2048)
+    t.migrate(512)  # shrinking (Sec. 4.3.1 "Shrinking")
+    assert t.size() == (100, 100, 512)
+
+
+@pytest.mark.parametrize("log2c,load,erase,shrink_log2", [
+    (16, 0.5, 0.6, 1),    # load 0.4 after shrinking by 2
+    (16, 0.5, 0.8, 2),
+    (18, 0.6, 0.975, 5),  # by 32: most elements spill from short blocks
+    (14, 0.9, 0.5, 1),    # long clusters: many spills
+    (12, 0.5, 0.97, 5),   # the target (128 cells) is smaller than one block
+    (20, 0.3, 0.99, 8),   # by 256
+])
+def test_shrinking_migration(cuda_lib, oracle_mod, log2c, load, erase, shrink_log2):
+    """Shrinking (Sec. 4.3.1): the live set is kept, every key stays reachable
+    from its home (the layout's invariants, checked by the oracle on the GPU's
+    cells), and the occupied cells equal those of the sequential migration of
+    the same snapshot (linear probing's occupancy does not depend on order)."""
+    t, _ = _fill(cuda_lib, oracle_mod, log2c, load, erase, seed=log2c + shrink_log2 + 100, wrap=5)
+    snap = to_np_u64(t.cells())
+    live = t.size()[0]
+    o = oracle_mod.OracleTable(64)
+    o.load_cells(snap)
+    new_c = (1 << log2c) >> shrink_log2
+    assert live < new_c
+    o.migrate(new_c)
+    t.migrate(new_c)
+    assert t.size(check=True) == (live, live, new_c)
+    got = to_np_u64(t.cells()).reshape(-1, 2)
+    assert np.array_equal(got[:, 0] != 0, o.cells()[:, 0] != 0)
+    g = oracle_mod.OracleTable(64)
+    g.load_cells(got)
+    g.assert_invariants()
+    assert_same_live_set(t, o)
+    # the shrunk table works: finds hit every live key
+    gk, gv = t.export()
+    vo, fo = vals_buf(live), codes_buf(live)
+    t.find(gk, vo, fo)
+    assert (to_np_u8(fo) == 1).all() and np.array_equal(to_np_u64(vo), to_np_u64(gv))
 
 
 def test_migration_oom_leaves_table_unchanged(cuda_lib):
