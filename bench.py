@@ -570,7 +570,18 @@ def run_case(args):
         return round(a.elapsed_time(b), 4)
 
     out = {"case": args.case, "log2c": log2c, "load": load}
-    if args.case in ("find", "insert", "migrate"):
+    if args.case == "shrink":
+        # the same shrink once untimed, so the timed one does not include the
+        # memory pool's first growth to these sizes
+        wl = W.bounded_workload(log2c, loads=(load,), n_find=c // 2, backend="cuda")
+        n = wl["counts"][load]
+        t = cht.Table(c)
+        t.insert(wl["keys"][:n], wl["vals"][:n])
+        t.erase(wl["keys"][: n - n // 8])
+        t.migrate(c // 4)
+        t.destroy()
+        torch.cuda.synchronize()
+    if args.case in ("find", "insert", "migrate", "shrink"):
         wl = W.bounded_workload(log2c, loads=(load,), n_find=c // 2, backend="cuda")
         n = wl["counts"][load]
         t = cht.Table(c)
@@ -582,6 +593,33 @@ def run_case(args):
             out["find_miss_ms"] = tm(lambda: t.find(wl["misses"], vout, codes[: c // 2]))
         if args.case == "migrate":
             out["migrate_x2_ms"] = tm(lambda: t.migrate(2 * c))
+        if args.case == "shrink":
+            # erase all but 1/8 of the keys, then shrink by 4 (load 0.5 x 1/8 x 4)
+            t.erase(wl["keys"][: n - n // 8])
+            live = t.size()[0]
+            out["live"] = live
+            out["shrink_x4_ms"] = tm(lambda: t.migrate(c // 4))
+            out["shrink_src_cells_per_s"] = round(c / (out["shrink_x4_ms"] * 1e-3), 1)
+        t.destroy()
+    elif args.case == "contention":
+        # Contended operations on a filled table (the paper's E4 overwrite and
+        # E5 find under skew): N = c/4 rank keys are present (load 0.25);
+        # c/2 operations per run draw keys Zipf(s) over those N ranks.
+        nr = c // 4
+        present = W.rank_to_key(torch.arange(1, nr + 1, dtype=torch.int64, device="cuda"), backend="cuda")
+        t = cht.Table(c)
+        t.insert(present, present)
+        vout = torch.empty(c // 2, dtype=torch.int64, device="cuda")
+        codes = torch.empty(c // 2, dtype=torch.uint8, device="cuda")
+        vals = torch.ones(c // 2, dtype=torch.int64, device="cuda")
+        for s_ in ZIPF_S:
+            z = W.zipf_keys(c // 2, s_, nr, W.SEED_ZIPF, backend="cuda")
+            out[f"find_s{s_}_ms"] = tm(lambda: t.find(z, vout, codes))
+            out[f"update_add_s{s_}_ms"] = tm(lambda: t.update(z, vals, cht.ADD, codes))
+            out[f"update_overwrite_s{s_}_ms"] = tm(lambda: t.update(z, vals, cht.OVERWRITE, codes))
+            out[f"iou_overwrite_s{s_}_ms"] = tm(lambda: t.insert_or_update(z, vals, cht.OVERWRITE, codes))
+            out[f"iou_add_s{s_}_ms"] = tm(lambda: t.insert_or_update(z, vals, cht.ADD, codes))
+        out["ops_per_run"] = c // 2
         t.destroy()
     elif args.case == "iou":
         z = W.zipf_keys(c, args.case_s, min(ZIPF_RANKS, c // 4), W.SEED_ZIPF, backend="cuda")
@@ -933,7 +971,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-reps", type=int, default=100)
-    ap.add_argument("--case", choices=["find", "insert", "migrate", "iou", "grow"],
+    ap.add_argument("--case", choices=["find", "insert", "migrate", "shrink", "iou", "grow", "contention"],
                     help="run one small single-operation case (for profiling) instead of the benchmark")
     ap.add_argument("--case-log2c", type=int, default=26)
     ap.add_argument("--case-load", type=float, default=0.9)

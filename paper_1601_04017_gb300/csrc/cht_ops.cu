@@ -66,7 +66,7 @@ cudaError_t launch_mode(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStre
 
 template <int MODE, bool WD, bool RE>
 cudaError_t launch_agg(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
-    constexpr size_t smem = size_t(kAggSlots) * (8 + 8 + 4);
+    constexpr size_t smem = agg_smem_bytes<MODE>();
     static std::atomic<int> occ{0};
     int per_sm = occ.load(std::memory_order_relaxed);
     if (per_sm == 0) {
@@ -107,6 +107,10 @@ cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, bool warp_dedup, i
         return warp_dedup ? launch_agg<kIouOverwrite, true, false>(a, ctas_per_sm, s)
                           : launch_agg<kIouOverwrite, false, false>(a, ctas_per_sm, s);
     }
+    // update: equal keys fold the same way; no cell is filled, so neither the
+    // warp pre-reduction nor tombstone reuse applies
+    if (mode == kUpdAdd) return launch_agg<kUpdAdd, false, false>(a, ctas_per_sm, s);
+    if (mode == kUpdOverwrite) return launch_agg<kUpdOverwrite, false, false>(a, ctas_per_sm, s);
     return cudaErrorInvalidValue;
 }
 

@@ -523,7 +523,7 @@ __device__ __forceinline__ unsigned char global_modify(const OpArgs& a, u64 key,
                 tpos = kNoPos;
                 continue;
             }
-            if (out == kStepDoneYes) ++n_ins;
+            if (out == kStepDoneYes && mode_fills(MODE)) ++n_ins;
             if (out == kStepDoneReused) {
                 ++n_reused;
                 return kYes;
@@ -531,7 +531,8 @@ __device__ __forceinline__ unsigned char global_modify(const OpArgs& a, u64 key,
             return (unsigned char)out;
         }
         if (tpos == kNoPos) break;
-        // every cell seen, no empty one and no key: take the tombstone
+        // every cell seen, no empty one and no key: take the tombstone (only
+        // insert modes record one)
         const int out = claim_tomb<MODE>(a.cells + tpos, key, d);
         if (out == kStepRestart) {
             pos = (tpos + 1) & cmask;
@@ -545,16 +546,30 @@ __device__ __forceinline__ unsigned char global_modify(const OpArgs& a, u64 key,
         }
         return (unsigned char)out;
     }
+    if (!mode_fills(MODE)) return kNo;  // update: every cell seen, the key is absent
     sbits |= kFull;
     return kCodeFull;
 }
 
+// Shared memory of the aggregation kernel: slot keys, values and first ops;
+// for update modes also each operation's slot and each slot's result (every
+// operation on a key reports whether the key was present).
+template <int MODE>
+constexpr size_t agg_smem_bytes() {
+    return size_t(kAggSlots) * (8 + 8 + 4) +
+           ((MODE == kUpdAdd || MODE == kUpdOverwrite) ? size_t(kAggWindow) * 2 + kAggSlots : 0);
+}
+
 template <int MODE, bool WARP_DEDUP, bool kReuse>
 __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
+    constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
+    constexpr bool kAdd = MODE == kIouAdd || MODE == kUpdAdd;
     extern __shared__ __align__(16) unsigned char agg_smem[];
     u64* const skey = reinterpret_cast<u64*>(agg_smem);
     u64* const sval = skey + kAggSlots;
     u32* const slead = reinterpret_cast<u32*>(sval + kAggSlots);  // window offset of the slot's first op
+    unsigned short* const sslot = reinterpret_cast<unsigned short*>(slead + kAggSlots);  // update: op -> slot
+    unsigned char* const sres = reinterpret_cast<unsigned char*>(sslot + kAggWindow);    // update: slot result
     const u64 cap = 1ull << a.log2c;
     const u32 shift = 64u - a.log2c;
     const int tid = threadIdx.x;
@@ -575,6 +590,7 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
             const u64 idx = w0 + off;
             bool valid = idx < a.n;
             u64 key = 0, d = 0;
+            if (kUpdate) sslot[off] = 0xffffu;
             if (valid) {
                 key = ld_stream(a.keys + idx);
                 d = ld_stream(a.vals + idx);
@@ -589,7 +605,7 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
             if (WARP_DEDUP && valid) {
                 const u32 same = __match_any_sync(vm, key);
                 const int lane = tid & 31;
-                if (MODE == kIouAdd) {
+                if (kAdd) {
                     u32 rem = same;
                     u64 total = 0;
                     while (__any_sync(vm, rem != 0)) {
@@ -618,14 +634,16 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
                     same = old == key;
                 }
                 if (mine) {
-                    if (MODE == kIouAdd) atomicAdd(reinterpret_cast<unsigned long long*>(sval + s), d);
+                    if (kAdd) atomicAdd(reinterpret_cast<unsigned long long*>(sval + s), d);
                     else sval[s] = d;
                     slead[s] = off;
+                    if (kUpdate) sslot[off] = (unsigned short)s;
                     break;
                 }
                 if (same) {
-                    if (MODE == kIouAdd) atomicAdd(reinterpret_cast<unsigned long long*>(sval + s), d);
-                    if (a.codes) a.codes[idx] = kNo;
+                    if (kAdd) atomicAdd(reinterpret_cast<unsigned long long*>(sval + s), d);
+                    if (kUpdate) sslot[off] = (unsigned short)s;
+                    else if (a.codes) a.codes[idx] = kNo;
                     break;
                 }
                 s = (s + 1) & (kAggSlots - 1);
@@ -637,11 +655,19 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
             const u64 k = skey[s];
             if (k == kEmpty) continue;
             const unsigned char r = global_modify<MODE, kReuse>(a, k, sval[s], cap, shift, n_ins, n_reused, sbits);
-            if (a.codes) a.codes[w0 + slead[s]] = r;
+            if (kUpdate) sres[s] = r;
+            else if (a.codes) a.codes[w0 + slead[s]] = r;
             skey[s] = kEmpty;
             sval[s] = 0;
         }
         __syncthreads();
+        if (kUpdate && a.codes) {  // every operation takes its key's result
+            for (int off = tid; off < kAggWindow; off += kAggBlock) {
+                const unsigned short sl = sslot[off];
+                if (sl != 0xffffu) a.codes[w0 + off] = sres[sl];
+            }
+            __syncthreads();
+        }
     }
     constexpr u32 FULL = 0xffffffffu;
     for (int o = 16; o > 0; o >>= 1) {

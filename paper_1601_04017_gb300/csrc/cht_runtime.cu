@@ -330,7 +330,8 @@ cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals
     a.codes = codes;
     a.n = n;
     a.st = h->st;
-    if ((mode == cht::kIouAdd || mode == cht::kIouOverwrite) && h->cfg.iou_aggregate)
+    if ((mode == cht::kIouAdd || mode == cht::kIouOverwrite || mode == cht::kUpdAdd || mode == cht::kUpdOverwrite) &&
+        h->cfg.iou_aggregate)
         return cuda_status(cht::launch_iou_aggregated(mode, a, h->cfg.iou_aggregate == 2, h->cfg.ctas_per_sm, s));
     const Width w = pick_width(h, mode, n);
     return cuda_status(cht::launch_op(mode, a, w.g, w.v, h->cfg.ctas_per_sm, s));

@@ -304,16 +304,16 @@ def test_reuse_tombstones_matches_oracle(cuda_lib, oracle_mod, g, agg, mode):
     assert t.size()[1] <= universe.size
 
 
-@pytest.mark.parametrize("g,v", [(0, 0), (1, 0), (4, 2), (8, 2), (2, 1), (32, 1)])
+@pytest.mark.parametrize("g,v,agg", [(0, 0, 1), (0, 0, 0), (1, 0, 0), (4, 2, 0), (8, 2, 0), (2, 1, 0), (32, 1, 0)])
 @pytest.mark.parametrize("mode", ["add", "overwrite"])
-def test_update_matches_oracle(cuda_lib, oracle_mod, g, v, mode):
+def test_update_matches_oracle(cuda_lib, oracle_mod, g, v, agg, mode):
     """update (Sec. 3): present keys change, absent and erased ones do not; the
     presence code of every operation is exact, add sums are exact, overwrite
     keeps one of the batch's values; nothing is inserted."""
     c = 1 << 15
     rng = np.random.default_rng(9)
     keys = W.uniform_keys(12_000, seed=58)
-    t = _table(cuda_lib, c, g, v=v)
+    t = _table(cuda_lib, c, g, v=v, iou_aggregate=agg)
     o = oracle_mod.OracleTable(c)
     t.insert(to_dev(keys), to_dev(keys))
     o.insert(keys, keys)
