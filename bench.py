@@ -448,7 +448,8 @@ def run_gpu(args):
                        "capacity_cells": 1 << LOG2C, "ops_per_step": runner.ops_per_step,
                        "l2": "inputs and table far larger than L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "probe_window": "auto by load (G=1 below 0.6; 4x32B or 8x32B above)"},
+                       "probe_window": "auto by load: finds 2 lanes x 64 B below 0.6, 4 x 64 B above; "
+                                       "inserts 1 x 32 B below 0.6, 4 x 64 B above"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "breakdown": breakdown, "latency_config1": lat,
         }

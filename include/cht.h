@@ -79,13 +79,13 @@ typedef enum {
 #define CHT_STATUS_RESERVED 0x2u
 
 /* Tunables.  group_width G: lanes that probe one key together, each loading
- * 16 bytes (G in {1,2,4,8,16,32}); G = 1 uses one 32-byte load (two cells,
- * one DRAM sector) per lane and probe step; 0 (default) picks the window
- * per batch from the table's load (for insert: the load after the batch):
- * G = 1 below 0.6, else G = 4 with one sector per lane (G = 8 for finds at
- * load 0.8 and above).  lane_cells V: cells each lane of a group loads per
- * probe step, 1 (16 bytes) or 2 (one 32-byte sector); 0 = default (2 for
- * G = 1 and for the automatic wide windows, else 1); G = 32 allows only 1.  ctas_per_sm: resident CTAs per
+ * lane_cells cells per probe step (G in {1,2,4,8,16,32}); 0 (default) picks
+ * the window per batch from the table's load (for insert: the load after the
+ * batch): below 0.6, finds 2 lanes x 4 cells (one 128-byte line) and the
+ * other operations 1 lane x 2 cells; above it, finds and inserts 4 lanes x 4
+ * cells and the others 4 lanes x 2 cells.  lane_cells V: 1 (16 bytes), 2 (one
+ * 32-byte sector) or 4 (two sectors, loaded together); 0 = default (2 for
+ * G = 1, else 1); G = 32 allows only 1, G = 16 at most 2.  ctas_per_sm: resident CTAs per
  * SM for the operation kernels (0 = occupancy maximum).  migrate_tile:
  * source cells per migration warp task (power of two, 64..8192; 0 = by load:
  * 256 below load 0.6, else 1024).  alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).

@@ -43,6 +43,15 @@ cudaError_t launch_mode(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStre
     if constexpr (MODE == kInsert || MODE == kIouAdd || MODE == kIouOverwrite) {
         if (a.reuse) return launch_reuse<MODE>(a, g, ctas_per_sm, s);
     }
+    if (v == 4) {
+        switch (g) {
+            case 1: return launch_one<1, 4, MODE>(a, ctas_per_sm, s);
+            case 2: return launch_one<2, 4, MODE>(a, ctas_per_sm, s);
+            case 4: return launch_one<4, 4, MODE>(a, ctas_per_sm, s);
+            case 8: return launch_one<8, 4, MODE>(a, ctas_per_sm, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (v == 2) {
         switch (g) {
             case 1: return launch_one<1, 2, MODE>(a, ctas_per_sm, s);

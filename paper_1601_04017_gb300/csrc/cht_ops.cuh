@@ -288,28 +288,34 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
         // ---- one probe step: load the window holding `pos`
         const u64 base = pos & ~u64(W - 1);
         const u32 first = u32(pos - base);
-        u64 k0 = 0, v0 = 0, k1 = 0, v1 = 0;
+        // each lane holds V consecutive cells of the window (V = 2: one
+        // 32-byte sector; V = 4: two sectors, issued back to back)
+        u64 kk[V], vv[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) kk[j] = vv[j] = 0;
         int hit = -1;
         bool match = false;
         u64 hv = 0;
         if (active) {
             const Cell* p = a.cells + base + u32(gl) * V;
-            if (V == 2) {
-                if (kModify || kCoherent) ld_pair_cg(p, k0, v0, k1, v1);
-                else ld_pair_nc(p, k0, v0, k1, v1);
+            if (V == 1) {
+                if (kModify || kCoherent) ld_cell_cg(p, kk[0], vv[0]);
+                else ld_cell_nc(p, kk[0], vv[0]);
             } else {
-                if (kModify || kCoherent) ld_cell_cg(p, k0, v0);
-                else ld_cell_nc(p, k0, v0);
+#pragma unroll
+                for (int j = 0; j < V; j += 2) {
+                    if (kModify || kCoherent) ld_pair_cg(p + j, kk[j], vv[j], kk[j + 1], vv[j + 1]);
+                    else ld_pair_nc(p + j, kk[j], vv[j], kk[j + 1], vv[j + 1]);
+                }
             }
             const u32 o0 = u32(gl) * V;
-            if (o0 >= first && (k0 == key || k0 == kEmpty)) {
-                hit = int(o0);
-                match = k0 == key;
-                hv = v0;
-            } else if (V == 2 && o0 + 1 >= first && (k1 == key || k1 == kEmpty)) {
-                hit = int(o0 + 1);
-                match = k1 == key;
-                hv = v1;
+#pragma unroll
+            for (int j = V - 1; j >= 0; --j) {  // the lowest qualifying cell wins
+                if (o0 + j >= first && (kk[j] == key || kk[j] == kEmpty)) {
+                    hit = int(o0 + j);
+                    match = kk[j] == key;
+                    hv = vv[j];
+                }
             }
         }
         int ghit = hit;
@@ -328,8 +334,9 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
             int toff = -1;
             if (active) {
                 const u32 o0 = u32(gl) * V;
-                if (o0 >= first && k0 == kTomb) toff = int(o0);
-                else if (V == 2 && o0 + 1 >= first && k1 == kTomb) toff = int(o0 + 1);
+#pragma unroll
+                for (int j = V - 1; j >= 0; --j)
+                    if (o0 + j >= first && kk[j] == kTomb) toff = int(o0 + j);
             }
             if (G > 1) {
                 const u32 b = __ballot_sync(FULL, toff >= 0) & group_lanes;

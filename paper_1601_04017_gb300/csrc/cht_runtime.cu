@@ -175,7 +175,8 @@ cht_config default_config() {
 bool valid_config(const cht_config& c) {
     const int g = c.group_width;
     if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32)) return false;
-    if (c.lane_cells < 0 || c.lane_cells > 2 || (g == 32 && c.lane_cells == 2)) return false;
+    if (!(c.lane_cells == 0 || c.lane_cells == 1 || c.lane_cells == 2 || c.lane_cells == 4)) return false;
+    if ((g == 32 && c.lane_cells >= 2) || (g == 16 && c.lane_cells == 4)) return false;
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64) return false;
     const int t = c.migrate_tile;
     if (t != 0 && (t < 64 || t > 8192 || (t & (t - 1)) != 0)) return false;
@@ -299,21 +300,25 @@ Width pick_width(const cht_table* h, cht::Mode mode, u64 n) {
     if (w.g == 0) {
         // Only a plain insert batch is assumed to add n new cells; insertOrUpdate
         // batches are mostly updates of few hot keys, which want G = 1.  Measured
-        // on GB300 (2^28 cells): below load 0.6 one sector per lane is best;
-        // above it 4 lanes x 1 sector (128 B windows), and for finds at load
-        // 0.8 and more, 8 lanes x 1 sector (256 B windows).
+        // on GB300 (2^28 cells, 2^27 operations per call): a random access moves
+        // a whole 128-byte DRAM line, so below load 0.6 finds read one line per
+        // step (2 lanes x 2 sectors) and modifications one sector per lane;
+        // above it finds and inserts use 4 lanes x 2 sectors (256-byte windows,
+        // two lines, each lane's two loads in flight together) and the others
+        // 4 lanes x 1 sector.
         u64 filled = h->i_bound;
         if (mode == cht::kInsert) filled += n;
         if (filled > h->cap()) filled = h->cap();
         const double load = double(filled) / double(h->cap());
         if (load < 0.6) {
-            w.g = 1;
+            w.g = mode == cht::kFind ? 2 : 1;
+            if (w.v == 0) w.v = mode == cht::kFind ? 4 : 2;
         } else {
-            w.g = (mode == cht::kFind && load >= 0.8) ? 8 : 4;
-            if (w.v == 0) w.v = 2;
+            w.g = 4;
+            if (w.v == 0) w.v = (mode == cht::kFind || mode == cht::kInsert) ? 4 : 2;
         }
     }
-    if (w.g == 1) w.v = 2;
+    if (w.g == 1 && w.v != 4) w.v = 2;
     else if (w.v == 0 || w.g == 32) w.v = 1;
     return w;
 }

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 GROUPS = [0, 1, 2, 4, 8, 16, 32]  # 0 = chosen by load
 # (group width, cells per lane): every probe window shape the kernels support
-WIDTHS = [(g, 0) for g in GROUPS] + [(2, 2), (4, 2), (8, 2), (16, 2)]
+WIDTHS = [(g, 0) for g in GROUPS] + [(2, 2), (4, 2), (8, 2), (16, 2), (1, 4), (2, 4), (4, 4), (8, 4)]
 
 
 def _table(cht, cap, g=1, growable=False, v=0, **cfg):
