@@ -443,8 +443,18 @@ __device__ __forceinline__ void warp_flush_counters(DevState* st, u64 n_ins, u64
     }
 }
 
+// Two sectors per lane (V = 4) need more registers; for the wide windows
+// (G >= 4, the long probes at high load) asking for 5 resident CTAs per SM
+// (48 registers) keeps 40 warps' loads in flight instead of 32 (measured:
+// find misses at load 0.9 3 % faster, inserts to 0.9 7 %).  The 2-lane
+// window of short probes is faster with its natural register count.
+template <int G, int V>
+constexpr int op_min_blocks() {
+    return (V == 4 && G >= 4) ? 5 : 1;
+}
+
 template <int G, int V, int MODE, bool kReuse>
-__global__ void __launch_bounds__(kOpBlock) op_kernel(OpArgs a) {
+__global__ void __launch_bounds__(kOpBlock, op_min_blocks<G, V>()) op_kernel(OpArgs a) {
     // each warp owns a contiguous slice of the batch
     const u64 warp = (u64(blockIdx.x) * kOpBlock + threadIdx.x) >> 5;
     const u64 nwarps = (u64(gridDim.x) * kOpBlock) >> 5;
