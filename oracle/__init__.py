@@ -54,6 +54,7 @@ def _load():
             "or_create": (p, [u64, ctypes.c_int, ctypes.c_double]),
             "or_destroy": (None, [p]),
             "or_set_reuse": (None, [p, ctypes.c_int]),
+            "or_set_full_keys": (None, [p, ctypes.c_int]),
             "or_capacity": (u64, [p]),
             "or_nonempty": (u64, [p]),
             "or_live": (u64, [p]),
@@ -112,12 +113,13 @@ class OracleTable:
     """Sequential folklore table with phase semantics (one op type per call)."""
 
     def __init__(self, capacity: int, growable: bool = False, alpha: float = 0.5,
-                 reuse_tombstones: bool = False):
+                 reuse_tombstones: bool = False, full_key_space: bool = False):
         self._lib = _load()
         self._t = self._lib.or_create(int(capacity), int(bool(growable)), float(alpha))
         if not self._t:
             raise MemoryError("oracle table allocation failed")
         self._lib.or_set_reuse(self._t, int(bool(reuse_tombstones)))
+        self._lib.or_set_full_keys(self._t, int(bool(full_key_space)))
 
     def close(self):
         if self._t:

@@ -54,6 +54,9 @@ typedef struct {
     uint64_t probes;   /* cells inspected by all operations so far (statistics) */
     uint64_t migrations;
     int reuse_tombstones; /* inserts may take the first tombstone on their path */
+    int full_keys;        /* keys 0 and ~0 live in two special slots (Sec. 5) */
+    int sp_present[2];    /* special slot 0: key 0, slot 1: key ~0 */
+    uint64_t sp_val[2];
 } or_table;
 
 /* 64-bit finalizer of MurmurHash3 (Appleby, public domain): the paper hashes
@@ -131,9 +134,52 @@ void or_destroy(or_table *t)
  * reachable from its home, and every result is the same as without reuse. */
 void or_set_reuse(or_table *t, int on) { t->reuse_tombstones = on; }
 
+/* Full key space (off by default: keys 0 and ~0 are reserved and rejected
+ * with code 3).  The paper keeps the empty and deleted markers out of the
+ * key space and notes they could be stored separately; on, the two keys
+ * live in two slots beside the table, outside every probe, and behave like
+ * any other key: insert / insertOrUpdate / update / find / erase apply the
+ * dictionary meaning to the slot; migrations leave the slots alone. */
+void or_set_full_keys(or_table *t, int on) { t->full_keys = on; }
+
+enum { SP_FIND = 0, SP_INSERT = 1, SP_IOU = 2, SP_ERASE = 3, SP_UPDATE = 4 };
+
+static int special_op(or_table *t, uint64_t k, uint64_t d, int kind, int op, uint64_t *vout)
+{
+    const int s = k == OR_TOMB;
+    const int was = t->sp_present[s];
+    switch (kind) {
+    case SP_FIND:
+        if (vout) *vout = was ? t->sp_val[s] : 0;
+        return was ? OR_YES : OR_NO;
+    case SP_INSERT:
+        if (was) return OR_NO;
+        t->sp_present[s] = 1;
+        t->sp_val[s] = d;
+        return OR_YES;
+    case SP_IOU:
+        if (!was) {
+            t->sp_present[s] = 1;
+            t->sp_val[s] = d;
+            return OR_YES;
+        }
+        t->sp_val[s] = (op == OR_ADD) ? t->sp_val[s] + d : d;
+        return OR_NO;
+    case SP_UPDATE:
+        if (!was) return OR_NO;
+        t->sp_val[s] = (op == OR_ADD) ? t->sp_val[s] + d : d;
+        return OR_YES;
+    default: /* SP_ERASE */
+        if (!was) return OR_NO;
+        t->sp_present[s] = 0;
+        t->sp_val[s] = 0;
+        return OR_YES;
+    }
+}
+
 uint64_t or_capacity(const or_table *t) { return t->cap; }
 uint64_t or_nonempty(const or_table *t) { return t->I; }
-uint64_t or_live(const or_table *t) { return t->I - t->D; }
+uint64_t or_live(const or_table *t) { return t->I - t->D + t->sp_present[0] + t->sp_present[1]; }
 uint64_t or_probes(const or_table *t) { return t->probes; }
 uint64_t or_migrations(const or_table *t) { return t->migrations; }
 void or_reset_probes(or_table *t) { t->probes = 0; }
@@ -216,7 +262,7 @@ static void grow_if_needed(or_table *t)
  * Mode 0 is the plain insert of Sec. 3 (a present key is left untouched). */
 static int or_modify1(or_table *t, uint64_t k, uint64_t d, int mode, int op)
 {
-    if (is_reserved(k)) return OR_RESERVED;
+    if (is_reserved(k)) return t->full_keys ? special_op(t, k, d, mode == 1 ? SP_IOU : SP_INSERT, op, NULL) : OR_RESERVED;
     grow_if_needed(t);
     uint64_t mask = t->cap - 1;
     uint64_t i = home_of(k, t->log2c);
@@ -279,7 +325,7 @@ void or_update(or_table *t, const uint64_t *keys, const uint64_t *vals, uint64_t
         uint64_t k = keys[j];
         int r = OR_NO;
         if (is_reserved(k)) {
-            r = OR_RESERVED;
+            r = t->full_keys ? special_op(t, k, vals[j], SP_UPDATE, op, NULL) : OR_RESERVED;
         } else {
             uint64_t i = home_of(k, t->log2c);
             for (uint64_t step = 0; step < t->cap; ++step, i = (i + 1) & mask) {
@@ -307,7 +353,7 @@ void or_find(or_table *t, const uint64_t *keys, uint64_t n, uint64_t *vals_out, 
         int r = OR_NO;
         uint64_t v = 0;
         if (is_reserved(k)) {
-            r = OR_RESERVED;
+            r = t->full_keys ? special_op(t, k, 0, SP_FIND, 0, &v) : OR_RESERVED;
         } else {
             uint64_t i = home_of(k, t->log2c);
             for (uint64_t step = 0; step < t->cap; ++step, i = (i + 1) & mask) {
@@ -331,7 +377,7 @@ void or_erase(or_table *t, const uint64_t *keys, uint64_t n, uint8_t *flags)
         uint64_t k = keys[j];
         int r = OR_NO;
         if (is_reserved(k)) {
-            r = OR_RESERVED;
+            r = t->full_keys ? special_op(t, k, 0, SP_ERASE, 0, NULL) : OR_RESERVED;
         } else {
             uint64_t i = home_of(k, t->log2c);
             for (uint64_t step = 0; step < t->cap; ++step, i = (i + 1) & mask) {
@@ -347,7 +393,7 @@ void or_erase(or_table *t, const uint64_t *keys, uint64_t n, uint8_t *flags)
 
 /* forall (Sec. 3 "Bulk Operations"): the live elements in cell order. Returns
  * how many were written (at most max_n). */
-uint64_t or_export(const or_table *t, uint64_t *keys, uint64_t *vals, uint64_t max_n)
+static uint64_t export_cells(const or_table *t, uint64_t *keys, uint64_t *vals, uint64_t max_n)
 {
     uint64_t m = 0;
     for (uint64_t i = 0; i < t->cap; ++i) {
@@ -356,6 +402,22 @@ uint64_t or_export(const or_table *t, uint64_t *keys, uint64_t *vals, uint64_t m
         if (m < max_n) {
             if (keys) keys[m] = c->key;
             if (vals) vals[m] = c->val;
+        }
+        ++m;
+    }
+    return m;
+}
+
+/* forall (Sec. 3): every live element, the table's cells first, then the
+ * special slots' keys (0, then ~0) when present. */
+uint64_t or_export(const or_table *t, uint64_t *keys, uint64_t *vals, uint64_t max_n)
+{
+    uint64_t m = export_cells(t, keys, vals, max_n);
+    for (int s = 0; s < 2; ++s) {
+        if (!t->sp_present[s]) continue;
+        if (m < max_n) {
+            if (keys) keys[m] = s ? OR_TOMB : OR_EMPTY;
+            if (vals) vals[m] = t->sp_val[s];
         }
         ++m;
     }
@@ -423,7 +485,7 @@ int or_check_invariants(const or_table *t, char *msg, size_t msglen)
     }
     uint64_t *ks = (uint64_t *)malloc((live ? live : 1) * sizeof(uint64_t));
     if (!ks) return -1;
-    uint64_t m = or_export(t, ks, NULL, live);
+    uint64_t m = export_cells(t, ks, NULL, live);
     qsort(ks, m, sizeof(uint64_t), cmp_u64);
     for (uint64_t j = 1; j < m; ++j) {
         if (ks[j] == ks[j - 1]) {

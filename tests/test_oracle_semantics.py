@@ -17,12 +17,12 @@ MASK = (1 << 64) - 1
 class DictModel:
     """A sequential dictionary with the paper's return conventions (Sec. 3)."""
 
-    def __init__(self):
+    def __init__(self, full_keys=False):
         self.d = {}
+        self.full_keys = full_keys  # keys 0 and ~0 are ordinary keys
 
-    @staticmethod
-    def reserved(k):
-        return k == 0 or k == MASK
+    def reserved(self, k):
+        return not self.full_keys and (k == 0 or k == MASK)
 
     def insert(self, k, v):
         if self.reserved(k):
@@ -86,14 +86,14 @@ def _random_batch(rng, pool, n):
 
 @pytest.mark.parametrize("log2c", [6, 7, 8, 10])
 @pytest.mark.parametrize("seed", [0, 1, 2])
-@pytest.mark.parametrize("reuse", [False, True])
-def test_oracle_matches_dictionary(oracle_mod, log2c, seed, reuse):
+@pytest.mark.parametrize("reuse,full_keys", [(False, False), (True, False), (False, True), (True, True)])
+def test_oracle_matches_dictionary(oracle_mod, log2c, seed, reuse, full_keys):
     c = 1 << log2c
     rng = np.random.default_rng(1000 * log2c + seed)
     pool = np.concatenate([W.uniform_keys(c // 2, start=seed * 4096, seed=5),
                            _wrap_keys(oracle_mod, log2c, 6, seed)])
-    t = oracle_mod.OracleTable(c, reuse_tombstones=reuse)
-    m = DictModel()
+    t = oracle_mod.OracleTable(c, reuse_tombstones=reuse, full_key_space=full_keys)
+    m = DictModel(full_keys)
     for step in range(40):
         kind = rng.choice(["insert", "iou_add", "iou_ow", "find", "erase", "upd_add", "upd_ow"])
         # keep the number of inserted cells (tombstones count) below c
@@ -300,4 +300,30 @@ def test_growable_purges_when_mostly_tombstones(oracle_mod):
     assert t.capacity == 256
     assert t.migrations > 0
     assert t.live == window
+    t.assert_invariants()
+
+
+def test_full_key_space_special_slots(oracle_mod):
+    """Keys 0 and ~0 in the special slots: dictionary results, kept across
+    growth and shrinking migrations, counted as live but never as a cell."""
+    t = oracle_mod.OracleTable(64, growable=True, full_key_space=True)
+    ks = W.uniform_keys(100, seed=23)
+    special = np.array([0, MASK], dtype=np.uint64)
+    assert (t.insert(special, np.array([7, 9], dtype=np.uint64)) == 1).all()
+    assert (t.insert(special, np.array([1, 1], dtype=np.uint64)) == 0).all()
+    t.insert(ks, ks)
+    assert t.capacity == 256 and t.nonempty == 100 and t.live == 102
+    assert (t.insert_or_update(special, np.array([5, 5], dtype=np.uint64), oracle_mod.ADD) == 0).all()
+    v, f = t.find(special)
+    assert f.tolist() == [1, 1] and v.tolist() == [12, 14]
+    assert t.erase(special[1:]).tolist() == [1] and t.erase(special[1:]).tolist() == [0]
+    v, f = t.find(special)
+    assert f.tolist() == [1, 0] and v.tolist() == [12, 0]
+    assert t.update(special, np.array([3, 3], dtype=np.uint64), oracle_mod.OVERWRITE).tolist() == [1, 0]
+    t.migrate(4096)
+    t.migrate(256)
+    ek, ev = t.export()
+    d = dict(zip(ek.tolist(), ev.tolist()))
+    assert d[0] == 3 and MASK not in d and len(d) == 101
+    assert t.nonempty == 100 and t.live == 101
     t.assert_invariants()
