@@ -100,7 +100,12 @@ typedef enum {
  * semantics: no erase runs during an insert batch).  Results are the same
  * either way; reuse keeps probes short when keys are erased and inserted
  * again and again, where without it every cycle leaves a tombstone on the
- * key's probe path. */
+ * key's probe path.  full_key_space: 0 (default) = keys 0 and ~0 are the
+ * empty and deleted markers and operations on them return code 3 with the
+ * CHT_STATUS_RESERVED bit; 1 = the two keys are stored in two special slots
+ * beside the table and behave like any other key (every operation, export,
+ * and the live count of cht_size include them; they never occupy a cell and
+ * migrations leave them alone). */
 typedef struct {
     int group_width;
     int lane_cells;
@@ -109,6 +114,7 @@ typedef struct {
     double alpha;
     int iou_aggregate;
     int reuse_tombstones;
+    int full_key_space;
 } cht_config;
 
 /* Create a table of at least `capacity` cells (rounded up to a power of two,
@@ -183,8 +189,9 @@ cht_status cht_erase(cht_handle h, const uint64_t *keys, uint64_t n, uint8_t *er
  * `stream`). */
 cht_status cht_migrate(cht_handle h, uint64_t new_capacity, cht_stream_t stream);
 
-/* Synchronize `stream` and report: live elements (I - D), non-empty cells
- * I (tombstones included), capacity c.  Any out-pointer may be NULL.
+/* Synchronize `stream` and report: live elements (I - D, plus the keys in
+ * the special slots under full_key_space), non-empty cells I (tombstones
+ * included), capacity c.  Any out-pointer may be NULL.
  * Returns CHT_ERR_TABLE_FULL / CHT_ERR_RESERVED_KEY if the sticky status has
  * that bit set (the status is not cleared), else CHT_OK. */
 cht_status cht_size(cht_handle h, uint64_t *live, uint64_t *nonempty, uint64_t *capacity,

@@ -37,6 +37,10 @@ struct DevState {
     u32 status;
     u32 mig_fail;
     u64 export_pos;
+    // full key space: keys 0 and ~0 live here, beside the cells
+    // (slot 0: key 0, slot 1: key ~0); untouched by migrations
+    u64 sp_val[2];
+    u32 sp_present[2];
 };
 
 // fmix64, the 64-bit finalizer of MurmurHash3 (Appleby, public domain).

@@ -125,7 +125,8 @@ __device__ __forceinline__ void run_item(const EngineArgs& e, const EngineChunk&
     OpArgs a;
     a.cells = t.cells;
     a.log2c = t.log2c;
-    a.reuse = t.reuse;
+    a.reuse = t.flags & kTabReuse;
+    a.full_keys = t.flags & kTabFullKeys;
     a.keys = b.keys;
     a.vals = b.vals;
     a.vals_out = b.vals_out;

@@ -22,6 +22,7 @@ struct OpArgs {
     Cell* cells;
     u32 log2c;
     u32 reuse;            // inserts may take the first tombstone on their path
+    u32 full_keys;        // keys 0 and ~0 go to the special slots in st
     const u64* keys;
     const u64* vals;      // insert / insert_or_update input values (else NULL)
     u64* vals_out;        // find output values (else NULL)
@@ -65,10 +66,14 @@ cudaError_t launch_export(const Cell* cells, u32 log2c, u64* keys_out, u64* vals
 // ---- batched engine (cht_engine.cu) ----------------------------------------
 constexpr u32 kChunkOps = 256;  // operations per engine work item
 
+// EngineTable::flags
+constexpr u32 kTabReuse = 1u;     // tombstone reuse by inserts
+constexpr u32 kTabFullKeys = 2u;  // keys 0 and ~0 in the special slots
+
 struct EngineTable {
     Cell* cells;
     u32 log2c;
-    u32 reuse;  // tombstone reuse by inserts (table configuration)
+    u32 flags;  // table configuration, kTab* bits
     DevState* st;
 };
 
@@ -150,7 +155,8 @@ struct TableInfo {
     int growable;
     double alpha;
     u64 bound;  // upper bound on the number of non-empty cells
-    int reuse;  // tombstone reuse by inserts
+    int reuse;      // tombstone reuse by inserts
+    int full_keys;  // keys 0 and ~0 in the special slots
 };
 TableInfo table_info(const cht_table* h);
 void table_set_bound(cht_table* h, u64 bound, bool exact);
@@ -177,6 +183,6 @@ namespace cht {
 // that live outside the runtime translation unit); group_width is the
 // effective width a find would use now.
 void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int* device,
-                int* group_width, int* lane_cells, int* ctas_per_sm);
+                int* group_width, int* lane_cells, int* ctas_per_sm, int* full_keys);
 
 }  // namespace cht

@@ -269,6 +269,14 @@ __global__ void __launch_bounds__(256) export_kernel(const Cell* __restrict__ ce
                                                      DevState* st) {
     const int lane = threadIdx.x & 31;
     const u64 stride = u64(gridDim.x) * blockDim.x;
+    if (blockIdx.x == 0 && threadIdx.x < 2 && st->sp_present[threadIdx.x]) {
+        // full key space: the special slots' keys (0, ~0) are live elements too
+        const u64 p = atomicAdd(&st->export_pos, 1ull);
+        if (p < max_n) {
+            keys_out[p] = threadIdx.x ? kTomb : kEmpty;
+            if (vals_out) vals_out[p] = st->sp_val[threadIdx.x];
+        }
+    }
     for (u64 base = u64(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); base < c;
          base += stride) {
         const u64 i = base + lane;

@@ -60,8 +60,8 @@ extern "C" cht_status cht_find_noalloc(cht_handle h, const uint64_t* keys, uint6
     cht::Cell* cells = nullptr;
     cht::u32 log2c = 0;
     cht::DevState* st = nullptr;
-    int device = 0, group_width = 1, lane_cells = 2, ctas_per_sm = 0;
-    cht::table_view(h, &cells, &log2c, &st, &device, &group_width, &lane_cells, &ctas_per_sm);
+    int device = 0, group_width = 1, lane_cells = 2, ctas_per_sm = 0, full_keys = 0;
+    cht::table_view(h, &cells, &log2c, &st, &device, &group_width, &lane_cells, &ctas_per_sm, &full_keys);
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != device && cudaSetDevice(device) != cudaSuccess) return CHT_ERR_CUDA;
@@ -81,6 +81,7 @@ extern "C" cht_status cht_find_noalloc(cht_handle h, const uint64_t* keys, uint6
             a.cells = cells;
             a.log2c = log2c;
             a.reuse = 0;  // finds never take cells
+            a.full_keys = cht::u32(full_keys);
             a.keys = s_keys;
             a.vals = nullptr;
             a.vals_out = s_vals;

@@ -84,6 +84,38 @@ __device__ __forceinline__ int modify_at(Cell* cp, bool is_key, u64 key, u64 d) 
     return kStepContinue;
 }
 
+// Full key space: an operation on key 0 or ~0 works on the table's special
+// slot for it (slot 0 / 1 in DevState) with the dictionary meaning; under
+// phase semantics one batch holds one operation type, so presence flips only
+// one way per batch.  The value of an absent key is 0, so insertOrUpdate(add)
+// can add unconditionally.  Returns the operation's result code.
+template <int MODE>
+__device__ __forceinline__ unsigned char special_op(DevState* st, u64 key, u64 d, u64* vout) {
+    const int s = key == kTomb ? 1 : 0;
+    unsigned int* pres = &st->sp_present[s];
+    unsigned long long* val = reinterpret_cast<unsigned long long*>(&st->sp_val[s]);
+    if (MODE == kFind) {
+        const u32 p = *reinterpret_cast<volatile unsigned int*>(pres);
+        *vout = p ? *reinterpret_cast<volatile unsigned long long*>(val) : 0;
+        return p ? kYes : kNo;
+    }
+    if (MODE == kUpdAdd || MODE == kUpdOverwrite) {
+        if (*reinterpret_cast<volatile unsigned int*>(pres) == 0) return kNo;
+        if (MODE == kUpdAdd) atomicAdd(val, d);
+        else atomicExch(val, d);
+        return kYes;
+    }
+    if (MODE == kErase) {
+        if (atomicCAS(pres, 1u, 0u) != 1u) return kNo;
+        atomicExch(val, 0ull);
+        return kYes;
+    }
+    const bool ins = atomicCAS(pres, 0u, 1u) == 0u;
+    if (MODE == kIouAdd) atomicAdd(val, d);
+    else if (MODE == kIouOverwrite || ins) atomicExch(val, d);
+    return ins ? kYes : kNo;
+}
+
 // Tombstone reuse (insert modes, reuse on): the probe has shown `key`
 // absent (it reached an empty cell or saw every cell) after passing the
 // tombstone at cp.  Claim it with a 16-byte CAS on the content read now.
@@ -220,10 +252,16 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                     if (kHasVals) d = kStaged ? op_val<kStaged>(a, sg, idx) : wv;
                     if (is_reserved(key)) {
                         if (gl == 0) {
-                            op_code<kStaged>(a, sg, idx, kCodeReserved);
-                            if (MODE == kFind) op_vout<kStaged>(a, sg, idx, 0);
+                            if (a.full_keys) {
+                                u64 v = 0;
+                                op_code<kStaged>(a, sg, idx, special_op<MODE>(a.st, key, d, &v));
+                                if (MODE == kFind) op_vout<kStaged>(a, sg, idx, v);
+                            } else {
+                                op_code<kStaged>(a, sg, idx, kCodeReserved);
+                                if (MODE == kFind) op_vout<kStaged>(a, sg, idx, 0);
+                            }
                         }
-                        sbits |= kReserved;
+                        if (!a.full_keys) sbits |= kReserved;
                     } else {
                         fresh = true;
                         active = true;
@@ -612,8 +650,13 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
                 key = ld_stream(a.keys + idx);
                 d = ld_stream(a.vals + idx);
                 if (is_reserved(key)) {
-                    if (a.codes) a.codes[idx] = kCodeReserved;
-                    sbits |= kReserved;
+                    if (a.full_keys) {
+                        const unsigned char r = special_op<MODE>(a.st, key, d, nullptr);
+                        if (a.codes) a.codes[idx] = r;
+                    } else {
+                        if (a.codes) a.codes[idx] = kCodeReserved;
+                        sbits |= kReserved;
+                    }
                     valid = false;
                 }
             }

@@ -169,6 +169,7 @@ cht_config default_config() {
     c.alpha = 0.5;
     c.iou_aggregate = 1;
     c.reuse_tombstones = 0;
+    c.full_key_space = 0;
     return c;
 }
 
@@ -183,6 +184,7 @@ bool valid_config(const cht_config& c) {
     if (!(c.alpha > 0.0 && c.alpha < 1.0)) return false;
     if (c.iou_aggregate < 0 || c.iou_aggregate > 2) return false;
     if (c.reuse_tombstones < 0 || c.reuse_tombstones > 1) return false;
+    if (c.full_key_space < 0 || c.full_key_space > 1) return false;
     return true;
 }
 
@@ -329,6 +331,7 @@ cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals
     a.cells = h->cells;
     a.log2c = h->log2c;
     a.reuse = u32(h->cfg.reuse_tombstones);
+    a.full_keys = u32(h->cfg.full_key_space);
     a.keys = keys;
     a.vals = vals;
     a.vals_out = vals_out;
@@ -586,6 +589,7 @@ TableInfo table_info(const cht_table* h) {
     i.alpha = h->cfg.alpha;
     i.bound = h->i_bound;
     i.reuse = h->cfg.reuse_tombstones;
+    i.full_keys = h->cfg.full_key_space;
     return i;
 }
 
@@ -613,7 +617,7 @@ cht_status runtime_alloc(void** p, u64 bytes, cudaStream_t s) { return lib_alloc
 void runtime_free(void* p, u64 bytes, cudaStream_t s) { lib_free(p, bytes, s); }
 
 void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int* device, int* group_width,
-                int* lane_cells, int* ctas_per_sm) {
+                int* lane_cells, int* ctas_per_sm, int* full_keys) {
     *cells = h->cells;
     *log2c = h->log2c;
     *st = h->st;
@@ -622,6 +626,7 @@ void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int
     *group_width = w.g;
     *lane_cells = w.v;
     *ctas_per_sm = h->cfg.ctas_per_sm;
+    *full_keys = h->cfg.full_key_space;
 }
 
 }  // namespace cht
@@ -819,7 +824,7 @@ cht_status cht_size(cht_handle h, uint64_t* live, uint64_t* nonempty, uint64_t* 
     if (r != CHT_OK) return r;
     h->i_bound = ds.I;
     h->i_exact = true;
-    if (live) *live = ds.I - ds.D;
+    if (live) *live = ds.I - ds.D + ds.sp_present[0] + ds.sp_present[1];
     if (nonempty) *nonempty = ds.I;
     if (capacity) *capacity = h->cap();
     if (ds.status & CHT_STATUS_FULL) return CHT_ERR_TABLE_FULL;
@@ -1063,7 +1068,8 @@ cht_status cht_plan_create(const cht_batch_op* ops, uint64_t n_ops, cht_plan_han
     for (size_t t = 0; t < p->tables.size(); ++t) {
         tabs[t].cells = p->tables[t]->cells;
         tabs[t].log2c = p->tables[t]->log2c;
-        tabs[t].reuse = u32(p->tables[t]->cfg.reuse_tombstones);
+        tabs[t].flags = (p->tables[t]->cfg.reuse_tombstones ? cht::kTabReuse : 0u) |
+                        (p->tables[t]->cfg.full_key_space ? cht::kTabFullKeys : 0u);
         tabs[t].st = p->tables[t]->st;
     }
     DeviceGuard g(p->tables.empty() ? current_device() : p->device);

@@ -346,7 +346,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
         const cht::TableInfo ti = cht::table_info(s->tables[t]);
         tabs[t].cells = ti.cells;
         tabs[t].log2c = ti.log2c;
-        tabs[t].reuse = u32(ti.reuse);
+        tabs[t].flags = (ti.reuse ? cht::kTabReuse : 0u) | (ti.full_keys ? cht::kTabFullKeys : 0u);
         tabs[t].st = ti.st;
     }
     std::vector<cht::EngineBatch> batches(parts.size());
@@ -413,7 +413,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
     e.spin_limit = 2000000000ll;
     e.max_backoff_ns = 8192;
     e.any_reuse = 0;
-    for (const cht::EngineTable& et : tabs) e.any_reuse |= int(et.reuse);
+    for (const cht::EngineTable& et : tabs) e.any_reuse |= int(et.flags & cht::kTabReuse);
     e.inject_stall = 0;
     if (cudaEventRecord(st.t_eng0, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
     if (cht::launch_engine(e, 1, 2, 0, true, s->stream) != cudaSuccess) {

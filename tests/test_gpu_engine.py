@@ -178,6 +178,8 @@ def test_engine_chain_of_small_batches(cuda_lib, oracle_mod, chunk, reuse):
         op = int(rng.choice([W.OP_FIND, W.OP_INSERT, W.OP_IOU_ADD, W.OP_ERASE, W.OP_UPDATE_ADD],
                             p=[0.35, 0.3, 0.15, 0.1, 0.1]))
         k = universe[rng.integers(0, universe.size, n)]
+        if t == 1 and i % 3 == 0:  # the reserved keys, on the table that stores them
+            k[: max(1, n // 100)] = np.uint64(0) if i % 2 else np.uint64((1 << 64) - 1)
         # an insert's value is a function of its key: whichever copy of a
         # repeated key wins, the stored value is the same
         v = k ^ np.uint64(0x5DEECE66D) if op == W.OP_INSERT else W.uniform_keys(n, seed=1000 + i)
@@ -192,7 +194,9 @@ def test_engine_chain_of_small_batches(cuda_lib, oracle_mod, chunk, reuse):
     tables = [cuda_lib.Table(1 << 14), cuda_lib.Table(1 << 14)]
     if reuse:
         tables[0].set_config(reuse_tombstones=1)  # one table with reuse, one without, in one launch
-    otabs = [oracle_mod.OracleTable(1 << 14, reuse_tombstones=bool(reuse)), oracle_mod.OracleTable(1 << 14)]
+    tables[1].set_config(full_key_space=1)  # keys 0 and ~0 in its special slots
+    otabs = [oracle_mod.OracleTable(1 << 14, reuse_tombstones=bool(reuse)),
+             oracle_mod.OracleTable(1 << 14, full_key_space=True)]
     ops, spans, o = [], [], 0
     for t, op, k, v in specs:
         n = k.size

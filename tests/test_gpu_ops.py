@@ -339,3 +339,58 @@ def test_update_matches_oracle(cuda_lib, oracle_mod, g, v, agg, mode):
         got = to_np_u64(vo)
         for k, gv in zip(uk, got):
             assert gv in set(vs[ks == k].tolist())
+
+
+@pytest.mark.parametrize("g,v,agg", [(0, 0, 1), (1, 0, 0), (4, 4, 0), (8, 2, 0), (32, 1, 0), (0, 0, 2)])
+def test_full_key_space_matches_oracle(cuda_lib, oracle_mod, g, v, agg):
+    """Keys 0 and ~0 mixed into every operation type (many copies per batch):
+    codes, found values and the exported contents equal the oracle's special
+    slots; the live count includes them, the cells never hold them."""
+    c = 1 << 14
+    rng = np.random.default_rng(31)
+    t = _table(cuda_lib, c, g, v=v, iou_aggregate=agg, full_key_space=1)
+    o = oracle_mod.OracleTable(c, full_key_space=True)
+    pool = np.concatenate([W.uniform_keys(3000, seed=59), np.array([0, (1 << 64) - 1], dtype=np.uint64)])
+    for r in range(30):
+        n = int(rng.integers(1, 3000))
+        ks = pool[rng.integers(0, pool.size, n)]
+        ks[rng.integers(0, n, max(1, n // 50))] = rng.choice(np.array([0, (1 << 64) - 1], dtype=np.uint64))
+        vs = rng.integers(1, 1 << 40, n).astype(np.uint64)
+        kind = rng.choice(["insert", "iou_add", "iou_ow", "find", "erase", "upd_add", "upd_ow"])
+        codes = codes_buf(n)
+        if kind == "find":
+            vo = vals_buf(n)
+            t.find(to_dev(ks), vo, codes)
+            ev, ef = o.find(ks)
+            assert np.array_equal(to_np_u8(codes), ef) and np.array_equal(to_np_u64(vo), ev)
+            continue
+        if kind == "insert":
+            vs = ks ^ np.uint64(0x1234567)  # the stored value does not depend on which copy wins
+            t.insert(to_dev(ks), to_dev(vs), codes)
+            oc = o.insert(ks, vs)
+        elif kind in ("iou_add", "iou_ow"):
+            op = cuda_lib.ADD if kind == "iou_add" else cuda_lib.OVERWRITE
+            vs = vs if kind == "iou_add" else ks ^ np.uint64(0x7654321)
+            t.insert_or_update(to_dev(ks), to_dev(vs), op, codes)
+            oc = o.insert_or_update(ks, vs, oracle_mod.ADD if kind == "iou_add" else oracle_mod.OVERWRITE)
+        elif kind in ("upd_add", "upd_ow"):
+            op = cuda_lib.ADD if kind == "upd_add" else cuda_lib.OVERWRITE
+            vs = vs if kind == "upd_add" else ks ^ np.uint64(0x55AA)
+            t.update(to_dev(ks), to_dev(vs), op, codes)
+            oc = o.update(ks, vs, oracle_mod.ADD if kind == "upd_add" else oracle_mod.OVERWRITE)
+            assert np.array_equal(to_np_u8(codes), oc)
+        else:
+            t.erase(to_dev(ks), codes)
+            oc = o.erase(ks)
+        gc = to_np_u8(codes)
+        for k in np.unique(ks):
+            m = ks == k
+            assert int(gc[m].astype(np.int64).sum()) == int(oc[m].astype(np.int64).sum()), (kind, k)
+        live, ne, _ = t.size(check=True)
+        assert live == o.live and ne == o.nonempty
+        assert_same_live_set(t, o)
+    cells = to_np_u64(t.cells()).reshape(-1, 2)
+    assert not (cells[:, 0] == 0).all() or o.nonempty == 0
+    g_ = oracle_mod.OracleTable(64)
+    g_.load_cells(cells)
+    g_.assert_invariants()
