@@ -343,6 +343,59 @@ def latency_percentiles(cht, inp, reps: int):
         p99 = v[min(len(v) - 1, int(math.ceil(0.99 * len(v))) - 1)]
         out[k] = {"p50_ms": round(p50, 5), "p99_ms": round(p99, 5),
                   "mops_at_p50": round(n / (p50 * 1e-3) / 1e6, 1)}
+    # The same calls back to back (the host enqueues ahead of the GPU, so the
+    # host-side cost of a call is hidden) and replayed from a CUDA graph (no
+    # host work at all: the device time of a call).  As in the single calls,
+    # the finds read one table, which stays in L2 (16 MiB); each insert fills
+    # a table just cleared (the clear's memset is timed alone and subtracted).
+    # frac_of_roofline: algorithmic bytes at load 0.5 over the measured copy
+    # bandwidth.
+    R = 32
+    peak = load_peaks()[0]
+    t1 = cht.Table(1 << 20)
+    t1.insert(wl["keys"], wl["vals"], codes)
+    t2 = cht.Table(1 << 20)
+    torch.cuda.synchronize()
+
+    def timed_calls(calls, graph):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if not graph:
+            torch.cuda.synchronize()
+            a.record(s)
+            for fn in calls:
+                fn()
+            b.record(s)
+            b.synchronize()
+            return a.elapsed_time(b) / len(calls)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for fn in calls:
+                fn()
+        g.replay()
+        torch.cuda.synchronize()
+        a.record(s)
+        g.replay()
+        b.record(s)
+        b.synchronize()
+        del g
+        return a.elapsed_time(b) / len(calls)
+
+    def ins():
+        t2.clear()
+        t2.insert(wl["keys"], wl["vals"], codes)
+
+    for name, bpo, call, base in (("insert", 89.0, ins, t2.clear),
+                                  ("find_hit", 57.0, lambda: t1.find(wl["hits"][0.5], vout, codes), None),
+                                  ("find_miss", 73.0, lambda: t1.find(wl["misses"], vout, codes), None)):
+        for kind, graph in (("back_to_back", False), ("graph", True)):
+            per_ms = timed_calls([call] * R, graph)
+            if base is not None:
+                per_ms -= timed_calls([base] * R, graph)
+            mops = n / (per_ms * 1e-3) / 1e6
+            out[f"{name}_{kind}"] = {"ms_per_call": round(per_ms, 5), "mops": round(mops, 1),
+                                     "frac_of_roofline": round(mops * 1e6 * bpo / (peak * 1e9), 4)}
+    t1.destroy()
+    t2.destroy()
     return out
 
 

@@ -6,6 +6,22 @@
 namespace cht {
 namespace {
 
+// Launch with programmatic stream serialization (see pdl_enter).
+template <typename K>
+cudaError_t launch_pdl(K kernel, unsigned grid, unsigned block, size_t smem, cudaStream_t s, const OpArgs& a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <int G, int V, int MODE, bool kReuse = false>
 cudaError_t launch_one(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     static std::atomic<int> occ{0};
@@ -22,9 +38,9 @@ cudaError_t launch_one(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     const u64 need = (a.n + kOpBlock - 1) / kOpBlock;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    op_kernel<G, V, MODE, kReuse><<<unsigned(grid), kOpBlock, 0, s>>>(a);
+    const cudaError_t e = launch_pdl(op_kernel<G, V, MODE, kReuse>, unsigned(grid), kOpBlock, 0, s, a);
     count_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Tombstone reuse (insert modes of a table that has it on): kernels exist for
@@ -92,9 +108,9 @@ cudaError_t launch_agg(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     const u64 nwin = (a.n + kAggWindow - 1) / kAggWindow;
     if (grid > nwin) grid = nwin;
     if (grid < 1) grid = 1;
-    iou_agg_kernel<MODE, WD, RE><<<unsigned(grid), kAggBlock, smem, s>>>(a);
+    const cudaError_t e = launch_pdl(iou_agg_kernel<MODE, WD, RE>, unsigned(grid), kAggBlock, smem, s, a);
     count_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace

@@ -491,8 +491,20 @@ constexpr int op_min_blocks() {
     return (V == 4 && G >= 4) ? 5 : 1;
 }
 
+// Programmatic dependent launch: the operation kernels are launched so that
+// the next one on the stream may be scheduled while this one drains; each
+// lets its dependents start at once and then waits until the grids before it
+// have completed and their memory is visible (a no-op when it was launched
+// the ordinary way).  Stream order of every memory effect is unchanged; the
+// launch latency of back-to-back calls overlaps the previous call's tail.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <int G, int V, int MODE, bool kReuse>
 __global__ void __launch_bounds__(kOpBlock, op_min_blocks<G, V>()) op_kernel(OpArgs a) {
+    pdl_enter();
     // each warp owns a contiguous slice of the batch
     const u64 warp = (u64(blockIdx.x) * kOpBlock + threadIdx.x) >> 5;
     const u64 nwarps = (u64(gridDim.x) * kOpBlock) >> 5;
@@ -617,6 +629,7 @@ constexpr size_t agg_smem_bytes() {
 
 template <int MODE, bool WARP_DEDUP, bool kReuse>
 __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
+    pdl_enter();
     constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
     constexpr bool kAdd = MODE == kIouAdd || MODE == kUpdAdd;
     extern __shared__ __align__(16) unsigned char agg_smem[];
