@@ -378,7 +378,8 @@ cht_status cht_server_stats(cht_server_handle s, uint64_t *steps, uint64_t *comp
  * clock).  gpu_step_ms: device time from a step's first migration or copy to
  * its last copy back (steps run one after another on the stream, so the
  * makespan minus this is time the stream had no step to run); engine_ms: the
- * engine launches alone; host_admit_ms: host time spent admitting requests
+ * engine launches (with the step's metadata upload when no migration or copy
+ * precedes the launch); host_admit_ms: host time spent admitting requests
  * and preparing launches (steps that launched); rounds: sum over steps of
  * the longest chain of dependent batches (one table's requests in arrival
  * order); parts: request parts launched; chunks: engine work items;

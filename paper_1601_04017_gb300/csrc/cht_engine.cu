@@ -225,6 +225,26 @@ __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
             run_item<G, V, kStaged, kReuse>(e, fc, fb, t, sg, lane, f + 1 == ch.nfollow ? ch.nfollow + 1u : 0u);
         }
     }
+    if (e.n_snap) {
+        // the last warp to finish reads the counts every other warp flushed
+        // (their fence orders the flush before their count here) and writes
+        // the snapshot, possibly straight into pinned host memory
+        u64 prior = 0;
+        if (lane == 0) {
+            __threadfence();
+            prior = atomicAdd(e.warps_done, 1ull);
+        }
+        prior = __shfl_sync(FULL, prior, 0);
+        const u64 nwarps = u64(gridDim.x) * (blockDim.x / 32);
+        if (prior + 1 == nwarps) {
+            __threadfence();
+            for (u32 i = lane; i < e.n_snap; i += 32) {
+                const DevState* st = e.tables[e.snap_tables[i]].st;
+                e.snap_out[2 * i] = *reinterpret_cast<const volatile unsigned long long*>(&st->I);
+                e.snap_out[2 * i + 1] = *reinterpret_cast<const volatile unsigned long long*>(&st->D);
+            }
+        }
+    }
 }
 
 template <int G, int V, bool kStaged, bool kReuse = false>
@@ -256,23 +276,7 @@ cudaError_t launch_engine_gv(const EngineArgs& e, bool staged, int ctas_per_sm, 
                   : launch_engine_gvs<G, V, false>(e, ctas_per_sm, s);
 }
 
-__global__ void snapshot_kernel(const EngineTable* tables, const u32* touched, u32 n, unsigned long long* out) {
-    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const DevState* st = tables[touched[i]].st;
-        out[2 * i] = st->I;
-        out[2 * i + 1] = st->D;
-    }
-}
-
 }  // namespace
-
-cudaError_t launch_snapshot(const EngineTable* tables, const u32* touched, u32 n, unsigned long long* out,
-                            cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    snapshot_kernel<<<(n + 255) / 256, 256, 0, s>>>(tables, touched, n, out);
-    count_launch();
-    return cudaGetLastError();
-}
 
 cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, bool staged,
                           cudaStream_t s) {

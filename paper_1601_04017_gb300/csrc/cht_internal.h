@@ -114,6 +114,13 @@ struct EngineArgs {
     long long spin_limit;      // bound of one dependency wait, in clock cycles
     unsigned max_backoff_ns;   // longest sleep between two polls of a dependency counter
     int any_reuse;             // some table of the launch reuses tombstones
+    // optional snapshot at the end of the launch: the last warp to finish
+    // writes I, D of tables[snap_tables[i]] to snap_out[2i], snap_out[2i + 1]
+    // (n_snap = 0: none); warps_done: a counter, zero before the launch
+    const u32* snap_tables;
+    u32 n_snap;
+    unsigned long long* snap_out;
+    unsigned long long* warps_done;
     int inject_stall;          // testing: the first chunk waits for a count nothing reaches
 };
 
@@ -122,10 +129,6 @@ struct EngineArgs {
 cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, bool staged,
                           cudaStream_t s);
 
-// out[2i], out[2i+1] = I, D of tables[touched[i]] (i < n), read after the
-// work before it on the stream.
-cudaError_t launch_snapshot(const EngineTable* tables, const u32* touched, u32 n, unsigned long long* out,
-                            cudaStream_t s);
 
 }  // namespace cht
 

@@ -969,6 +969,10 @@ cht::EngineArgs plan_args(const cht_plan* p) {
     e.max_backoff_ns = p->cfg.poll_ns > 0 ? unsigned(p->cfg.poll_ns) : 8192u;
     e.any_reuse = 0;
     for (const cht_table* h : p->tables) e.any_reuse |= h->cfg.reuse_tombstones;
+    e.snap_tables = nullptr;
+    e.n_snap = 0;
+    e.snap_out = nullptr;
+    e.warps_done = nullptr;
     return e;
 }
 

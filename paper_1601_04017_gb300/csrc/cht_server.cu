@@ -84,6 +84,7 @@ struct Step {
     // timing: start of the step's device work (migrations, copies), engine
     // launch start / end; the step ends at `ev`
     cudaEvent_t t_begin = nullptr, t_eng0 = nullptr, t_eng1 = nullptr;
+    bool eng_from_begin = false;  // no migration or copy ran before the engine: t_eng0 not recorded
     u64 arena_end = 0, meta_end = 0, dmeta_end = 0;
     std::vector<u32> touched;
     std::vector<u64> new_cells;          // per touched table
@@ -175,7 +176,8 @@ cht_status poll(cht_server* s, u32* completed_now) {
         }
         float ms_step = 0, ms_eng = 0;
         if (cudaEventElapsedTime(&ms_step, st.t_begin, st.ev) == cudaSuccess) s->prof.gpu_step_ms += ms_step;
-        if (cudaEventElapsedTime(&ms_eng, st.t_eng0, st.t_eng1) == cudaSuccess) s->prof.engine_ms += ms_eng;
+        if (cudaEventElapsedTime(&ms_eng, st.eng_from_begin ? st.t_begin : st.t_eng0, st.t_eng1) == cudaSuccess)
+            s->prof.engine_ms += ms_eng;
         cudaGetLastError();
         st.rec.gpu_ms = ms_step;
         st.rec.engine_ms = ms_eng;
@@ -232,6 +234,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
         }
     } guard{s, &st};
     if (cudaEventRecord(st.t_begin, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
+    bool enqueued_before_engine = false;  // a migration or staging copy precedes the engine
     std::vector<char> blocked(nt, 0);
     std::vector<u64> step_new(nt, 0);
     std::vector<Part> parts;
@@ -277,6 +280,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
                 }
                 cht_status r = cht::table_migrate_to(h, nl, ~0ull, s->stream);
                 if (r != CHT_OK) return r;
+                enqueued_before_engine = true;
                 ++s->prof.migrations;
                 ++st.rec.migrations;
             }
@@ -319,6 +323,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
         p.d_codes = rq.r.codes ? base + kb2 * (has_vals(rq.r.op) || rq.r.op == CHT_OP_FIND ? 2 : 1) : nullptr;
         if (cudaMemcpyAsync(p.d_keys, rq.r.keys + rq.admitted, m * 8, cudaMemcpyDefault, s->stream) != cudaSuccess)
             return CHT_ERR_CUDA;
+        enqueued_before_engine = true;
         if (p.d_vals &&
             cudaMemcpyAsync(p.d_vals, rq.r.vals + rq.admitted, m * 8, cudaMemcpyDefault, s->stream) != cudaSuccess)
             return CHT_ERR_CUDA;
@@ -361,12 +366,11 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
         batches[i].mode = u32(rq.r.op);
     }
     // work items sized per table from its chain of dependent requests; if
-    // that needs more metadata than a step of 256-operation items may use,
-    // take 256-operation items
+    // that needs more metadata than a step may use, take 64-operation items
     std::vector<cht::EngineChunk> chunks;
     u64 n_queue = cht::plan_order(batches, nt, 0, chunks);
     if (chunks.size() > s->max_step_items) {
-        n_queue = cht::plan_order(batches, nt, int(cht::kChunkOps), chunks);
+        n_queue = cht::plan_order(batches, nt, 64, chunks);
         st.rec.recut = 1;
     }
     std::vector<u32> touched;
@@ -385,7 +389,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
     // their counts is gathered on the device after the engine and read back
     // with one copy.
     const u64 b_tabs = nt * sizeof(cht::EngineTable), b_bat = batches.size() * sizeof(cht::EngineBatch);
-    const u64 b_chk = chunks.size() * sizeof(cht::EngineChunk), b_cnt = (2 + nt) * sizeof(unsigned long long);
+    const u64 b_chk = chunks.size() * sizeof(cht::EngineChunk), b_cnt = (3 + nt) * sizeof(unsigned long long);
     const u64 b_tch = touched.size() * sizeof(u32), b_snap = touched.size() * 16;
     const u64 o_bat = (b_tabs + 255) & ~255ull, o_chk = o_bat + ((b_bat + 255) & ~255ull);
     const u64 o_cnt = o_chk + ((b_chk + 255) & ~255ull), o_tch = o_cnt + ((b_cnt + 255) & ~255ull);
@@ -415,7 +419,16 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
     e.any_reuse = 0;
     for (const cht::EngineTable& et : tabs) e.any_reuse |= int(et.flags & cht::kTabReuse);
     e.inject_stall = 0;
-    if (cudaEventRecord(st.t_eng0, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
+    // the engine's last warp writes the touched tables' counts straight into
+    // the step's pinned snapshot (no separate kernel or copy)
+    st.snap = reinterpret_cast<unsigned long long*>(hm + o_snap);
+    e.snap_tables = reinterpret_cast<const u32*>(dm + o_tch);
+    e.n_snap = u32(touched.size());
+    e.snap_out = st.snap;
+    e.warps_done = e.done + nt + 1;
+    // nothing before the engine in this step: its start is the step's start
+    st.eng_from_begin = !enqueued_before_engine;
+    if (!st.eng_from_begin && cudaEventRecord(st.t_eng0, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
     if (cht::launch_engine(e, 1, 2, 0, true, s->stream) != cudaSuccess) {
         cudaGetLastError();
         return CHT_ERR_CUDA;
@@ -446,15 +459,6 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
             cudaMemcpyAsync(rq.r.codes + p.off, p.d_codes, p.n, cudaMemcpyDefault, s->stream) != cudaSuccess)
             return CHT_ERR_CUDA;
     }
-    st.snap = reinterpret_cast<unsigned long long*>(hm + o_snap);
-    if (cht::launch_snapshot(reinterpret_cast<const cht::EngineTable*>(dm), reinterpret_cast<const u32*>(dm + o_tch),
-                             u32(touched.size()), reinterpret_cast<unsigned long long*>(dm + o_snap),
-                             s->stream) != cudaSuccess) {
-        cudaGetLastError();
-        return CHT_ERR_CUDA;
-    }
-    if (cudaMemcpyAsync(st.snap, dm + o_snap, b_snap, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
-        return CHT_ERR_CUDA;
     if (!s->spare_events.empty()) {
         st.ev = s->spare_events.back();
         s->spare_events.pop_back();
@@ -536,7 +540,9 @@ cht_status cht_server_create(const cht_handle* tables, uint32_t n_tables, const 
     for (size_t t = 0; t < nt && r == CHT_OK; ++t) r = cht::table_read_counts(s->tables[t], &s->known_I[t], &s->known_D[t], s->stream);
     // metadata rings: room for several steps of the largest size (twice
     // over, so a step also fits when the free space is split at the ring end)
-    s->max_step_items = s->cfg.max_step_ops / cht::kChunkOps + s->cfg.max_step_requests;
+    // work items: room for items of 64 operations on average (the per-table
+    // sizing cuts long chains finer than 256)
+    s->max_step_items = s->cfg.max_step_ops / 64 + s->cfg.max_step_requests;
     s->meta_bytes = (s->max_step_items + s->cfg.max_step_requests + 1) * 48 +
                     nt * (sizeof(cht::EngineTable) + 40) + (1u << 20);
     s->meta_bytes *= 2 * (s->cfg.max_inflight_steps + 1);
