@@ -85,6 +85,7 @@ struct Step {
     // launch start / end; the step ends at `ev`
     cudaEvent_t t_begin = nullptr, t_eng0 = nullptr, t_eng1 = nullptr;
     bool eng_from_begin = false;  // no migration or copy ran before the engine: t_eng0 not recorded
+    cudaEvent_t up = nullptr;     // the step's metadata upload (on the upload stream) is done
     u64 arena_end = 0, meta_end = 0, dmeta_end = 0;
     std::vector<u32> touched;
     std::vector<u64> new_cells;          // per touched table
@@ -114,6 +115,7 @@ u64 per_op_bytes(const cht_request& r) {
 struct cht_server {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t ustream = nullptr;  // uploads of step metadata, overlapping the running step
     std::vector<cht_table*> tables;
     cht_server_config cfg{};
     unsigned char* arena = nullptr;  // device: request data
@@ -131,6 +133,7 @@ struct cht_server {
     std::vector<u32> parts_inflight;
     std::vector<cudaEvent_t> spare_events;
     std::vector<cudaEvent_t> spare_timers;
+    std::vector<cudaEvent_t> spare_sync;  // upload-done events (no timing)
     u64 steps = 0, completed = 0;
     cht_server_profile prof{};
     std::vector<cht_server_step_record> trace;  // one record per completed step
@@ -189,6 +192,7 @@ cht_status poll(cht_server* s, u32* completed_now) {
         s->spare_timers.push_back(st.t_begin);
         s->spare_timers.push_back(st.t_eng0);
         s->spare_timers.push_back(st.t_eng1);
+        if (st.up) s->spare_sync.push_back(st.up);
         s->inflight.pop_front();
     }
     if (completed_now) *completed_now = done;
@@ -404,8 +408,21 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
     memcpy(hm + o_chk, chunks.data(), b_chk);
     memset(hm + o_cnt, 0, b_cnt);
     memcpy(hm + o_tch, touched.data(), b_tch);
-    if (cudaMemcpyAsync(dm, hm, o_tch + b_tch, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+    // the upload runs on its own stream, so it overlaps the step still running
+    // on the main stream; the engine launch waits for it
+    if (!s->spare_sync.empty()) {
+        st.up = s->spare_sync.back();
+        s->spare_sync.pop_back();
+    } else if (cudaEventCreateWithFlags(&st.up, cudaEventDisableTiming) != cudaSuccess) {
+        st.up = nullptr;
         return CHT_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(dm, hm, o_tch + b_tch, cudaMemcpyHostToDevice, s->ustream) != cudaSuccess ||
+        cudaEventRecord(st.up, s->ustream) != cudaSuccess || cudaStreamWaitEvent(s->stream, st.up, 0) != cudaSuccess) {
+        s->spare_sync.push_back(st.up);
+        st.up = nullptr;
+        return CHT_ERR_CUDA;
+    }
     cht::EngineArgs e;
     e.tables = reinterpret_cast<const cht::EngineTable*>(dm);
     e.batches = reinterpret_cast<const cht::EngineBatch*>(dm + o_bat);
@@ -529,6 +546,13 @@ cht_status cht_server_create(const cht_handle* tables, uint32_t n_tables, const 
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != s->device) cudaSetDevice(s->device);
+    if (cudaStreamCreateWithFlags(&s->ustream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        s->ustream = nullptr;
+        if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+        delete s;
+        return CHT_ERR_CUDA;
+    }
     int pageable = 0;
     if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, s->device) != cudaSuccess) {
         cudaGetLastError();
@@ -669,11 +693,14 @@ cht_status cht_server_get_trace(cht_server_handle s, cht_server_step_record* out
 cht_status cht_server_destroy(cht_server_handle s) {
     if (!s) return CHT_ERR_INVALID_ARG;
     if (s->stream || !s->inflight.empty()) cudaStreamSynchronize(s->stream);
+    if (s->ustream) cudaStreamSynchronize(s->ustream);
     for (Step& st : s->inflight)
-        for (cudaEvent_t e : {st.ev, st.t_begin, st.t_eng0, st.t_eng1})
+        for (cudaEvent_t e : {st.ev, st.t_begin, st.t_eng0, st.t_eng1, st.up})
             if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
     for (cudaEvent_t e : s->spare_timers) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->spare_sync) cudaEventDestroy(e);
+    if (s->ustream) cudaStreamDestroy(s->ustream);
     if (s->arena) cht::runtime_free(s->arena, s->cfg.arena_bytes, s->stream);
     if (s->dmeta) cht::runtime_free(s->dmeta, s->meta_bytes, s->stream);
     if (s->meta) cudaFreeHost(s->meta);
