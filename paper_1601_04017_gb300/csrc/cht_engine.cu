@@ -71,37 +71,54 @@ __device__ __forceinline__ void red_release_add(unsigned long long* p, u64 v) {
 constexpr u32 kStageWarpBytes = kChunkOps * (8 + 8 + 1);
 static_assert(kStageWarpBytes % 8 == 0, "warp areas stay 8-byte aligned");
 
-template <int G, int V, int MODE, bool kStaged, bool kReuse>
+template <int G, int V, int MODE, bool kStaged, int F>
 __device__ __forceinline__ void engine_window(const OpArgs& a, u64 first, u64 end, u64& n_ins, u64& n_del,
                                               u32& sbits, const WarpStage& sg) {
-    warp_ops<G, V, MODE, true, kStaged, kReuse>(a, first, end, n_ins, n_del, sbits, sg);
+    warp_ops<G, V, MODE, true, kStaged, F>(a, first, end, n_ins, n_del, sbits, sg);
 }
 
-// kReuse: the launch holds tables with tombstone reuse; their insert modes
-// take the reuse variant of the probe loop, everything else the plain one.
-template <int G, int V, bool kStaged, bool kReuse>
+// kEF: the flag variants (tombstone reuse, full key space) some table of the
+// launch needs; each item takes the variant of its own table.
+template <int G, int V, int MODE, bool kStaged, int kEF>
+__device__ __forceinline__ void engine_mode(const OpArgs& a, u64 first, u64 end, u64& n_ins, u64& n_del,
+                                            u32& sbits, const WarpStage& sg) {
+    if constexpr (kEF == 0) {
+        engine_window<G, V, MODE, kStaged, 0>(a, first, end, n_ins, n_del, sbits, sg);
+    } else {
+        constexpr bool fills = mode_fills(MODE);
+        const int f = ((kEF & kFlagReuse) && fills && a.reuse ? kFlagReuse : 0) |
+                      ((kEF & kFlagFullKeys) && a.full_keys ? kFlagFullKeys : 0);
+        if (f == 0) {
+            engine_window<G, V, MODE, kStaged, 0>(a, first, end, n_ins, n_del, sbits, sg);
+        } else if (f == kFlagReuse) {
+            if constexpr ((kEF & kFlagReuse) && fills)
+                engine_window<G, V, MODE, kStaged, kFlagReuse>(a, first, end, n_ins, n_del, sbits, sg);
+        } else if (f == kFlagFullKeys) {
+            if constexpr ((kEF & kFlagFullKeys) != 0)
+                engine_window<G, V, MODE, kStaged, kFlagFullKeys>(a, first, end, n_ins, n_del, sbits, sg);
+        } else {
+            if constexpr ((kEF & kFlagReuse) && (kEF & kFlagFullKeys) && fills)
+                engine_window<G, V, MODE, kStaged, kFlagReuse | kFlagFullKeys>(a, first, end, n_ins, n_del, sbits,
+                                                                              sg);
+        }
+    }
+}
+
+template <int G, int V, bool kStaged, int kEF>
 __device__ __forceinline__ void engine_run(int mode, const OpArgs& a, u64 first, u64 end, u64& n_ins,
                                            u64& n_del, u32& sbits, const WarpStage& sg) {
-    const bool re = kReuse && a.reuse;
     switch (mode) {
-        case kFind: engine_window<G, V, kFind, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg); break;
-        case kInsert:
-            if (re) engine_window<G, V, kInsert, kStaged, true>(a, first, end, n_ins, n_del, sbits, sg);
-            else engine_window<G, V, kInsert, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg);
-            break;
-        case kIouAdd:
-            if (re) engine_window<G, V, kIouAdd, kStaged, true>(a, first, end, n_ins, n_del, sbits, sg);
-            else engine_window<G, V, kIouAdd, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg);
-            break;
+        case kFind: engine_mode<G, V, kFind, kStaged, kEF>(a, first, end, n_ins, n_del, sbits, sg); break;
+        case kInsert: engine_mode<G, V, kInsert, kStaged, kEF>(a, first, end, n_ins, n_del, sbits, sg); break;
+        case kIouAdd: engine_mode<G, V, kIouAdd, kStaged, kEF>(a, first, end, n_ins, n_del, sbits, sg); break;
         case kIouOverwrite:
-            if (re) engine_window<G, V, kIouOverwrite, kStaged, true>(a, first, end, n_ins, n_del, sbits, sg);
-            else engine_window<G, V, kIouOverwrite, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg);
+            engine_mode<G, V, kIouOverwrite, kStaged, kEF>(a, first, end, n_ins, n_del, sbits, sg);
             break;
-        case kUpdAdd: engine_window<G, V, kUpdAdd, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg); break;
+        case kUpdAdd: engine_mode<G, V, kUpdAdd, kStaged, kEF>(a, first, end, n_ins, n_del, sbits, sg); break;
         case kUpdOverwrite:
-            engine_window<G, V, kUpdOverwrite, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg);
+            engine_mode<G, V, kUpdOverwrite, kStaged, kEF>(a, first, end, n_ins, n_del, sbits, sg);
             break;
-        default: engine_window<G, V, kErase, kStaged, false>(a, first, end, n_ins, n_del, sbits, sg); break;
+        default: engine_mode<G, V, kErase, kStaged, kEF>(a, first, end, n_ins, n_del, sbits, sg); break;
     }
 }
 
@@ -119,7 +136,7 @@ __device__ __forceinline__ void stage_in(const EngineChunk& ch, const EngineBatc
 // it in its group done for its table; with 0 (an item inside a group) the
 // next item of the group, run by this same warp, only needs this warp's
 // lanes to agree on memory order, which __syncwarp gives.
-template <int G, int V, bool kStaged, bool kReuse>
+template <int G, int V, bool kStaged, int kEF>
 __device__ __forceinline__ void run_item(const EngineArgs& e, const EngineChunk& ch, const EngineBatch& b,
                                          const EngineTable& t, WarpStage& sg, int lane, u32 count) {
     OpArgs a;
@@ -138,9 +155,9 @@ __device__ __forceinline__ void run_item(const EngineArgs& e, const EngineChunk&
     u32 sbits = 0;
     if (kStaged) {
         sg.base = ch.start;
-        engine_run<G, V, true, kReuse>(b.mode, a, ch.start, end, n_ins, n_del, sbits, sg);
+        engine_run<G, V, true, kEF>(b.mode, a, ch.start, end, n_ins, n_del, sbits, sg);
     } else {
-        engine_run<G, V, false, kReuse>(b.mode, a, ch.start, end, n_ins, n_del, sbits, sg);
+        engine_run<G, V, false, kEF>(b.mode, a, ch.start, end, n_ins, n_del, sbits, sg);
     }
     // Count the items done as soon as the table writes are ordered: the
     // results (found values, codes -- possibly in host memory) and the
@@ -159,7 +176,7 @@ __device__ __forceinline__ void run_item(const EngineArgs& e, const EngineChunk&
     __syncwarp();  // the next item overwrites this one's staging area
 }
 
-template <int G, int V, bool kStaged, bool kReuse>
+template <int G, int V, bool kStaged, int kEF>
 __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
     constexpr u32 FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char engine_smem[];
@@ -212,7 +229,7 @@ __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
         }
         fence_acq_rel_gpu();  // lane 0: table reads after the count it saw ...
         __syncwarp();         // ... and the other lanes' reads after lane 0's fence
-        run_item<G, V, kStaged, kReuse>(e, ch, b, t, sg, lane, ch.nfollow ? 0u : 1u);
+        run_item<G, V, kStaged, kEF>(e, ch, b, t, sg, lane, ch.nfollow ? 0u : 1u);
         // the group this item leads: later levels of the same table, in
         // order; the whole group is counted done by its last item
         for (u32 f = 0; f < ch.nfollow; ++f) {
@@ -222,7 +239,7 @@ __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
                 stage_in(fc, fb, sg, lane);
                 __syncwarp();
             }
-            run_item<G, V, kStaged, kReuse>(e, fc, fb, t, sg, lane, f + 1 == ch.nfollow ? ch.nfollow + 1u : 0u);
+            run_item<G, V, kStaged, kEF>(e, fc, fb, t, sg, lane, f + 1 == ch.nfollow ? ch.nfollow + 1u : 0u);
         }
     }
     if (e.n_snap) {
@@ -247,14 +264,14 @@ __global__ void __launch_bounds__(kOpBlock) engine_kernel(EngineArgs e) {
     }
 }
 
-template <int G, int V, bool kStaged, bool kReuse = false>
+template <int G, int V, bool kStaged, int kEF = 0>
 cudaError_t launch_engine_gvs(const EngineArgs& e, int ctas_per_sm, cudaStream_t s) {
     const u32 smem = kStaged ? (kOpBlock / 32) * kStageWarpBytes : 0;
     static std::atomic<int> occ{0};
     int per_sm = occ.load(std::memory_order_relaxed);
     if (per_sm == 0) {
         cudaError_t err =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel<G, V, kStaged, kReuse>, kOpBlock, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel<G, V, kStaged, kEF>, kOpBlock, smem);
         if (err != cudaSuccess) return err;
         if (per_sm < 1) per_sm = 1;
         occ.store(per_sm, std::memory_order_relaxed);
@@ -265,7 +282,7 @@ cudaError_t launch_engine_gvs(const EngineArgs& e, int ctas_per_sm, cudaStream_t
     const u64 need = (e.n_chunks + kOpBlock / 32 - 1) / (kOpBlock / 32);
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    engine_kernel<G, V, kStaged, kReuse><<<unsigned(grid), kOpBlock, smem, s>>>(e);
+    engine_kernel<G, V, kStaged, kEF><<<unsigned(grid), kOpBlock, smem, s>>>(e);
     count_launch();
     return cudaGetLastError();
 }
@@ -281,12 +298,22 @@ cudaError_t launch_engine_gv(const EngineArgs& e, bool staged, int ctas_per_sm, 
 cudaError_t launch_engine(const EngineArgs& e, int group_width, int lane_cells, int ctas_per_sm, bool staged,
                           cudaStream_t s) {
     if (e.n_chunks == 0) return cudaSuccess;
-    if (e.any_reuse) {
-        // tables with tombstone reuse: staged I/O and the automatic windows
-        // (1, 4 or 8 lanes of one sector), the nearest to the configured one
-        if (group_width <= 2) return launch_engine_gvs<1, 2, true, true>(e, ctas_per_sm, s);
-        if (group_width == 4) return launch_engine_gvs<4, 2, true, true>(e, ctas_per_sm, s);
-        return launch_engine_gvs<8, 2, true, true>(e, ctas_per_sm, s);
+    const int ef = (e.any_reuse ? kFlagReuse : 0) | (e.any_full ? kFlagFullKeys : 0);
+    if (ef) {
+        // tables with tombstone reuse or the full key space: staged I/O and
+        // 1 or 4 lanes of one sector, the nearest to the configured window
+        const bool wide = group_width >= 4;
+        switch (ef) {
+            case kFlagReuse:
+                return wide ? launch_engine_gvs<4, 2, true, kFlagReuse>(e, ctas_per_sm, s)
+                            : launch_engine_gvs<1, 2, true, kFlagReuse>(e, ctas_per_sm, s);
+            case kFlagFullKeys:
+                return wide ? launch_engine_gvs<4, 2, true, kFlagFullKeys>(e, ctas_per_sm, s)
+                            : launch_engine_gvs<1, 2, true, kFlagFullKeys>(e, ctas_per_sm, s);
+            default:
+                return wide ? launch_engine_gvs<4, 2, true, kFlagReuse | kFlagFullKeys>(e, ctas_per_sm, s)
+                            : launch_engine_gvs<1, 2, true, kFlagReuse | kFlagFullKeys>(e, ctas_per_sm, s);
+        }
     }
     if (lane_cells == 2) {
         switch (group_width) {

@@ -114,6 +114,7 @@ struct EngineArgs {
     long long spin_limit;      // bound of one dependency wait, in clock cycles
     unsigned max_backoff_ns;   // longest sleep between two polls of a dependency counter
     int any_reuse;             // some table of the launch reuses tombstones
+    int any_full;              // some table of the launch has the full key space
     // optional snapshot at the end of the launch: the last warp to finish
     // writes I, D of tables[snap_tables[i]] to snap_out[2i], snap_out[2i + 1]
     // (n_snap = 0: none); warps_done: a counter, zero before the launch

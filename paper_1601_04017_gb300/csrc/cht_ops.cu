@@ -22,13 +22,14 @@ cudaError_t launch_pdl(K kernel, unsigned grid, unsigned block, size_t smem, cud
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
-template <int G, int V, int MODE, bool kReuse = false>
+
+template <int G, int V, int MODE, int kFlags = 0>
 cudaError_t launch_one(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     static std::atomic<int> occ{0};
     int per_sm = occ.load(std::memory_order_relaxed);
     if (per_sm == 0) {
         cudaError_t e =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, op_kernel<G, V, MODE, kReuse>, kOpBlock, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, op_kernel<G, V, MODE, kFlags>, kOpBlock, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         occ.store(per_sm, std::memory_order_relaxed);
@@ -38,27 +39,43 @@ cudaError_t launch_one(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     const u64 need = (a.n + kOpBlock - 1) / kOpBlock;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    const cudaError_t e = launch_pdl(op_kernel<G, V, MODE, kReuse>, unsigned(grid), kOpBlock, 0, s, a);
+    const cudaError_t e = launch_pdl(op_kernel<G, V, MODE, kFlags>, unsigned(grid), kOpBlock, 0, s, a);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// Tombstone reuse (insert modes of a table that has it on): kernels exist for
-// the automatic windows only -- 1, 4 or 8 lanes of one 32-byte sector; any
-// other configured window takes the one of these with the nearest width.
+// Tables with tombstone reuse or the full key space: kernels exist for the
+// automatic windows only -- 1 lane x 1 sector, 2 lanes x 2 sectors, 4 lanes x
+// 1 or 2 sectors; any other configured window takes the nearest of these.
+template <int MODE, int F>
+cudaError_t launch_window(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStream_t s) {
+    if (g <= 1) return launch_one<1, 2, MODE, F>(a, ctas_per_sm, s);
+    if (g == 2) return launch_one<2, 4, MODE, F>(a, ctas_per_sm, s);
+    if (g == 4 && v != 4) return launch_one<4, 2, MODE, F>(a, ctas_per_sm, s);
+    return launch_one<4, 4, MODE, F>(a, ctas_per_sm, s);
+}
+
 template <int MODE>
-cudaError_t launch_reuse(const OpArgs& a, int g, int ctas_per_sm, cudaStream_t s) {
-    if (g <= 2) return launch_one<1, 2, MODE, true>(a, ctas_per_sm, s);
-    if (g == 4) return launch_one<4, 2, MODE, true>(a, ctas_per_sm, s);
-    return launch_one<8, 2, MODE, true>(a, ctas_per_sm, s);
+cudaError_t launch_flagged(const OpArgs& a, int g, int v, int flags, int ctas_per_sm, cudaStream_t s) {
+    constexpr bool fills = mode_fills(MODE);
+    switch (flags) {
+        case kFlagReuse:
+            if constexpr (fills) return launch_window<MODE, kFlagReuse>(a, g, v, ctas_per_sm, s);
+            break;
+        case kFlagFullKeys: return launch_window<MODE, kFlagFullKeys>(a, g, v, ctas_per_sm, s);
+        case kFlagReuse | kFlagFullKeys:
+            if constexpr (fills) return launch_window<MODE, kFlagReuse | kFlagFullKeys>(a, g, v, ctas_per_sm, s);
+            break;
+        default: break;
+    }
+    return cudaErrorInvalidValue;
 }
 
 // (group width G, cells per lane V): G = 1 always loads a whole sector.
 template <int MODE>
 cudaError_t launch_mode(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStream_t s) {
-    if constexpr (MODE == kInsert || MODE == kIouAdd || MODE == kIouOverwrite) {
-        if (a.reuse) return launch_reuse<MODE>(a, g, ctas_per_sm, s);
-    }
+    const int flags = ((mode_fills(MODE) && a.reuse) ? kFlagReuse : 0) | (a.full_keys ? kFlagFullKeys : 0);
+    if (flags) return launch_flagged<MODE>(a, g, v, flags, ctas_per_sm, s);
     if (v == 4) {
         switch (g) {
             case 1: return launch_one<1, 4, MODE>(a, ctas_per_sm, s);

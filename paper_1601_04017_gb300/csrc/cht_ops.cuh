@@ -185,7 +185,12 @@ __device__ __forceinline__ void op_vout(const OpArgs& a, const WarpStage& sg, u6
     else a.vals_out[idx] = v;
 }
 
-template <int G, int V, int MODE, bool kCoherent = false, bool kStaged = false, bool kReuse = false>
+// kFlags: bit 0 = tombstone reuse (insert modes), bit 1 = full key space;
+// compile-time, so a table without them runs the plain probe loop.
+constexpr int kFlagReuse = 1;
+constexpr int kFlagFullKeys = 2;
+
+template <int G, int V, int MODE, bool kCoherent = false, bool kStaged = false, int kFlags = 0>
 __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 end, u64& n_ins, u64& n_del,
                                          u32& sbits, const WarpStage& sg = WarpStage{}) {
     constexpr u32 W = G * V;
@@ -208,7 +213,8 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
     u64 idx = 0, key = 0, d = 0, pos = 0, probed = 0;
     // tombstone reuse: tdist = 1 + the distance from the current key's home
     // to the first tombstone on its path (0: none yet)
-    constexpr bool reuse = kInsLike && kReuse;
+    constexpr bool reuse = kInsLike && (kFlags & kFlagReuse) != 0;
+    constexpr bool kFullKeys = (kFlags & kFlagFullKeys) != 0;  // (kFull is the status bit)
     u64 tdist = 0;
 
     // Unstaged: the warp's next 64 keys (and values) are held in registers,
@@ -252,7 +258,7 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                     if (kHasVals) d = kStaged ? op_val<kStaged>(a, sg, idx) : wv;
                     if (is_reserved(key)) {
                         if (gl == 0) {
-                            if (a.full_keys) {
+                            if (kFullKeys) {
                                 u64 v = 0;
                                 op_code<kStaged>(a, sg, idx, special_op<MODE>(a.st, key, d, &v));
                                 if (MODE == kFind) op_vout<kStaged>(a, sg, idx, v);
@@ -261,7 +267,7 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                                 if (MODE == kFind) op_vout<kStaged>(a, sg, idx, 0);
                             }
                         }
-                        if (!a.full_keys) sbits |= kReserved;
+                        if (!kFullKeys) sbits |= kReserved;
                     } else {
                         fresh = true;
                         active = true;
@@ -502,7 +508,7 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-template <int G, int V, int MODE, bool kReuse>
+template <int G, int V, int MODE, int kFlags>
 __global__ void __launch_bounds__(kOpBlock, op_min_blocks<G, V>()) op_kernel(OpArgs a) {
     pdl_enter();
     // each warp owns a contiguous slice of the batch
@@ -513,7 +519,7 @@ __global__ void __launch_bounds__(kOpBlock, op_min_blocks<G, V>()) op_kernel(OpA
     const u64 end = begin + per < a.n ? begin + per : a.n;
     u64 n_ins = 0, n_del = 0;
     u32 sbits = 0;
-    warp_ops<G, V, MODE, false, false, kReuse>(a, begin, end, n_ins, n_del, sbits);
+    warp_ops<G, V, MODE, false, false, kFlags>(a, begin, end, n_ins, n_del, sbits);
     warp_flush_counters(a.st, n_ins, n_del, sbits);
 }
 

@@ -968,7 +968,11 @@ cht::EngineArgs plan_args(const cht_plan* p) {
     e.inject_stall = p->cfg.fault_inject & 1;
     e.max_backoff_ns = p->cfg.poll_ns > 0 ? unsigned(p->cfg.poll_ns) : 8192u;
     e.any_reuse = 0;
-    for (const cht_table* h : p->tables) e.any_reuse |= h->cfg.reuse_tombstones;
+    e.any_full = 0;
+    for (const cht_table* h : p->tables) {
+        e.any_reuse |= h->cfg.reuse_tombstones;
+        e.any_full |= h->cfg.full_key_space;
+    }
     e.snap_tables = nullptr;
     e.n_snap = 0;
     e.snap_out = nullptr;

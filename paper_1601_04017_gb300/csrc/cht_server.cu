@@ -434,7 +434,11 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
     e.spin_limit = 2000000000ll;
     e.max_backoff_ns = 8192;
     e.any_reuse = 0;
-    for (const cht::EngineTable& et : tabs) e.any_reuse |= int(et.flags & cht::kTabReuse);
+    e.any_full = 0;
+    for (const cht::EngineTable& et : tabs) {
+        e.any_reuse |= int(et.flags & cht::kTabReuse);
+        e.any_full |= int((et.flags & cht::kTabFullKeys) != 0);
+    }
     e.inject_stall = 0;
     // the engine's last warp writes the touched tables' counts straight into
     // the step's pinned snapshot (no separate kernel or copy)
