@@ -72,7 +72,7 @@ def insert_probe_cells(a0: float, a1: float) -> float:
 
 
 def algorithmic_bytes(kind: str, **kw) -> float:
-    """Bytes one operation must move to or from HBM (SURVEY-style formula):
+    """Bytes one operation must move to or from HBM (32-byte sectors):
     its input/output streams plus the 32-byte sectors its probe touches
     (plus one dirty sector written back for an insert)."""
     if kind == "find_hit":
