@@ -682,6 +682,35 @@ def run_case(args):
         t = cht.Table(c)
         out["iou_ms"] = tm(lambda: t.insert_or_update(z, ones, cht.ADD, codes))
         t.destroy()
+    elif args.case == "window":
+        # Sliding window on a growable table (the paper's E7): 2^24 live keys;
+        # 2^27 / 2^20 rounds, each inserting the next 2^20 keys of the stream
+        # and erasing the 2^20 inserted 2^24 keys earlier.  Migrations purge
+        # the tombstones (gamma = 1) or grow the table (gamma = 2) as the
+        # policy decides.  Reported: operations/s and insert+erase pairs/s.
+        win, batch = 1 << 24, 1 << 20
+        rounds = args.window_rounds
+        keys = W.uniform_keys(win + batch * rounds, backend="cuda")
+        t = cht.Table(1 << GROW_LOG2C0, growable=True)
+        codes = torch.empty(batch, dtype=torch.uint8, device="cuda")
+        t.insert(keys[:win], keys[:win])
+        torch.cuda.synchronize()
+        mig0 = t.size()[2]
+
+        def run():
+            for r in range(rounds):
+                ins = keys[win + r * batch: win + (r + 1) * batch]
+                t.insert(ins, ins, codes)
+                t.erase(keys[r * batch: (r + 1) * batch], codes)
+
+        ms = tm(run)
+        live, ne, cap = t.size(check=True)
+        assert live == win
+        out.update({"rounds": rounds, "window": win, "batch": batch, "ms": ms,
+                    "mops": round(2 * batch * rounds / (ms * 1e-3) / 1e6, 1),
+                    "pairs_per_s_M": round(batch * rounds / (ms * 1e-3) / 1e6, 1),
+                    "capacity_before": mig0, "capacity_after": cap, "nonempty_after": ne})
+        t.destroy()
     elif args.case == "grow":
         keys = W.uniform_keys(c // 2, backend="cuda")
         vals = W.values_for(keys, backend="cuda")
@@ -1025,7 +1054,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-reps", type=int, default=100)
-    ap.add_argument("--case", choices=["find", "insert", "migrate", "shrink", "iou", "grow", "contention"],
+    ap.add_argument("--window-rounds", type=int, default=128,
+                    help="sliding-window case: rounds of 2^20 inserts + 2^20 erases (128 = 2^27 of each)")
+    ap.add_argument("--case", choices=["find", "insert", "migrate", "shrink", "iou", "grow", "contention", "window"],
                     help="run one small single-operation case (for profiling) instead of the benchmark")
     ap.add_argument("--case-log2c", type=int, default=26)
     ap.add_argument("--case-load", type=float, default=0.9)
