@@ -12,7 +12,7 @@ typedef unsigned long long u64;
 typedef unsigned int u32;
 
 // One table cell: <key, value>, 16-byte aligned so a 2-word CAS covers it
-// (Sec. 3: "128-bit aligned cells", 2-word CAS on key and value together).
+// (Sec. 3: cells aligned to 16 bytes, one double-word CAS on key and value).
 struct __align__(16) Cell {
     u64 key;
     u64 val;

@@ -46,10 +46,12 @@ cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, bool warp_dedup, i
 // (2^dst_log2 cells, dst_log2 >= src_log2).  dst needs no initialisation:
 // every target cell is written.  `st` receives the new I (it must be zero
 // on entry) and mig_fail.  tile: source cells per warp task (power of two,
-// 0 = default); border: device scratch of migrate_border_count() u64.
+// 0 = default); windows: place cells 32 at a time per warp (long clusters)
+// instead of one cluster per lane; border: device scratch of
+// migrate_border_count() u64.
 u64 migrate_border_count(u32 src_log2, int tile);
 cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log2, DevState* st,
-                           int tile, u64* border, cudaStream_t s);
+                           int tile, bool windows, u64* border, cudaStream_t s);
 
 // Shrinking migration (Sec. 4.3.1 "Shrinking") of `src` into `dst` (2^dst_log2
 // cells, dst_log2 < src_log2, more cells than live elements; no

@@ -10,22 +10,25 @@
 // integer-gamma form of the lemma's bound), so the owned target ranges of
 // different tiles are disjoint and together cover the target table: no
 // atomics on the table and no separate initialisation -- each tile writes
-// every cell of its range, empties included (the paper's "each thread is
-// responsible for initializing all cells in its region").  Each cluster is
-// re-inserted by one thread in source index order, so the layout equals the
+// every cell of its range, empties included (Sec. 4.3.1: the target is
+// initialised by the same threads that fill it, region by region).  A tile's
+// live cells are re-inserted in source index order, so the layout equals the
 // sequential migration (Lemma 1).
 //
 // GB300 mapping.  A border kernel computes m(d) for every tile once (a short
 // forward scan per tile).  In the migration kernel every warp then works on
 // its own tiles with no block-wide barrier, so a long cluster only delays
-// its own warp: lanes find the cluster starts of the tile (ballots), then
-// each lane walks one cluster, re-inserting its live cells in order.  The
-// occupancy of the warp's owned target range is a bitmap in shared memory
-// (lanes own disjoint target ranges, so a lane only ever claims its own
-// cells).  For owned ranges of up to 2048 cells (nearly all at load 0.5) a
-// lane records which source cell went to each target cell, and the warp then
-// writes the whole range in one coalesced pass -- every 32-byte sector once
-// and whole; longer ranges store elements directly and zero-fill the rest.
+// its own warp.  The warp reads its source range coalesced, 32 cells per
+// window with the next 64 in flight, and re-inserts the window's live cells
+// in source order: all lanes look up the first free target cell at or after
+// their new home at once, and rounds of warp votes settle lanes that picked
+// the same cell (place_window), so the layout is the sequential one.  The
+// occupancy of the warp's owned target range is a bitmap in shared memory.
+// For owned ranges of up to 2048 cells (nearly all at loads up to 0.9 with
+// tiles of 512) the warp records which source cell went to each target
+// cell and then writes the whole range in one coalesced pass -- every
+// 32-byte sector once and whole; longer ranges store elements directly and
+// zero-fill the rest.
 // A border scan that finds no empty cell within kMaxScan cells (a full
 // table, or a cluster longer than that) sets mig_fail; a single-CTA fallback
 // kernel, always launched after the tile kernel, then redoes the whole
@@ -51,7 +54,7 @@ struct MigArgs {
     DevState* st;
     u64* border;     // m(d) of every tile (scratch, ntiles entries)
     u32 tile;        // T, power of two, <= c
-    u32 start_cap;   // per-warp capacity of the cluster-start list
+    u32 start_cap;   // per-warp capacity of the cluster-start list (walk kernel)
 };
 
 __device__ __forceinline__ u64 ld_key_nc(const Cell* p) {
@@ -89,12 +92,295 @@ __device__ __forceinline__ u64 warp_sum(u64 x) {
     return x;
 }
 
-__global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
+// Re-insertion of one window of 32 consecutive source cells (lane i holds
+// source offset off - lane + i) in source order, exactly as a sequential
+// migration would.  A live lane's candidate is the first free cell >= its new
+// home; lanes with the same candidate form a group, and the group's m-th lane
+// (in lane order) proposes the m-th free cell from the candidate on.  Taken in
+// lane order, a proposal is the sequential placement if no earlier lane
+// proposes the same cell: the cells from the lane's home to its candidate were
+// taken before the window, the first m free ones after it go to the group's
+// earlier lanes, and every earlier lane takes its own, different, proposal.
+// So each round commits every pending lane below the first lane whose
+// proposal repeats an earlier one (at least the lowest pending lane); the
+// others look again from their candidate.  Sets `fail` if an element found no
+// free cell in the owned range, which Lemma 1 rules out for a consistent
+// table (the caller then leaves the migration to the fallback).
+//
+// Owned ranges of up to 32768 cells: the range's occupancy bitmap `bm` is in
+// shared memory and offsets are 32-bit; MODE 0 records the source offset of
+// each placed cell in `map`, MODE 1 stores the cell directly.
+template <int MODE>
+__device__ __forceinline__ void place_window_smem(u32* bm, unsigned short* map, Cell* dst, u64 tbase, u64 nmask,
+                                                  u32 tl, u32 dshift, u64 k, u64 v, bool valid, u32 off, int lane,
+                                                  u32& moved, bool& fail) {
+    const bool live = valid && !is_reserved(k);
+    u32 loc = 0;
+    if (live) {
+        const u64 o = (home_of(k, dshift) - tbase) & nmask;
+        if (o < tl) loc = u32(o);
+        else fail = true;  // outside the owned range: inconsistent source
+    }
+    u32 pending = __ballot_sync(0xffffffffu, live && !fail);
+    const u32 below = (1u << lane) - 1u;
+    const u32 wend = (tl + 31) >> 5;
+    const volatile u32* vbm = bm;
+    while (pending) {
+        const bool mine = (pending >> lane) & 1u;
+        // candidate: the first free cell >= loc (loc < tl for every lane)
+        u32 w = loc >> 5;
+        u32 bits = ~vbm[w] & (~0u << (loc & 31));
+        if (mine)
+            while (bits == 0 && ++w < wend) bits = ~vbm[w];
+        const u32 c = bits ? (w << 5) + u32(__ffs(bits) - 1) : tl;
+        // sentinels (bit 31 set) never match a real cell offset (< 2^15)
+        const u32 cand = mine ? c : (0x80000000u | u32(lane));
+        const u32 m = __popc(__match_any_sync(0xffffffffu, cand) & below);
+        u32 prop = cand;
+        if (mine && m != 0u && c < tl) {
+            // the m-th free cell after c: drop c, then skip m - 1 free cells
+            u32 r = m;
+            bits &= bits - 1u;
+            for (;;) {
+                const u32 cnt = __popc(bits);
+                if (r <= cnt) {
+                    for (; r > 1u; --r) bits &= bits - 1u;
+                    prop = (w << 5) + u32(__ffs(bits) - 1);
+                    break;
+                }
+                r -= cnt;
+                if (++w >= wend) {
+                    prop = tl;
+                    break;
+                }
+                bits = ~vbm[w];
+            }
+        }
+        // (every lane takes part in both votes: neither sits behind a branch)
+        const u32 psame = __match_any_sync(0xffffffffu, prop);
+        const u32 dups = __ballot_sync(0xffffffffu, mine && (psame & below) != 0u);
+        const u32 commit = pending & ((dups & (0u - dups)) - 1u);  // all pending lanes if dups == 0
+        if ((commit >> lane) & 1u) {
+            if (prop < tl) {
+                atomicOr(&bm[prop >> 5], 1u << (prop & 31));
+                if (MODE == 0) {
+                    map[prop] = (unsigned short)off;
+                } else {
+                    Cell cl;
+                    cl.key = k;
+                    cl.val = v;
+                    dst[(tbase + prop) & nmask] = cl;
+                }
+                ++moved;
+            } else {
+                fail = true;
+            }
+        }
+        if (mine && c < tl) loc = c;
+        pending &= ~commit;
+        __syncwarp();
+    }
+}
+
+// The same for owned ranges beyond the shared bitmap (a table grown by a
+// large factor, or clusters of tens of thousands of cells): the target cells
+// themselves, read from L2, are the occupancy, and offsets are 64-bit.
+__device__ __forceinline__ void place_window_global(Cell* dst, u64 tbase, u64 nmask, u64 tl, u32 dshift, u64 k,
+                                                    u64 v, bool valid, int lane, u64& moved, bool& fail) {
+    const bool live = valid && !is_reserved(k);
+    u64 loc = live ? ((home_of(k, dshift) - tbase) & nmask) : 0;
+    if (live && loc >= tl) fail = true;
+    u32 pending = __ballot_sync(0xffffffffu, live && !fail);
+    const u32 below = (1u << lane) - 1u;
+    while (pending) {
+        const bool mine = (pending >> lane) & 1u;
+        u64 cand = ~0ull - u64(lane);  // never a real candidate: those are < tl
+        if (mine) {
+            for (; loc < tl; ++loc) {
+                u64 tk, tv;
+                ld_cell_cg(dst + ((tbase + loc) & nmask), tk, tv);
+                if (tk == kEmpty) break;
+            }
+            cand = loc;
+        }
+        const u32 same = __match_any_sync(0xffffffffu, cand);
+        const u32 dups = __ballot_sync(0xffffffffu, mine && (same & below) != 0u);
+        const u32 commit = pending & ((dups & (0u - dups)) - 1u);
+        if ((commit >> lane) & 1u) {
+            if (cand < tl) {
+                Cell cl;
+                cl.key = k;
+                cl.val = v;
+                dst[(tbase + cand) & nmask] = cl;
+                ++moved;
+            } else {
+                fail = true;
+            }
+        }
+        pending &= ~commit;
+        __syncwarp();
+    }
+}
+
+// The placement pass of one tile: source cells [m0, m0 + L) in order, 64 per
+// step (two windows), the next 64 loading while these are placed.  MODE 0
+// needs only the keys here (the write pass gathers whole cells).
+template <int MODE>
+__device__ __forceinline__ bool place_range(const MigArgs& a, u32* bm, unsigned short* map, u64 m0, u64 L,
+                                            u64 tbase, u64 tl, int lane, u64& moved) {
+    const u64 cmask = (1ull << a.slog2) - 1, nmask = (1ull << a.dlog2) - 1;
+    const u32 dshift = 64u - a.dlog2;
+    bool fail = false;
+    u64 k0 = 0, v0 = 0, k1 = 0, v1 = 0;
+    auto load = [&](u64 j, u64& k, u64& v) {
+        if (j < L) {
+            if (MODE == 0) k = ld_key_nc(a.src + ((m0 + j) & cmask));
+            else ld_cell_nc(a.src + ((m0 + j) & cmask), k, v);
+        }
+    };
+    load(lane, k0, v0);
+    load(32 + lane, k1, v1);
+    for (u64 j = 0; j < L; j += 64) {
+        u64 n0 = 0, w0 = 0, n1 = 0, w1 = 0;
+        load(j + 64 + lane, n0, w0);
+        load(j + 96 + lane, n1, w1);
+        if (MODE < 2) {
+            u32 mv = 0;
+            place_window_smem<MODE>(bm, map, a.dst, tbase, nmask, u32(tl), dshift, k0, v0, j + lane < L,
+                                    u32(j + lane), lane, mv, fail);
+            place_window_smem<MODE>(bm, map, a.dst, tbase, nmask, u32(tl), dshift, k1, v1, j + 32 + lane < L,
+                                    u32(j + 32 + lane), lane, mv, fail);
+            moved += mv;
+        } else {
+            place_window_global(a.dst, tbase, nmask, tl, dshift, k0, v0, j + lane < L, lane, moved, fail);
+            place_window_global(a.dst, tbase, nmask, tl, dshift, k1, v1, j + 32 + lane < L, lane, moved, fail);
+        }
+        if (__any_sync(0xffffffffu, fail)) return true;
+        k0 = n0;
+        v0 = w0;
+        k1 = n1;
+        v1 = w1;
+    }
+    return false;
+}
+
+// The part of a tile that every migration kernel shares: its source range
+// [m0, m0 + L) of whole clusters, its owned target range [tbase, tbase + tl)
+// and how that range is written (0: source-offset map, 1: shared bitmap and
+// direct stores, 2: global probing).  False if the tile owns nothing.
+struct Tile {
+    u64 m0, L, tl, tbase, sl;  // sl: cells of [m0, d + T) where clusters can start
+    int mode;
+};
+
+__device__ __forceinline__ bool tile_of(const MigArgs& a, u64 t, u64 ntiles, Tile& x) {
+    const u64 c = 1ull << a.slog2;
+    const u64 m0 = a.border[t];
+    const u64 b1 = t + 1 < ntiles ? a.border[t + 1] : a.border[0];
+    if (m0 == kNoBorder || b1 == kNoBorder) return false;  // fallback redoes everything
+    const u64 m1 = t + 1 < ntiles ? b1 : b1 + c;
+    if (m1 <= m0) return false;  // the tile lies inside a cluster owned by an earlier tile
+    const u32 g = a.dlog2 - a.slog2;
+    const u64 dT = (t + 1) * u64(a.tile);
+    x.m0 = m0;
+    x.L = m1 - m0;
+    x.tl = x.L << g;
+    x.tbase = m0 << g;
+    x.sl = (m1 < dT ? m1 : dT) - m0;
+    x.mode = x.tl <= kMapCells ? 0 : (x.tl <= u64(kRegionWords) * 32 ? 1 : 2);
+    return true;
+}
+
+// Clears the owned range's bitmap (modes 0, 1) or zero-fills its target
+// cells (mode 2) before placement.
+__device__ __forceinline__ void clear_owned(const MigArgs& a, const Tile& x, u32* bm, int lane) {
+    const u64 nmask = (1ull << a.dlog2) - 1;
+    if (x.mode < 2) {
+        const u32 words = u32((x.tl + 31) / 32);
+        for (u32 w = lane; w < words; w += 32) bm[w] = 0;
+    } else {
+        const Cell zero = {0ull, 0ull};
+        for (u64 k = lane; k < x.tl; k += 32) a.dst[(x.tbase + k) & nmask] = zero;
+    }
+    __syncwarp();
+}
+
+// Writes the owned target range after placement: mode 0 every cell once
+// (placed cells gathered from the source through the map, four gathers in
+// flight per lane, the rest zero), mode 1 the zero cells.
+__device__ __forceinline__ void write_owned(const MigArgs& a, const Tile& x, const u32* bm,
+                                            const unsigned short* map, int lane) {
+    const u64 cmask = (1ull << a.slog2) - 1, nmask = (1ull << a.dlog2) - 1;
+    const Cell zero = {0ull, 0ull};
+    __syncwarp();
+    if (x.mode == 0) {
+        const u32 tl = u32(x.tl);
+        for (u32 k0 = 0; k0 < tl; k0 += 128) {
+            Cell cl[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const u32 k = k0 + u * 32 + lane;
+                cl[u] = zero;
+                if (k < tl && ((bm[k >> 5] >> (k & 31)) & 1u))
+                    ld_cell_nc(a.src + ((x.m0 + map[k]) & cmask), cl[u].key, cl[u].val);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const u32 k = k0 + u * 32 + lane;
+                if (k < tl) a.dst[(x.tbase + k) & nmask] = cl[u];
+            }
+        }
+    } else if (x.mode == 1) {
+        for (u64 k = lane; k < x.tl; k += 32)
+            if (!((bm[k >> 5] >> (k & 31)) & 1u)) a.dst[(x.tbase + k) & nmask] = zero;
+    }
+    __syncwarp();
+}
+
+// Migration by windows (tables at load >= 0.6, where clusters are long): the
+// warp places the tile's cells 32 at a time in source order (place_range).
+__global__ void __launch_bounds__(kMigBlock, 5) migrate_window_kernel(MigArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // per warp: a region of kRegionWords words (the source-offset map of a
-    // short owned range, or the occupancy bitmap of a long one), the small
-    // bitmap of the map mode, and the cluster-start list
+    // short owned range, or the occupancy bitmap of a long one) and the
+    // small bitmap of the map mode
+    u32* const region = reinterpret_cast<u32*>(smem) + wib * (kRegionWords + kSmallBitWords);
+    unsigned short* const map = reinterpret_cast<unsigned short*>(region);
+    u32* const small_bm = region + kRegionWords;
+    const u64 ntiles = (1ull << a.slog2) / a.tile;
+    const u64 nwarps = u64(gridDim.x) * kMigWarps;
+    u64 moved = 0;
+    bool bad = false;
+    for (u64 t = u64(blockIdx.x) * kMigWarps + wib; t < ntiles && !bad; t += nwarps) {
+        Tile x;
+        if (!tile_of(a, t, ntiles, x)) continue;
+        u32* const bm = x.mode == 0 ? small_bm : region;
+        clear_owned(a, x, bm, lane);
+        if (x.mode == 0)
+            bad = place_range<0>(a, bm, map, x.m0, x.L, x.tbase, x.tl, lane, moved);
+        else if (x.mode == 1)
+            bad = place_range<1>(a, bm, map, x.m0, x.L, x.tbase, x.tl, lane, moved);
+        else
+            bad = place_range<2>(a, bm, map, x.m0, x.L, x.tbase, x.tl, lane, moved);
+        if (bad) break;
+        write_owned(a, x, bm, map, lane);
+    }
+    if (bad && lane == 0) atomicOr(&a.st->mig_fail, 2u);
+    moved = warp_sum(moved);
+    if (lane == 0 && moved) atomicAdd(&a.st->I, moved);
+}
+
+// Migration by clusters (tables below load 0.6, where clusters are short and
+// many): each lane re-inserts whole clusters of the tile in source order.
+// The tile's keys are read with all loads in flight (eight 32-cell chunks at
+// a time) and the cluster starts -- a live cell after an empty one -- come
+// from ballots of the empties; the walks then read cells the scan has just
+// brought into L1.  Lanes own disjoint target ranges by Lemma 1, so a lane
+// only ever claims its own cells.
+__global__ void __launch_bounds__(kMigBlock, 5) migrate_walk_kernel(MigArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     u32* const region = reinterpret_cast<u32*>(smem) + wib * (kRegionWords + kSmallBitWords);
     unsigned short* const map = reinterpret_cast<unsigned short*>(region);
     u32* const small_bm = region + kRegionWords;
@@ -102,63 +388,56 @@ __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
         reinterpret_cast<unsigned short*>(reinterpret_cast<u32*>(smem) + kMigWarps * (kRegionWords + kSmallBitWords)) +
         wib * a.start_cap;
 
-    const u64 c = 1ull << a.slog2, cmask = c - 1;
-    const u64 nc = 1ull << a.dlog2, nmask = nc - 1;
-    const u32 g = a.dlog2 - a.slog2;
+    const u64 cmask = (1ull << a.slog2) - 1;
+    const u64 nmask = (1ull << a.dlog2) - 1;
     const u32 dshift = 64u - a.dlog2;
-    const u32 T = a.tile;
-    const u64 ntiles = c / T;
+    const u32 below = (1u << lane) - 1u;
+    const u64 ntiles = (1ull << a.slog2) / a.tile;
     const u64 nwarps = u64(gridDim.x) * kMigWarps;
     u64 moved = 0;
     int bad = 0;
-    const Cell zero = {0ull, 0ull};
 
     for (u64 t = u64(blockIdx.x) * kMigWarps + wib; t < ntiles; t += nwarps) {
-        const u64 d = t * T;
-        const u64 m0 = a.border[t];
-        const u64 b1 = t + 1 < ntiles ? a.border[t + 1] : a.border[0];
-        if (m0 == kNoBorder || b1 == kNoBorder) continue;  // fallback redoes everything
-        const u64 m1 = t + 1 < ntiles ? b1 : b1 + c;
-        if (m1 <= m0) continue;  // the tile lies inside a cluster owned by an earlier tile
-        const u64 L = m1 - m0;     // source cells of this tile's clusters
-        const u64 tl = L << g;     // owned target cells
-        const u64 tbase = m0 << g; // first owned target cell (unwrapped)
-        // map mode: placements recorded, target written in one full-cell pass;
-        // bitmap mode: direct stores plus a zero fill; else global probing
-        const int mode = tl <= kMapCells ? 0 : (tl <= u64(kRegionWords) * 32 ? 1 : 2);
-        u32* const bm = mode == 0 ? small_bm : region;
+        Tile x;
+        if (!tile_of(a, t, ntiles, x)) continue;
+        u32* const bm = x.mode == 0 ? small_bm : region;
+        clear_owned(a, x, bm, lane);
 
-        // ---- cluster starts in [m0, min(m1, d+T)): non-empty after an empty
-        const u64 sl = (m1 < d + T ? m1 : d + T) - m0;
-        u32 ns = 0;
-        for (u64 j0 = 0; j0 < sl; j0 += 32) {
-            const u64 j = j0 + lane;
-            bool st = false;
-            if (j < sl) {
-                const u64 k = ld_key_nc(a.src + ((m0 + j) & cmask));
-                st = k != kEmpty && (j == 0 || ld_key_nc(a.src + ((m0 + j - 1) & cmask)) == kEmpty);
+        // ---- cluster starts in [m0, m0 + sl); cell m0 - 1 is empty
+        u32 ns = 0, carry = 1u;
+        for (u64 j0 = 0; j0 < x.sl; j0 += 256) {
+            u64 key[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const u64 j = j0 + q * 32 + lane;
+                key[q] = j < x.sl ? ld_key_nc(a.src + ((x.m0 + j) & cmask)) : kEmpty;
             }
-            const u32 b = __ballot_sync(0xffffffffu, st);
-            if (st) starts[ns + __popc(b & ((1u << lane) - 1u))] = (unsigned short)j;
-            ns += __popc(b);
-        }
-        if (mode < 2) {
-            const u32 words = u32((tl + 31) / 32);
-            for (u32 w = lane; w < words; w += 32) bm[w] = 0;
-        } else {
-            for (u64 k = lane; k < tl; k += 32) a.dst[(tbase + k) & nmask] = zero;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (j0 + q * 32 >= x.sl) break;
+                const u32 e = __ballot_sync(0xffffffffu, key[q] == kEmpty);  // past sl counts as empty
+                const u32 st = ~e & ((e << 1) | carry);
+                carry = e >> 31;
+                if ((st >> lane) & 1u) starts[ns + __popc(st & below)] = (unsigned short)(j0 + q * 32 + lane);
+                ns += __popc(st);
+            }
         }
         __syncwarp();
 
         // ---- one lane per cluster: re-insert its live cells in index order
+        const u64 tl = x.tl, tbase = x.tbase;
         for (u32 q = lane; q < ns && !bad; q += 32) {
-            for (u64 i = m0 + starts[q];; ++i) {
+            for (u64 i = x.m0 + starts[q];; ++i) {
                 u64 k, v;
                 ld_cell_nc(a.src + (i & cmask), k, v);
                 if (k == kEmpty) break;
                 if (k == kTomb) continue;
                 u64 loc = (home_of(k, dshift) - tbase) & nmask;
-                if (mode < 2) {
+                if (loc >= tl) {
+                    bad = 1;
+                    break;
+                }
+                if (x.mode < 2) {
                     // first free bit >= loc (bits of other lanes' ranges are
                     // never in this cluster's window, so a plain read is safe)
                     u32 w = u32(loc >> 5);
@@ -173,8 +452,8 @@ __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
                         break;
                     }
                     atomicOr(&bm[w], 1u << (loc & 31));
-                    if (mode == 0) {
-                        map[loc] = (unsigned short)(i - m0);
+                    if (x.mode == 0) {
+                        map[loc] = (unsigned short)(i - x.m0);
                     } else {
                         Cell cl;
                         cl.key = k;
@@ -200,21 +479,13 @@ __global__ void __launch_bounds__(kMigBlock) migrate_kernel(MigArgs a) {
                 ++moved;
             }
         }
-        __syncwarp();
-        // ---- write the owned target range: every cell once
-        if (mode == 0) {
-            for (u64 k = lane; k < tl; k += 32) {
-                Cell cl = zero;
-                if ((bm[k >> 5] >> (k & 31)) & 1u) ld_cell_nc(a.src + ((m0 + map[k]) & cmask), cl.key, cl.val);
-                a.dst[(tbase + k) & nmask] = cl;
-            }
-        } else if (mode == 1) {
-            for (u64 k = lane; k < tl; k += 32)
-                if (!((bm[k >> 5] >> (k & 31)) & 1u)) a.dst[(tbase + k) & nmask] = zero;
+        if (__any_sync(0xffffffffu, bad)) {
+            bad = 1;
+            break;
         }
-        __syncwarp();
+        write_owned(a, x, bm, map, lane);
     }
-    if (bad) atomicOr(&a.st->mig_fail, 2u);
+    if (bad && lane == 0) atomicOr(&a.st->mig_fail, 2u);
     moved = warp_sum(moved);
     if (lane == 0 && moved) atomicAdd(&a.st->I, moved);
 }
@@ -464,7 +735,7 @@ u64 migrate_border_count(u32 src_log2, int tile) {
 }
 
 cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log2, DevState* st,
-                           int tile, u64* border, cudaStream_t s) {
+                           int tile, bool windows, u64* border, cudaStream_t s) {
     const u64 c = 1ull << src_log2;
     u32 T = tile > 0 ? u32(tile) : 256u;
     if (T > c) T = u32(c);
@@ -476,7 +747,7 @@ cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log
     a.st = st;
     a.border = border;
     a.tile = T;
-    a.start_cap = (T / 2 + 8 + 7) & ~7u;
+    a.start_cap = windows ? 0u : (T / 2 + 8 + 7) & ~7u;
     const u64 ntiles = c / T;
     u64 bgrid = (ntiles + 255) / 256;
     const u64 bcap = u64(sm_count()) * 8;
@@ -486,16 +757,21 @@ cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = size_t(kMigWarps) * ((kRegionWords + kSmallBitWords) * 4 + size_t(a.start_cap) * 2);
-    e = cudaFuncSetAttribute(migrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const void* fn = windows ? reinterpret_cast<const void*>(migrate_window_kernel)
+                             : reinterpret_cast<const void*>(migrate_walk_kernel);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, migrate_kernel, kMigBlock, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMigBlock, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     u64 grid = u64(sm_count()) * per_sm;
     const u64 need = (ntiles + kMigWarps - 1) / kMigWarps;
     if (grid > need) grid = need;
-    migrate_kernel<<<unsigned(grid), kMigBlock, smem, s>>>(a);
+    if (windows)
+        migrate_window_kernel<<<unsigned(grid), kMigBlock, smem, s>>>(a);
+    else
+        migrate_walk_kernel<<<unsigned(grid), kMigBlock, smem, s>>>(a);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -248,10 +248,12 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
     const u64 bytes = (1ull << new_log2) * sizeof(Cell);
     cht_status r = lib_alloc(reinterpret_cast<void**>(&dst), bytes, s);
     if (r != CHT_OK) return r;
-    // tile: short clusters (load below 0.6) want small tiles for parallelism,
-    // long ones want large tiles so few clusters straddle tile borders
+    // below load 0.6 (short clusters) one lane re-inserts each cluster, in
+    // small tiles for parallelism; above it (long clusters) the warp places
+    // 32 cells at a time, in large tiles so few clusters straddle tile borders
+    const bool windows = double(h->i_bound) >= 0.6 * double(h->cap());
     int tile = h->cfg.migrate_tile;
-    if (tile == 0) tile = double(h->i_bound) < 0.6 * double(h->cap()) ? 256 : 1024;
+    if (tile == 0) tile = windows ? 1024 : 256;
     // scratch: the moved border of every migration tile (growing), or the
     // spill list of c' cells plus its counter (shrinking)
     const u64 sbytes = shrink ? bytes + 256 : cht::migrate_border_count(h->log2c, tile) * sizeof(u64);
@@ -271,7 +273,8 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
             e = cht::launch_shrink(h->cells, h->log2c, dst, new_log2, h->st, reinterpret_cast<Cell*>(scratch),
                                    nspill, s);
     } else if (e == cudaSuccess) {
-        e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, tile, reinterpret_cast<u64*>(scratch), s);
+        e = cht::launch_migrate(h->cells, h->log2c, dst, new_log2, h->st, tile, windows,
+                                reinterpret_cast<u64*>(scratch), s);
     }
     lib_free(scratch, sbytes, s);
     if (e != cudaSuccess) {

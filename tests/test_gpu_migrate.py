@@ -3,9 +3,11 @@
 The migration's cell layout is deterministic given the source snapshot: the
 GPU's cluster-parallel result must equal, bit for bit, the oracle's
 sequential migration of the same snapshot.  Cases cover several tiles and
-one tile larger than the table, loads up to 0.95 (long clusters crossing tile
-borders), tombstones (gamma = 1 purge), gamma = 2 and 4, clusters wrapping
-past the last cell, and a completely full table (fallback path).
+one tile larger than the table, loads up to 0.99 (long clusters crossing tile
+borders), both placement kernels (one lane per cluster below load 0.6, 32-cell
+windows above) with each way of writing the target, tombstones (gamma = 1
+purge), gamma from 2 to 256, clusters wrapping past the last cell, and a
+completely full table (fallback path).
 """
 import numpy as np
 import pytest
@@ -46,6 +48,11 @@ def _fill(cuda_lib, oracle_mod, log2c, load, erase_frac, seed, wrap=0):
     (18, 0.7, 0.1, 1, 4096),
     (14, 0.5, 0.0, 4, 1024),     # gamma = 16
     (13, 0.5, 0.0, 8, 256),      # gamma = 256: owned ranges beyond the bitmap (global path)
+    (18, 0.9, 0.3, 1, 512),      # many windows whose lanes pick the same target cell
+    (16, 0.99, 0.0, 1, 512),     # clusters of thousands of cells: bitmap and global paths
+    (16, 0.55, 0.2, 1, 256),     # below load 0.6 (one lane per cluster) with tombstones
+    (14, 0.7, 0.0, 4, 1024),     # windows into a 16x larger table (shared bitmap path)
+    (13, 0.7, 0.0, 8, 256),      # windows into a 256x larger table (global path)
 ])
 def test_migration_layout_equals_sequential(cuda_lib, oracle_mod, log2c, load, erase, gamma_log2, tile):
     t, _ = _fill(cuda_lib, oracle_mod, log2c, load, erase, seed=log2c + gamma_log2, wrap=5)
