@@ -88,7 +88,7 @@ typedef enum {
  * G = 1, else 1); G = 32 allows only 1, G = 16 at most 2.  ctas_per_sm: resident CTAs per
  * SM for the operation kernels (0 = occupancy maximum).  migrate_tile:
  * source cells per migration warp task (power of two, 64..8192; 0 = by load:
- * 256 below load 0.6, else 1024).  alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).
+ * 512 below load 0.6, else 1024).  alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).
  * iou_aggregate: 1 (default) folds equal keys of each window of 1024
  * insertOrUpdate or update operations in shared memory first (one table
  * operation per distinct key and window); 2 also combines equal keys within

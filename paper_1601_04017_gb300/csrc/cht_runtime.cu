@@ -248,12 +248,12 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
     const u64 bytes = (1ull << new_log2) * sizeof(Cell);
     cht_status r = lib_alloc(reinterpret_cast<void**>(&dst), bytes, s);
     if (r != CHT_OK) return r;
-    // below load 0.6 (short clusters) one lane re-inserts each cluster, in
-    // small tiles for parallelism; above it (long clusters) the warp places
-    // 32 cells at a time, in large tiles so few clusters straddle tile borders
+    // below load 0.6 (short clusters) one lane re-inserts each cluster; above
+    // it (long clusters) the warp places 32 cells at a time.  Tiles of 512 and
+    // 1024 cells were the fastest of 256..2048 for each (2^28 cells, GB300).
     const bool windows = double(h->i_bound) >= 0.6 * double(h->cap());
     int tile = h->cfg.migrate_tile;
-    if (tile == 0) tile = windows ? 1024 : 256;
+    if (tile == 0) tile = windows ? 1024 : 512;
     // scratch: the moved border of every migration tile (growing), or the
     // spill list of c' cells plus its counter (shrinking)
     const u64 sbytes = shrink ? bytes + 256 : cht::migrate_border_count(h->log2c, tile) * sizeof(u64);
