@@ -63,6 +63,8 @@ def _load():
             "or_reset_probes": (None, [p]),
             "or_migrate": (ctypes.c_int, [p, u64]),
             "or_insert": (None, [p, p, p, u64, p]),
+            "or_build": (ctypes.c_int, [p, p, p, u64]),
+            "or_build_sort_bits": (ctypes.c_uint, [ctypes.c_uint]),
             "or_insert_or_update": (None, [p, p, p, u64, ctypes.c_int, p]),
             "or_update": (None, [p, p, p, u64, ctypes.c_int, p]),
             "or_find": (None, [p, p, u64, p, p]),
@@ -98,6 +100,11 @@ def hash64(keys) -> np.ndarray:
     out = np.zeros(k.size, dtype=np.uint64)
     lib.or_hash_many(_ptr(k), k.size, _ptr(out))
     return out
+
+
+def build_sort_bits(log2c: int) -> int:
+    """Hash bits the bulk build orders by in a table of 2^log2c cells."""
+    return int(_load().or_build_sort_bits(int(log2c)))
 
 
 def homes(keys, log2c: int) -> np.ndarray:
@@ -169,6 +176,16 @@ class OracleTable:
         f = np.zeros(k.size, dtype=np.uint8)
         self._lib.or_insert(self._t, _ptr(k), _ptr(v), k.size, _ptr(f))
         return f
+
+    def build(self, keys, vals) -> int:
+        """Sort-based bulk build into the empty table (Sec. 3 "Bulk Operations").
+
+        0 = built; 1 = built, reserved keys skipped; -1 = table not empty;
+        -2 = the distinct keys would leave no empty cell (table unchanged).
+        """
+        k, v = _u64(keys), _u64(vals)
+        assert k.shape == v.shape
+        return int(self._lib.or_build(self._t, _ptr(k), _ptr(v), k.size))
 
     def insert_or_update(self, keys, vals, op: int = ADD) -> np.ndarray:
         k, v = _u64(keys), _u64(vals)

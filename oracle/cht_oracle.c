@@ -314,6 +314,112 @@ void or_insert_or_update(or_table *t, const uint64_t *keys, const uint64_t *vals
     }
 }
 
+/* Sort-based bulk build (Sec. 3 "Bulk Operations"): building a table from a
+ * batch of n elements by sorting them by hash.  Reading taken here (the
+ * paper's text stops mid-sentence):
+ *   - the table must be empty (returns -1 otherwise); a growable table first
+ *     grows, empty, to the smallest power of two c' >= c with n <= floor(alpha
+ *     c'), since n bounds the number of distinct keys (Sec. 3: grow to an
+ *     upper bound of the new size first);
+ *   - the elements are ordered by the top B bits of their hash, B = 32 for
+ *     tables of up to 2^32 cells (else log2(c) rounded up to a multiple of 8),
+ *     ties in input order; B >= log2(c), so the order is also by home cell;
+ *   - among equal keys all but the last (in input order) are dropped (Sec. 3:
+ *     keep the last);
+ *   - the survivors are inserted one by one in that order, each at the first
+ *     empty cell from its home on (wrapping past the last cell); a sorted
+ *     insertion's free cell search can start at max(home, previous position),
+ *     which is what the paper's merge does;
+ *   - keys 0 and ~0 go to the special slots (last value wins) with the full
+ *     key space on, else they are skipped and the result is 1;
+ *   - if the survivors would leave no empty cell (a bounded table), nothing
+ *     is changed and the result is -2.
+ * Returns 0 on success, 1 on success with reserved keys skipped. */
+typedef struct {
+    uint64_t s;   /* top B hash bits */
+    uint64_t idx; /* input position */
+} or_sortkey;
+
+static int cmp_sortkey(const void *a, const void *b)
+{
+    const or_sortkey *x = (const or_sortkey *)a, *y = (const or_sortkey *)b;
+    if (x->s != y->s) return x->s < y->s ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+unsigned or_build_sort_bits(unsigned log2c) { return log2c <= 32 ? 32u : 8u * ((log2c + 7u) / 8u); }
+
+int or_build(or_table *t, const uint64_t *keys, const uint64_t *vals, uint64_t n)
+{
+    if (t->I != 0 || t->sp_present[0] || t->sp_present[1]) return -1;
+    if (t->growable) {
+        uint64_t nc = t->cap;
+        while (n > (uint64_t)(t->alpha * (double)nc)) nc <<= 1;
+        if (nc != t->cap) {
+            or_cell *cells = (or_cell *)calloc(nc, sizeof(or_cell));
+            if (!cells) return -1;
+            free(t->cells);
+            t->cells = cells;
+            t->cap = round_cap(nc, &t->log2c);
+        }
+    }
+    const unsigned B = or_build_sort_bits(t->log2c);
+    or_sortkey *v = (or_sortkey *)malloc((n ? n : 1) * sizeof(or_sortkey));
+    if (!v) return -1;
+    uint64_t m = 0;
+    int reserved = 0, sp_set[2] = {0, 0};
+    uint64_t sp_v[2] = {0, 0};
+    for (uint64_t i = 0; i < n; ++i) {
+        if (is_reserved(keys[i])) {
+            const int sl = keys[i] == OR_TOMB;
+            if (t->full_keys) {
+                sp_set[sl] = 1;
+                sp_v[sl] = vals[i];
+            } else {
+                reserved = 1;
+            }
+            continue;
+        }
+        v[m].s = or_hash(keys[i]) >> (64 - B);
+        v[m].idx = i;
+        ++m;
+    }
+    qsort(v, m, sizeof(or_sortkey), cmp_sortkey);
+    /* keep the last of equal keys: equal keys have equal hashes, so a later
+     * copy of v[a]'s key lies in v[a]'s run of equal sort keys */
+    uint64_t S = 0;
+    for (uint64_t a = 0; a < m; ++a) {
+        int later = 0;
+        for (uint64_t b = a + 1; b < m && v[b].s == v[a].s && !later; ++b)
+            later = keys[v[b].idx] == keys[v[a].idx];
+        if (!later) v[S++] = v[a];
+    }
+    if (S >= t->cap) {
+        free(v);
+        return -2;
+    }
+    const uint64_t mask = t->cap - 1;
+    for (uint64_t j = 0; j < S; ++j) {
+        const uint64_t k = keys[v[j].idx];
+        uint64_t p = home_of(k, t->log2c);
+        while (t->cells[p].key != OR_EMPTY) {
+            t->probes++;
+            p = (p + 1) & mask;
+        }
+        t->cells[p].key = k;
+        t->cells[p].val = vals[v[j].idx];
+    }
+    t->I = S;
+    t->D = 0;
+    for (int sl = 0; sl < 2; ++sl)
+        if (sp_set[sl]) {
+            t->sp_present[sl] = 1;
+            t->sp_val[sl] = sp_v[sl];
+        }
+    free(v);
+    return reserved;
+}
+
 /* update (Sec. 3 interface: update(x, d, up)): probe from home like find; at
  * the cell holding k set value <- up(value, d) (overwrite: d; add: value + d
  * mod 2^64) and report 1; reaching an empty cell (or seeing every cell)

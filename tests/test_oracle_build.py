@@ -1,0 +1,166 @@
+"""Pins of the oracle's sort-based bulk build (Sec. 3 "Bulk Operations").
+
+Independent facts used:
+* Dictionary meaning: after building from pairs with repeated keys, every key
+  maps to the value of its LAST occurrence (the paper keeps the last of equal
+  keys), and the live count is the number of distinct keys -- checked against a
+  Python dict.
+* A layout is a valid linear-probing table iff no empty cell lies between any
+  element's home and its cell (cyclically).
+* Characterisation of an insertion in sorted order: reading the table from
+  just after an empty cell, the elements appear in sort order (hash bits, then
+  input position), and every element sits at its home or right after another
+  element.  Together with validity these facts fix every position (the first
+  element of a run sits at its home, each next one at max(home, previous + 1)).
+* A worked example on 64 cells with keys chosen for their homes, where the
+  last home's elements wrap around to the front cells.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+TOMB = (1 << 64) - 1
+
+
+def _run_keys(cells):
+    """Keys in cell order, starting just after the first empty cell."""
+    c = cells.shape[0]
+    empties = np.nonzero(cells[:, 0] == 0)[0]
+    start = (int(empties[0]) + 1) % c
+    order = [(start + j) % c for j in range(c)]
+    return [(p, int(cells[p, 0])) for p in order if cells[p, 0] != 0]
+
+
+def _check_valid(cells, log2c, oracle_mod):
+    c = cells.shape[0]
+    keys = cells[:, 0]
+    live = np.nonzero(keys != 0)[0]
+    homes = oracle_mod.homes(keys[live], log2c).astype(np.int64)
+    for p, h in zip(live, homes):
+        q = int(h)
+        while q != p:
+            assert keys[q] != 0, f"empty cell {q} between home {h} and cell {p}"
+            q = (q + 1) % c
+
+
+def _dup_batch(n, distinct, seed):
+    rng = np.random.default_rng(seed)
+    base = W.uniform_keys(distinct, start=seed * 1000, seed=31)
+    keys = base[rng.integers(0, distinct, n)]
+    vals = rng.integers(1, 1 << 62, n).astype(np.uint64)
+    return keys, vals
+
+
+@pytest.mark.parametrize("log2c,n,distinct", [(8, 100, 60), (10, 600, 400), (12, 3500, 1500)])
+def test_build_is_the_dictionary_of_last_values(oracle_mod, log2c, n, distinct):
+    keys, vals = _dup_batch(n, distinct, seed=log2c)
+    t = oracle_mod.OracleTable(1 << log2c)
+    assert t.build(keys, vals) == 0
+    last = {}
+    for k, v in zip(keys.tolist(), vals.tolist()):
+        last[k] = v
+    assert t.live == t.nonempty == len(last)
+    q = np.array(list(last.keys()), dtype=np.uint64)
+    got, found = t.find(q)
+    assert found.all()
+    assert got.tolist() == [last[k] for k in q.tolist()]
+
+
+@pytest.mark.parametrize("log2c,load", [(8, 0.5), (10, 0.9), (12, 0.97)])
+def test_build_layout_is_sorted_insertion(oracle_mod, log2c, load):
+    c = 1 << log2c
+    keys, vals = _dup_batch(int(load * c * 1.3), int(load * c), seed=log2c + 7)
+    t = oracle_mod.OracleTable(c)
+    assert t.build(keys, vals) == 0
+    cells = t.cells()
+    _check_valid(cells, log2c, oracle_mod)
+    # sort order: top B hash bits, then the input position of the kept copy
+    B = oracle_mod.build_sort_bits(log2c)
+    assert B >= log2c
+    last_pos = {}
+    for i, k in enumerate(keys.tolist()):
+        last_pos[k] = i
+    run = _run_keys(cells)
+    ks = np.array([k for _, k in run], dtype=np.uint64)
+    sk = (oracle_mod.hash64(ks) >> np.uint64(64 - B)).tolist()
+    order = [(s, last_pos[k]) for s, k in zip(sk, ks.tolist())]
+    # cyclic: ascending with at most one descent (where the last homes wrapped)
+    descents = sum(1 for a, b in zip(order, order[1:]) if b < a)
+    if descents == 1:
+        cut = next(i for i, (a, b) in enumerate(zip(order, order[1:])) if b < a) + 1
+        order = order[cut:] + order[:cut]
+    assert order == sorted(order)
+    # compact: each element at its home or right after an occupied cell
+    homes = oracle_mod.homes(ks, log2c).tolist()
+    for (p, _), h in zip(run, homes):
+        assert p == h or cells[(p - 1) % c, 0] != 0
+
+
+def test_build_worked_example_wraps(oracle_mod):
+    # 64 cells; keys picked for their homes: a at home 0, b at home 1 and three
+    # keys x, y, z at home 63.  Sorted insertion puts a at 0, b at 1, the first
+    # of x, y, z (by hash) at 63 and the other two, wrapping, at 2 and 3.
+    cand = W.uniform_keys(20000, start=0, seed=5)
+    h = oracle_mod.homes(cand, 6)
+    a = cand[h == 0][0]
+    b = cand[h == 1][0]
+    xyz = cand[h == 63][:3]
+    keys = np.array([xyz[0], a, xyz[1], b, xyz[2]], dtype=np.uint64)
+    vals = np.arange(1, 6, dtype=np.uint64)
+    t = oracle_mod.OracleTable(64)
+    assert t.build(keys, vals) == 0
+    cells = t.cells()
+    B = oracle_mod.build_sort_bits(6)
+    s = (oracle_mod.hash64(xyz) >> np.uint64(64 - B)).tolist()
+    first, second, third = [xyz[i] for i in sorted(range(3), key=lambda i: (s[i], i))]
+    assert cells[0, 0] == a and cells[1, 0] == b
+    assert cells[63, 0] == first and cells[2, 0] == second and cells[3, 0] == third
+    assert (cells[4:63, 0] == 0).all()
+    assert cells[0, 1] == 2 and cells[1, 1] == 4
+
+
+def test_build_equals_inserting_survivors_in_order(oracle_mod):
+    log2c = 11
+    keys, vals = _dup_batch(1800, 1500, seed=3)
+    t = oracle_mod.OracleTable(1 << log2c)
+    assert t.build(keys, vals) == 0
+    B = oracle_mod.build_sort_bits(log2c)
+    last = {}
+    for i, (k, v) in enumerate(zip(keys.tolist(), vals.tolist())):
+        last[k] = (i, v)
+    ks = np.array(list(last.keys()), dtype=np.uint64)
+    s = (oracle_mod.hash64(ks) >> np.uint64(64 - B)).tolist()
+    order = sorted(range(len(ks)), key=lambda j: (s[j], last[int(ks[j])][0]))
+    u = oracle_mod.OracleTable(1 << log2c)
+    sk = ks[order]
+    u.insert(sk, np.array([last[int(k)][1] for k in sk], dtype=np.uint64))
+    assert np.array_equal(t.cells(), u.cells())
+
+
+def test_build_full_and_not_empty(oracle_mod):
+    ks = W.uniform_keys(64, start=0, seed=9)
+    t = oracle_mod.OracleTable(64)
+    assert t.build(ks, ks) == -2          # 64 distinct keys leave no empty cell
+    assert t.live == 0 and (t.cells() == 0).all()
+    assert t.build(ks[:63], ks[:63]) == 0  # 63 do
+    assert t.live == 63
+    assert t.build(ks[:1], ks[:1]) == -1  # not empty any more
+    g = oracle_mod.OracleTable(64, growable=True, alpha=0.5)
+    k2 = W.uniform_keys(100, start=500, seed=9)
+    assert g.build(k2, k2) == 0
+    assert g.capacity == 256 and g.live == 100  # 100 > 0.5 * 128, <= 0.5 * 256
+
+
+def test_build_reserved_keys(oracle_mod):
+    ks = W.uniform_keys(10, start=0, seed=4)
+    keys = np.concatenate([ks, np.array([0, TOMB, 0], dtype=np.uint64)])
+    vals = np.arange(1, keys.size + 1, dtype=np.uint64)
+    t = oracle_mod.OracleTable(64)
+    assert t.build(keys, vals) == 1
+    assert t.live == 10
+    f = oracle_mod.OracleTable(64, full_key_space=True)
+    assert f.build(keys, vals) == 0
+    assert f.live == 12
+    v, found = f.find(np.array([0, TOMB], dtype=np.uint64))
+    assert found.all() and v.tolist() == [13, 12]
