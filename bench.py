@@ -655,6 +655,44 @@ def run_case(args):
             out["shrink_x4_ms"] = tm(lambda: t.migrate(c // 4))
             out["shrink_src_cells_per_s"] = round(c / (out["shrink_x4_ms"] * 1e-3), 1)
         t.destroy()
+    elif args.case == "build":
+        # Sort-based bulk build (Sec. 3 "Bulk Operations") of the bench table's
+        # keys at the given load, against inserting the same keys one call
+        # (each into a cleared table; one untimed round first)
+        wl = W.bounded_workload(log2c, loads=(load,), n_find=1 << 20, backend="cuda")
+        n = wl["counts"][load]
+        k, v = wl["keys"][:n], wl["vals"][:n]
+        t = cht.Table(c)
+        for timed in (False, True):
+            t.clear()
+            ms_b = tm(lambda: t.build(k, v))
+            t.clear()
+            ms_i = tm(lambda: t.insert(k, v))
+            if timed:
+                out["build_ms"], out["insert_ms"] = ms_b, ms_i
+        t.clear()
+        t.build(k, v)
+        got = torch.empty(1 << 20, dtype=torch.int64, device="cuda")
+        fc = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+        t.find(wl["hits"][load], got, fc)
+        out["n"] = n
+        out["build_mops"] = round(n / (out["build_ms"] * 1e-3) / 1e6, 1)
+        out["sampled_finds_ok"] = bool((fc == 1).all().item()) and bool(
+            torch.equal(got, W.values_for(wl["hits"][load], backend="cuda")))
+        out["live"] = t.size()[0]
+        # batches with repeated keys (Zipf(s) over n/2 ranks): the build keeps
+        # the last value per key without contention; insertOrUpdate(overwrite)
+        # of the same batch is the per-operation way to the same key set
+        for s_ in (0.5, 1.0, 1.5):
+            z = W.zipf_keys(n, s_, n // 2, W.SEED_ZIPF, backend="cuda")
+            zv = torch.arange(1, n + 1, dtype=torch.int64, device="cuda")
+            for timed in (False, True):
+                t.clear()
+                mb = tm(lambda: t.build(z, zv))
+                t.clear()
+                mi = tm(lambda: t.insert_or_update(z, zv, cht.OVERWRITE))
+            out[f"zipf{s_}_build_ms"], out[f"zipf{s_}_iou_overwrite_ms"] = mb, mi
+        t.destroy()
     elif args.case == "contention":
         # Contended operations on a filled table (the paper's E4 overwrite and
         # E5 find under skew): N = c/4 rank keys are present (load 0.25);
@@ -1056,7 +1094,7 @@ def main():
     ap.add_argument("--latency-reps", type=int, default=100)
     ap.add_argument("--window-rounds", type=int, default=128,
                     help="sliding-window case: rounds of 2^20 inserts + 2^20 erases (128 = 2^27 of each)")
-    ap.add_argument("--case", choices=["find", "insert", "migrate", "shrink", "iou", "grow", "contention", "window"],
+    ap.add_argument("--case", choices=["find", "insert", "migrate", "shrink", "iou", "grow", "contention", "window", "build"],
                     help="run one small single-operation case (for profiling) instead of the benchmark")
     ap.add_argument("--case-log2c", type=int, default=26)
     ap.add_argument("--case-load", type=float, default=0.9)

@@ -140,6 +140,22 @@ cht_status cht_get_config(cht_handle h, cht_config *cfg);
 cht_status cht_insert(cht_handle h, const uint64_t *keys, const uint64_t *vals, uint64_t n,
                       uint8_t *inserted, cht_stream_t stream);
 
+/* Sort-based bulk build (Sec. 3 "Bulk Operations") of an EMPTY table (no
+ * insert since creation or the last cht_clear; else CHT_ERR_INVALID_ARG) from
+ * n < 2^32 pairs.  Of equal keys the last (in input order) is kept.  The
+ * pairs are ordered by the top B bits of the 64-bit hash (B = 32 for tables
+ * of up to 2^32 cells, else log2(c) rounded up to a multiple of 8), ties in
+ * input order, and placed as inserting them one by one in that order would
+ * place them; the layout is therefore deterministic.  A growable table first
+ * takes the smallest capacity >= c with n <= alpha * c'.  Keys 0 / ~0 go to
+ * the special slots with the full key space on, else they are skipped and
+ * set the RESERVED status bit.  CHT_ERR_TABLE_FULL, table unchanged, if the
+ * distinct keys would leave no empty cell (only possible for n >= c; the call
+ * then synchronizes `stream` once).  keys / vals: n u64 each, host or device;
+ * the scratch (about 32 B per pair) is freed stream-ordered. */
+cht_status cht_build(cht_handle h, const uint64_t *keys, const uint64_t *vals, uint64_t n,
+                     cht_stream_t stream);
+
 /* find (Sec. 3 "Lookup", copy semantics): vals_out[i] = the value stored
  * with keys[i], or 0 if absent; found[i] = 1 / 0 (3 for a reserved key).
  * Writes nothing to the table.  vals_out: n u64 (required); found: n u8 or NULL. */

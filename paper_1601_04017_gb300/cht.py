@@ -111,6 +111,7 @@ def load_library(build: bool = True):
             "cht_set_config": (i32, [p, ctypes.POINTER(ChtConfig)]),
             "cht_get_config": (i32, [p, ctypes.POINTER(ChtConfig)]),
             "cht_insert": (i32, [p, p, p, u64, p, p]),
+            "cht_build": (i32, [p, p, p, u64, p]),
             "cht_find": (i32, [p, p, u64, p, p, p]),
             "cht_insert_or_update": (i32, [p, p, p, u64, i32, p, p]),
             "cht_update": (i32, [p, p, p, u64, i32, p, p]),
@@ -255,6 +256,12 @@ class Table:
         cp, _, _ = _ptr(inserted, 1, n, "inserted")
         _check(self._lib.cht_insert(self._h, kp, vp, n, cp, _stream(stream)), "cht_insert")
         return inserted
+
+    def build(self, keys, vals, stream=None):
+        """Sort-based bulk build of this empty table (keeps the last of equal keys)."""
+        kp, n, _ = _ptr(keys, 8, what="keys")
+        vp, _, _ = _ptr(vals, 8, n, "vals")
+        _check(self._lib.cht_build(self._h, kp, vp, n, _stream(stream)), "cht_build")
 
     def find(self, keys, vals_out, found=None, stream=None):
         kp, n, _ = _ptr(keys, 8, what="keys")

@@ -60,6 +60,28 @@ cudaError_t launch_migrate(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log
 cudaError_t launch_shrink(const Cell* src, u32 src_log2, Cell* dst, u32 dst_log2, DevState* st, Cell* spill,
                           unsigned long long* nspill, cudaStream_t s);
 
+// Sort-based bulk build (Sec. 3 "Bulk Operations") into an empty table, in
+// three stream-ordered steps over one scratch block of build_scratch_bytes(n):
+// launch_build_sort sorts the batch's cells by the top build_sort_bits(log2c)
+// hash bits (stable) and routes keys 0 / ~0; launch_build_count counts the
+// survivors (the last copy of each key) into ex->S; launch_build_place writes
+// them into the zeroed cells, wraps the tail and sets I, D and the special
+// slots.  n < 2^32.
+struct BuildExtra {
+    u64 sp_last[2];  // 1 + input position of the last key 0 / ~0 (0: none)
+    u64 S;           // survivors
+    u64 first_ov;    // lowest rank placed past the last cell (~0: none)
+    u64 reserved;    // nonzero: a key 0 / ~0 was skipped (full key space off)
+};
+u32 build_sort_bits(u32 log2c);
+u64 build_scratch_bytes(u64 n);
+cudaError_t launch_build_sort(const u64* keys, const u64* vals, u64 n, u32 log2c, int full_keys, void* scratch,
+                              const Cell** sorted, BuildExtra** ex, cudaStream_t s);
+cudaError_t launch_build_count(const Cell* sorted, u64 n, u32 log2c, void* scratch, BuildExtra* ex,
+                               cudaStream_t s);
+cudaError_t launch_build_place(const Cell* sorted, u64 n, Cell* cells, u32 log2c, void* scratch, BuildExtra* ex,
+                               DevState* st, const u64* vals, cudaStream_t s);
+
 // Compact the live cells into keys_out / vals_out (max_n entries); the count
 // lands in st->export_pos, which must be zero on entry.
 cudaError_t launch_export(const Cell* cells, u32 log2c, u64* keys_out, u64* vals_out, u64 max_n,

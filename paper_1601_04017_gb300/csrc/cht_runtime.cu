@@ -748,6 +748,67 @@ cht_status cht_update(cht_handle h, const uint64_t* keys, const uint64_t* vals, 
     return r != CHT_OK ? r : f;
 }
 
+cht_status cht_build(cht_handle h, const uint64_t* keys, const uint64_t* vals, uint64_t n, cht_stream_t stream) {
+    if (!h || (n > 0 && (!keys || !vals)) || n >= (1ull << 32)) return CHT_ERR_INVALID_ARG;
+    if (h->i_bound != 0) return CHT_ERR_INVALID_ARG;  // not empty since creation or the last clear
+    if (n == 0) return CHT_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last = s;
+    Staging stg(s);
+    const void *dk, *dv;
+    cht_status r = stg.in(keys, n * 8, &dk);
+    if (r == CHT_OK) r = stg.in(vals, n * 8, &dv);
+    if (r != CHT_OK) return r;
+    // a growable table takes, empty, the capacity that holds n elements at
+    // alpha (n bounds the distinct keys); nothing to migrate
+    if (h->growable) {
+        u32 nl = h->log2c;
+        while (double(n) > h->cfg.alpha * double(1ull << nl)) ++nl;
+        if (nl != h->log2c) {
+            Cell* cells = nullptr;
+            const u64 bytes = (1ull << nl) * sizeof(Cell);
+            r = lib_alloc(reinterpret_cast<void**>(&cells), bytes, s);
+            if (r != CHT_OK) return r;
+            if (cudaMemsetAsync(cells, 0, bytes, s) != cudaSuccess) {
+                lib_free(cells, bytes, s);
+                return CHT_ERR_CUDA;
+            }
+            lib_free(h->cells, h->cap() * sizeof(Cell), s);
+            h->cells = cells;
+            h->log2c = nl;
+        }
+    }
+    const u64 sbytes = cht::build_scratch_bytes(n);
+    void* scratch = nullptr;
+    r = lib_alloc(&scratch, sbytes, s);
+    if (r != CHT_OK) return r;
+    const Cell* sorted = nullptr;
+    cht::BuildExtra* ex = nullptr;
+    cudaError_t e = cht::launch_build_sort(static_cast<const u64*>(dk), static_cast<const u64*>(dv), n, h->log2c,
+                                           h->cfg.full_key_space, scratch, &sorted, &ex, s);
+    if (e == cudaSuccess) e = cht::launch_build_count(sorted, n, h->log2c, scratch, ex, s);
+    if (e == cudaSuccess && n >= h->cap()) {
+        // only a batch of >= c elements can leave no empty cell: read the
+        // survivor count before touching the table
+        u64 S = 0;
+        e = cudaMemcpyAsync(&S, &ex->S, sizeof(u64), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && S >= h->cap()) {
+            lib_free(scratch, sbytes, s);
+            stg.finish();
+            return CHT_ERR_TABLE_FULL;
+        }
+    }
+    if (e == cudaSuccess)
+        e = cht::launch_build_place(sorted, n, h->cells, h->log2c, scratch, ex, h->st, static_cast<const u64*>(dv), s);
+    lib_free(scratch, sbytes, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    h->i_bound = n;
+    h->i_exact = false;
+    return stg.finish();
+}
+
 cht_status cht_find(cht_handle h, const uint64_t* keys, uint64_t n, uint64_t* vals_out, uint8_t* found,
                     cht_stream_t stream) {
     if (!h || (n > 0 && (!keys || !vals_out))) return CHT_ERR_INVALID_ARG;

@@ -1,0 +1,138 @@
+"""GPU parity of the sort-based bulk build (Sec. 3 "Bulk Operations").
+
+The build's layout is deterministic (pairs ordered by hash bits, ties in input
+order, the last of equal keys kept, placed as a sequential insertion in that
+order), so the GPU's cells must equal the oracle's bit for bit.  Cases cover a
+single pair, less than one radix tile, several tiles with a ragged tail, many
+placement chunks, heavy duplicates, a tail that wraps past the last cell, a
+growable table's sizing, a bounded table that would be full, keys 0 / ~0 with
+and without the full key space, host input arrays, and the empty-table rule.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import to_dev, to_np_u64
+
+pytestmark = pytest.mark.gpu
+
+TOMB = (1 << 64) - 1
+
+
+def _batch(n, distinct, seed):
+    rng = np.random.default_rng(seed)
+    base = W.uniform_keys(distinct, start=seed * 1_000_000, seed=41)
+    keys = base[rng.permutation(distinct)] if n == distinct else base[rng.integers(0, distinct, n)]
+    vals = rng.integers(1, 1 << 62, n).astype(np.uint64)
+    return np.ascontiguousarray(keys, dtype=np.uint64), vals
+
+
+def _both(cuda_lib, oracle_mod, c, keys, vals, **kw):
+    t = cuda_lib.Table(c, **kw)
+    t.build(to_dev(keys), to_dev(vals))
+    o = oracle_mod.OracleTable(c, **kw)
+    r = o.build(keys, vals)
+    return t, o, r
+
+
+@pytest.mark.parametrize("log2c,n,distinct", [
+    (10, 1, 1),             # a single pair
+    (12, 2000, 1500),       # less than one radix tile (2048), duplicates
+    (14, 9001, 7000),       # several tiles, ragged tail
+    (16, 59000, 58000),     # load 0.885: long runs
+    (16, 70000, 3000),      # each key about 23 times
+    (18, 200003, 200003),   # load 0.76, no duplicates, many placement chunks
+])
+def test_build_layout_equals_oracle(cuda_lib, oracle_mod, log2c, n, distinct):
+    keys, vals = _batch(n, distinct, seed=log2c + n % 97)
+    t, o, r = _both(cuda_lib, oracle_mod, 1 << log2c, keys, vals)
+    assert r == 0
+    assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), o.cells())
+    live, ne, cap = t.size(check=True)
+    assert live == ne == o.live and cap == 1 << log2c
+    import torch
+
+    q = to_dev(keys)
+    got = torch.empty_like(q)
+    t.find(q, got)
+    ov, _ = o.find(keys)
+    assert np.array_equal(to_np_u64(got), ov)
+
+
+def test_build_wraps_tail(cuda_lib, oracle_mod):
+    # 300 keys homed in the last 64 cells of a 4096-cell table: the sorted
+    # insertion runs past the last cell and wraps to the front
+    log2c = 12
+    cand = W.uniform_keys(200_000, start=0, seed=17)
+    h = oracle_mod.homes(cand, log2c)
+    tail = cand[h >= (1 << log2c) - 64][:300]
+    front = cand[h < 8][:10]
+    keys = np.concatenate([tail, front])
+    vals = np.arange(1, keys.size + 1, dtype=np.uint64)
+    t, o, r = _both(cuda_lib, oracle_mod, 1 << log2c, keys, vals)
+    assert r == 0
+    cells = o.cells()
+    assert cells[0, 0] != 0 and cells[(1 << log2c) - 1, 0] != 0
+    assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), cells)
+
+
+def test_build_growable_sizing(cuda_lib, oracle_mod):
+    keys, vals = _batch(5000, 4000, seed=8)
+    t, o, r = _both(cuda_lib, oracle_mod, 1024, keys, vals, growable=True)
+    assert r == 0
+    assert t.size()[2] == o.capacity == 16384  # 5000 <= 0.5 * 16384
+    assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), o.cells())
+
+
+def test_build_full_then_fits(cuda_lib, oracle_mod):
+    import paper_1601_04017_gb300 as cht
+
+    ks = W.uniform_keys(1024, start=0, seed=12)
+    t = cht.Table(1024)
+    with pytest.raises(cht.ChtError) as ei:
+        t.build(to_dev(ks), to_dev(ks))     # 1024 distinct keys leave no empty cell
+    assert ei.value.status == cht.CHT_ERR_TABLE_FULL
+    assert t.size()[0] == 0 and (to_np_u64(t.cells()) == 0).all()
+    t.build(to_dev(ks[:1023]), to_dev(ks[:1023]))
+    o = oracle_mod.OracleTable(1024)
+    assert o.build(ks[:1023], ks[:1023]) == 0
+    assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), o.cells())
+    with pytest.raises(cht.ChtError) as ei:
+        t.build(to_dev(ks[:1]), to_dev(ks[:1]))  # not empty any more
+    assert ei.value.status == cht.CHT_ERR_INVALID_ARG
+    t.clear()
+    t.build(to_dev(ks[:10]), to_dev(ks[:10]))    # empty again after clear
+    assert t.size()[0] == 10
+
+
+@pytest.mark.parametrize("full", [False, True])
+def test_build_reserved_keys(cuda_lib, oracle_mod, full):
+    keys, vals = _batch(3000, 2500, seed=6)
+    keys = keys.copy()
+    keys[[5, 700, 2999]] = [0, TOMB, 0]
+    t = cuda_lib.Table(4096)
+    t.set_config(full_key_space=int(full))
+    t.build(to_dev(keys), to_dev(vals))
+    o = oracle_mod.OracleTable(4096, full_key_space=full)
+    assert o.build(keys, vals) == (0 if full else 1)
+    assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), o.cells())
+    assert t.size()[0] == o.live
+    assert bool(t.status() & 2) == (not full)
+    if full:
+        import torch
+
+        q = to_dev(np.array([0, TOMB], dtype=np.uint64))
+        got = torch.empty_like(q)
+        t.find(q, got)
+        assert to_np_u64(got).tolist() == [int(vals[2999]), int(vals[700])]
+
+
+def test_build_from_host_arrays_and_empty_batch(cuda_lib, oracle_mod):
+    keys, vals = _batch(30000, 20000, seed=3)
+    t = cuda_lib.Table(1 << 16)
+    t.build(keys[:0], vals[:0])
+    assert t.size()[0] == 0
+    t.build(keys, vals)                      # numpy: staged through the library
+    o = oracle_mod.OracleTable(1 << 16)
+    assert o.build(keys, vals) == 0
+    assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), o.cells())
