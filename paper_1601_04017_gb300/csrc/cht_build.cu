@@ -18,8 +18,8 @@
 //      (count, max) pairs under (C1, M1) + (C2, M2) = (C1 + C2,
 //      max(M1, M2 - C1)) gives every position at once.  One pass reduces
 //      chunks of 2048 cells (8 consecutive ones per thread), one CTA scans the
-//      chunk totals, one pass writes the cells (positions rise with i, so the
-//      writes of a chunk cover one stretch of the table).
+//      chunk totals, one pass writes the cells (positions rise with i: a
+//      chunk's survivors are staged by rank and stored by consecutive threads).
 //   3. One thread places the survivors whose position passed the last cell
 //      (the tail of the sorted order) at the first empty cells from 0, in
 //      order, and sets the counters and special slots.
@@ -292,12 +292,15 @@ __device__ __forceinline__ Agg block_incl_agg(Agg x, Agg& total, u32* shc, long 
 }
 
 struct PlaceArgs {
-    const Cell* srt;  // sorted cells
+    const Cell* srt;       // sorted cells
     u64 n;
     u32 B, log2c;
-    Agg* parts;       // per chunk: its join (reduce pass), then its exclusive prefix
-    Cell* cells;      // the table
-    Cell* ov;         // survivors past the last cell, by rank
+    Agg* parts;            // per chunk: its join (count passes), then its exclusive prefix
+    unsigned char* flags;  // per sorted cell: 1 survivor, 0 not, 2 deferred
+    u32* deferred;         // cells whose survivor test was deferred (count in ex->n_deferred)
+    unsigned char* dirty;  // per chunk: a deferred cell of it turned out to survive
+    Cell* cells;           // the table
+    Cell* ov;              // survivors past the last cell, by rank
     BuildExtra* ex;
 };
 
@@ -307,29 +310,43 @@ __device__ __forceinline__ u64 ld_key(const Cell* p) {
     return k;
 }
 
-// Whether a cell from j on, still in the run of sort key s, holds key k (the
-// rare case of two different keys sharing the top B hash bits in between).
-__device__ __noinline__ bool later_in_run(const PlaceArgs& a, u64 j, u64 k, u64 s) {
-    for (; j < a.n; ++j) {
+constexpr int kRunScan = 32;  // cells a survivor test looks ahead before deferring
+
+// Survivor test, first try.  A cell survives if its key is not reserved and
+// no later cell of the same sort key (equal keys have equal hashes, so their
+// copies share that run) holds the same key.  Nearly always the next cell
+// decides; when a different key with the same top B hash bits sits between
+// (a run mixing keys), up to kRunScan cells are looked at, after which the
+// test is deferred (2) to a CTA of its own (build_resolve_kernel), so that a
+// rare key inside a long run of copies of another key costs no long scan by
+// one thread.
+__device__ __forceinline__ unsigned char survivor_first(const PlaceArgs& a, u64 i, u64 k, u64 kn) {
+    if (is_reserved(k)) return 0;
+    if (i + 1 >= a.n) return 1;
+    const u64 s = sort_key(k, a.B);
+    if (sort_key(kn, a.B) != s) return 1;
+    if (kn == k) return 0;
+    for (u64 j = i + 2; j < a.n && j < i + 2 + kRunScan; ++j) {
         const u64 kj = ld_key(a.srt + j);
-        if (sort_key(kj, a.B) != s) return false;
-        if (kj == k) return true;
+        if (sort_key(kj, a.B) != s) return 1;
+        if (kj == k) return 0;
     }
-    return false;
+    return i + 2 + kRunScan >= a.n ? 1 : 2;
 }
 
-// Each thread takes kPlaceItems consecutive sorted cells.  Survivor: not a
-// reserved key, and no later cell of the same sort key (equal keys have equal
-// hashes, so their copies share that run) holds it -- nearly always decided
-// by the next cell.  The reduce pass (kWrite false) stores each chunk's join;
-// the write pass turns the chunk's exclusive prefix plus the thread's
-// exclusive prefix into ranks and positions.
-template <bool kWrite>
+// Count passes (MODE 0: decide survivors and write the flags; MODE 1: only
+// for chunks where a deferred cell survived, recount from the flags) and the
+// write pass
+// (MODE 2).  Each thread takes kPlaceItems consecutive sorted cells.  The
+// count passes store each chunk's join; the write pass turns the chunk's
+// exclusive prefix plus the thread's into ranks and positions.
+template <int MODE>
 __global__ void __launch_bounds__(256) build_place_kernel(PlaceArgs a) {
     __shared__ u32 shc[8];
     __shared__ long long shm[8];
     __shared__ u32 ic[256];
     __shared__ long long im[256];
+    if (MODE == 1 && a.dirty[blockIdx.x] == 0) return;
     const u64 c = 1ull << a.log2c;
     const u32 hshift = a.B - a.log2c;
     const u64 i0 = u64(blockIdx.x) * kPlaceChunk + u64(threadIdx.x) * kPlaceItems;
@@ -343,37 +360,49 @@ __global__ void __launch_bounds__(256) build_place_kernel(PlaceArgs a) {
         else if (i0 + q < a.n)
             ld_cell_nc(a.srt + i0 + q, ks[q], vs[q]);
     }
-    const u64 knext = i0 + kPlaceItems < a.n ? ld_key(a.srt + i0 + kPlaceItems) : kEmpty;
     u32 sv = 0;
+    if (MODE == 0) {
+        const u64 knext = i0 + kPlaceItems < a.n ? ld_key(a.srt + i0 + kPlaceItems) : kEmpty;
+#pragma unroll
+        for (int q = 0; q < kPlaceItems; ++q) {
+            if (i0 + q >= a.n) continue;
+            const unsigned char f = survivor_first(a, i0 + q, ks[q], q + 1 < kPlaceItems ? ks[q + 1] : knext);
+            a.flags[i0 + q] = f;
+            if (f == 1) sv |= 1u << q;
+            if (f == 2) a.deferred[atomicAdd(&a.ex->n_deferred, 1u)] = u32(i0 + q);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kPlaceItems; ++q)
+            if (i0 + q < a.n && a.flags[i0 + q] == 1) sv |= 1u << q;
+    }
     Agg loc = {0u, kNegInf};
 #pragma unroll
     for (int q = 0; q < kPlaceItems; ++q) {
-        const u64 i = i0 + q;
-        if (i >= a.n || is_reserved(ks[q])) continue;
-        const u64 s = sort_key(ks[q], a.B);
-        const u64 kn = q + 1 < kPlaceItems ? ks[q + 1] : knext;
-        bool later = false;
-        if (i + 1 < a.n && sort_key(kn, a.B) == s) later = kn == ks[q] || later_in_run(a, i + 2, ks[q], s);
-        if (!later) {
-            sv |= 1u << q;
-            const Agg x = {1u, (long long)(s >> hshift)};
-            loc = agg_join(loc, x);
-        }
+        if (!((sv >> q) & 1u)) continue;
+        const Agg x = {1u, (long long)(sort_key(ks[q], a.B) >> hshift)};
+        loc = agg_join(loc, x);
     }
     Agg tot;
     const Agg incl = block_incl_agg(loc, tot, shc, shm);
-    if (!kWrite) {
+    if (MODE != 2) {
         if (threadIdx.x == 0) a.parts[blockIdx.x] = tot;
         return;
     }
     ic[threadIdx.x] = incl.c;
     im[threadIdx.x] = incl.m;
     __syncthreads();
-    Agg carry = a.parts[blockIdx.x];
+    const Agg first = a.parts[blockIdx.x];
+    Agg carry = first;
     if (threadIdx.x > 0) {
         const Agg left = {ic[threadIdx.x - 1], im[threadIdx.x - 1]};
         carry = agg_join(carry, left);
     }
+    // the chunk's survivors, by rank, with their positions: staged so that
+    // consecutive threads then store consecutive survivors (rising positions)
+    extern __shared__ __align__(16) unsigned char psm[];
+    Cell* const stage = reinterpret_cast<Cell*>(psm);
+    u64* const spos = reinterpret_cast<u64*>(stage + kPlaceChunk);
 #pragma unroll
     for (int q = 0; q < kPlaceItems; ++q) {
         if (!((sv >> q) & 1u)) continue;
@@ -381,17 +410,81 @@ __global__ void __launch_bounds__(256) build_place_kernel(PlaceArgs a) {
         const u64 rank = carry.c;
         const long long hm = (long long)home - (long long)rank;
         const long long m = carry.m > hm ? carry.m : hm;
-        const u64 p = rank + u64(m);
+        const u32 j = carry.c - first.c;
+        spos[j] = rank + u64(m);
+        stage[j].key = ks[q];
+        stage[j].val = vs[q];
         const Agg x = {1u, (long long)home};
         carry = agg_join(carry, x);
-        Cell cl;
-        cl.key = ks[q];
-        cl.val = vs[q];
+    }
+    __syncthreads();
+    for (u32 j = threadIdx.x; j < tot.c; j += 256) {
+        const u64 p = spos[j];
         if (p < c) {
-            a.cells[p] = cl;
+            a.cells[p] = stage[j];
         } else {
-            a.ov[rank] = cl;
+            const u64 rank = u64(first.c) + j;
+            a.ov[rank] = stage[j];
             atomicMin(&a.ex->first_ov, rank);
+        }
+    }
+}
+
+u64 place_smem_bytes() { return size_t(kPlaceChunk) * (sizeof(Cell) + sizeof(u64)); }
+
+// ---------------------------------------------------------------------------
+// Deferred survivor tests: one CTA per deferred cell scans the rest of its run
+// 2048 cells at a time (coalesced) for another copy of its key; a survivor
+// marks its chunk for the recount.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) build_resolve_kernel(PlaceArgs a) {
+    __shared__ u64 sh_found[8], sh_end[8];
+    const u32 nd = a.ex->n_deferred;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (u32 d = blockIdx.x; d < nd; d += gridDim.x) {
+        const u64 i = a.deferred[d];
+        const u64 k = ld_key(a.srt + i);
+        const u64 s = sort_key(k, a.B);
+        unsigned char f = 1;
+        for (u64 j0 = i + 2; j0 < a.n; j0 += kPlaceChunk) {
+            u64 found = ~0ull, end = ~0ull;
+            for (int q = 0; q < kPlaceItems; ++q) {
+                const u64 j = j0 + u64(q) * 256 + threadIdx.x;
+                if (j >= a.n) {
+                    end = end < a.n ? end : a.n;
+                    continue;
+                }
+                const u64 kj = ld_key(a.srt + j);
+                if (sort_key(kj, a.B) != s) end = end < j ? end : j;
+                else if (kj == k) found = found < j ? found : j;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const u64 f2 = __shfl_xor_sync(0xffffffffu, found, o);
+                const u64 e2 = __shfl_xor_sync(0xffffffffu, end, o);
+                found = f2 < found ? f2 : found;
+                end = e2 < end ? e2 : end;
+            }
+            if (lane == 0) {
+                sh_found[w] = found;
+                sh_end[w] = end;
+            }
+            __syncthreads();
+            found = sh_found[0];
+            end = sh_end[0];
+            for (int v = 1; v < 8; ++v) {
+                found = sh_found[v] < found ? sh_found[v] : found;
+                end = sh_end[v] < end ? sh_end[v] : end;
+            }
+            __syncthreads();
+            if (found < end) {  // a later copy inside the run
+                f = 0;
+                break;
+            }
+            if (end != ~0ull) break;  // the run ended first
+        }
+        if (threadIdx.x == 0) {
+            a.flags[i] = f;
+            if (f) a.dirty[i / kPlaceChunk] = 1;
         }
     }
 }
@@ -466,36 +559,64 @@ __global__ void build_finish_kernel(Cell* cells, u32 log2c, const Cell* ov, Buil
 
 u32 build_sort_bits(u32 log2c) { return log2c <= 32 ? 32u : 8u * ((log2c + 7u) / 8u); }
 
-u64 build_scratch_bytes(u64 n) {
-    const u64 ntiles = (n + kSortTile - 1) / kSortTile;
-    const u64 hist = 256 * ntiles;
-    const u64 nparts = (hist + kScanChunk - 1) / kScanChunk;
-    const u64 nchunks = (n + kPlaceChunk - 1) / kPlaceChunk;
-    auto al = [](u64 x) { return (x + 255) & ~255ull; };
-    return 2 * al(n * sizeof(Cell)) + al(hist * 4) + al(nparts * 4) + al(nchunks * sizeof(Agg)) +
-           al(sizeof(BuildExtra));
+namespace {
+// Scratch layout: two sort buffers, the digit histogram and its scan
+// partials, the chunk joins, the survivor flags, the deferred list, the
+// chunks' recount marks, the counters.
+struct Layout {
+    u64 ntiles, hist_n, nparts, nchunks;
+    u64 off_buf1, off_hist, off_part, off_parts, off_flags, off_def, off_dirty, off_ex, total;
+    explicit Layout(u64 n) {
+        auto al = [](u64 x) { return (x + 255) & ~255ull; };
+        ntiles = (n + kSortTile - 1) / kSortTile;
+        hist_n = 256 * ntiles;
+        nparts = (hist_n + kScanChunk - 1) / kScanChunk;
+        nchunks = (n + kPlaceChunk - 1) / kPlaceChunk;
+        off_buf1 = al(n * sizeof(Cell));
+        off_hist = off_buf1 + al(n * sizeof(Cell));
+        off_part = off_hist + al(hist_n * 4);
+        off_parts = off_part + al(nparts * 4);
+        off_flags = off_parts + al(nchunks * sizeof(Agg));
+        off_def = off_flags + al(n);
+        off_dirty = off_def + al(n * 4);
+        off_ex = off_dirty + al(nchunks);
+        total = off_ex + al(sizeof(BuildExtra));
+    }
+};
+
+PlaceArgs place_args(const Cell* sorted, u64 n, u32 log2c, void* scratch, BuildExtra* ex) {
+    const Layout L(n);
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+    PlaceArgs a;
+    a.srt = sorted;
+    a.n = n;
+    a.B = build_sort_bits(log2c);
+    a.log2c = log2c;
+    a.parts = reinterpret_cast<Agg*>(base + L.off_parts);
+    a.flags = base + L.off_flags;
+    a.deferred = reinterpret_cast<u32*>(base + L.off_def);
+    a.dirty = base + L.off_dirty;
+    a.cells = nullptr;
+    // the survivors past the last cell go to whichever sort buffer does not
+    // hold the sorted cells
+    Cell* b0 = reinterpret_cast<Cell*>(base);
+    a.ov = sorted == b0 ? reinterpret_cast<Cell*>(base + L.off_buf1) : b0;
+    a.ex = ex;
+    return a;
 }
+}  // namespace
+
+u64 build_scratch_bytes(u64 n) { return Layout(n).total; }
 
 cudaError_t launch_build_sort(const u64* keys, const u64* vals, u64 n, u32 log2c, int full_keys, void* scratch,
                               const Cell** sorted, BuildExtra** ex_out, cudaStream_t s) {
     const u32 B = build_sort_bits(log2c);
-    const u64 ntiles = (n + kSortTile - 1) / kSortTile;
-    const u64 hist_n = 256 * ntiles;
-    const u64 nparts = (hist_n + kScanChunk - 1) / kScanChunk;
-    const u64 nchunks = (n + kPlaceChunk - 1) / kPlaceChunk;
-    auto al = [](u64 x) { return (x + 255) & ~255ull; };
-    unsigned char* p = static_cast<unsigned char*>(scratch);
-    Cell* buf[2];
-    buf[0] = reinterpret_cast<Cell*>(p);
-    p += al(n * sizeof(Cell));
-    buf[1] = reinterpret_cast<Cell*>(p);
-    p += al(n * sizeof(Cell));
-    u32* hist = reinterpret_cast<u32*>(p);
-    p += al(hist_n * 4);
-    u32* part = reinterpret_cast<u32*>(p);
-    p += al(nparts * 4);
-    p += al(nchunks * sizeof(Agg));
-    BuildExtra* ex = reinterpret_cast<BuildExtra*>(p);
+    const Layout L(n);
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+    Cell* buf[2] = {reinterpret_cast<Cell*>(base), reinterpret_cast<Cell*>(base + L.off_buf1)};
+    u32* hist = reinterpret_cast<u32*>(base + L.off_hist);
+    u32* part = reinterpret_cast<u32*>(base + L.off_part);
+    BuildExtra* ex = reinterpret_cast<BuildExtra*>(base + L.off_ex);
     cudaError_t e = cudaMemsetAsync(ex, 0, sizeof(BuildExtra), s);
     if (e != cudaSuccess) return e;
     SortSrc src;
@@ -507,12 +628,13 @@ cudaError_t launch_build_sort(const u64* keys, const u64* vals, u64 n, u32 log2c
     if (e != cudaSuccess) return e;
     int cur = 0;
     for (u32 shift = 0; shift < B; shift += 8) {
-        radix_hist_kernel<<<unsigned(ntiles), kSortThreads, 0, s>>>(src, n, B, shift, hist, ntiles, ex, full_keys);
+        radix_hist_kernel<<<unsigned(L.ntiles), kSortThreads, 0, s>>>(src, n, B, shift, hist, L.ntiles, ex,
+                                                                    full_keys);
         count_launch();
-        e = scan_exclusive(hist, hist_n, part, s);
+        e = scan_exclusive(hist, L.hist_n, part, s);
         if (e != cudaSuccess) return e;
-        radix_scatter_kernel<<<unsigned(ntiles), kSortThreads, scatter_smem_bytes(), s>>>(src, buf[cur], n, B,
-                                                                                        shift, hist, ntiles);
+        radix_scatter_kernel<<<unsigned(L.ntiles), kSortThreads, scatter_smem_bytes(), s>>>(src, buf[cur], n, B,
+                                                                                          shift, hist, L.ntiles);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -526,50 +648,28 @@ cudaError_t launch_build_sort(const u64* keys, const u64* vals, u64 n, u32 log2c
 
 cudaError_t launch_build_count(const Cell* sorted, u64 n, u32 log2c, void* scratch, BuildExtra* ex,
                                cudaStream_t s) {
-    const u64 ntiles = (n + kSortTile - 1) / kSortTile;
-    const u64 hist_n = 256 * ntiles;
-    const u64 nparts = (hist_n + kScanChunk - 1) / kScanChunk;
-    const u64 nchunks = (n + kPlaceChunk - 1) / kPlaceChunk;
-    auto al = [](u64 x) { return (x + 255) & ~255ull; };
-    unsigned char* p = static_cast<unsigned char*>(scratch) + 2 * al(n * sizeof(Cell)) + al(hist_n * 4) +
-                       al(nparts * 4);
-    PlaceArgs a;
-    a.srt = sorted;
-    a.n = n;
-    a.B = build_sort_bits(log2c);
-    a.log2c = log2c;
-    a.parts = reinterpret_cast<Agg*>(p);
-    a.cells = nullptr;
-    a.ov = nullptr;
-    a.ex = ex;
-    build_place_kernel<false><<<unsigned(nchunks), 256, 0, s>>>(a);
-    build_place_scan_kernel<<<1, 256, 0, s>>>(a.parts, nchunks, ex);
-    count_launch();
-    count_launch();
+    const Layout L(n);
+    const PlaceArgs a = place_args(sorted, n, log2c, scratch, ex);
+    cudaError_t e = cudaMemsetAsync(a.dirty, 0, L.nchunks, s);
+    if (e != cudaSuccess) return e;
+    build_place_kernel<0><<<unsigned(L.nchunks), 256, 0, s>>>(a);
+    // deferred survivor tests (both kernels return at once when there are none)
+    build_resolve_kernel<<<unsigned(sm_count() * 4), 256, 0, s>>>(a);
+    build_place_kernel<1><<<unsigned(L.nchunks), 256, 0, s>>>(a);
+    build_place_scan_kernel<<<1, 256, 0, s>>>(a.parts, L.nchunks, ex);
+    for (int i = 0; i < 4; ++i) count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_build_place(const Cell* sorted, u64 n, Cell* cells, u32 log2c, void* scratch, BuildExtra* ex,
                                DevState* st, const u64* vals, cudaStream_t s) {
-    const u64 ntiles = (n + kSortTile - 1) / kSortTile;
-    const u64 hist_n = 256 * ntiles;
-    const u64 nparts = (hist_n + kScanChunk - 1) / kScanChunk;
-    const u64 nchunks = (n + kPlaceChunk - 1) / kPlaceChunk;
-    auto al = [](u64 x) { return (x + 255) & ~255ull; };
-    unsigned char* base = static_cast<unsigned char*>(scratch);
-    PlaceArgs a;
-    a.srt = sorted;
-    a.n = n;
-    a.B = build_sort_bits(log2c);
-    a.log2c = log2c;
-    a.parts = reinterpret_cast<Agg*>(base + 2 * al(n * sizeof(Cell)) + al(hist_n * 4) + al(nparts * 4));
+    const Layout L(n);
+    PlaceArgs a = place_args(sorted, n, log2c, scratch, ex);
     a.cells = cells;
-    // the survivors past the last cell go to whichever sort buffer does not
-    // hold the sorted cells
-    Cell* b0 = reinterpret_cast<Cell*>(base);
-    a.ov = sorted == b0 ? reinterpret_cast<Cell*>(base + al(n * sizeof(Cell))) : b0;
-    a.ex = ex;
-    build_place_kernel<true><<<unsigned(nchunks), 256, 0, s>>>(a);
+    cudaError_t e = cudaFuncSetAttribute(build_place_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(place_smem_bytes()));
+    if (e != cudaSuccess) return e;
+    build_place_kernel<2><<<unsigned(L.nchunks), 256, place_smem_bytes(), s>>>(a);
     build_finish_kernel<<<1, 32, 0, s>>>(cells, log2c, a.ov, ex, st, vals);
     count_launch();
     count_launch();

@@ -72,6 +72,8 @@ struct BuildExtra {
     u64 S;           // survivors
     u64 first_ov;    // lowest rank placed past the last cell (~0: none)
     u64 reserved;    // nonzero: a key 0 / ~0 was skipped (full key space off)
+    u32 n_deferred;  // cells whose survivor test was deferred to a CTA scan
+    u32 pad;
 };
 u32 build_sort_bits(u32 log2c);
 u64 build_scratch_bytes(u64 n);

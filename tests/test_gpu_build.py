@@ -136,3 +136,46 @@ def test_build_from_host_arrays_and_empty_batch(cuda_lib, oracle_mod):
     o = oracle_mod.OracleTable(1 << 16)
     assert o.build(keys, vals) == 0
     assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), o.cells())
+
+
+def _unfmix64(h):
+    """Inverse of the MurmurHash3 fmix64 finalizer (test-side, checked against the oracle's hash)."""
+    m = (1 << 64) - 1
+    x = h
+    x ^= x >> 33
+    x = (x * pow(0xc4ceb9fe1a85ec53, -1, 1 << 64)) & m
+    x ^= x >> 33
+    x = (x * pow(0xff51afd7ed558ccd, -1, 1 << 64)) & m
+    x ^= x >> 33
+    return x
+
+
+def test_build_runs_mixing_keys(cuda_lib, oracle_mod):
+    # Two keys whose hashes differ only in the lowest bit share every sort
+    # bit: their copies form one run, in input order.  A copy of the rare key
+    # followed by hundreds of copies of the other defers its survivor test to
+    # the jump pass (both outcomes: a later copy exists / does not).
+    base = W.uniform_keys(40_000, start=7_000_000, seed=23)
+    hk = int(oracle_mod.hash64(base[:1])[0])
+    k_hot = int(base[0])
+    k_rare = _unfmix64(hk ^ 1)
+    assert int(oracle_mod.hash64(np.array([k_rare], dtype=np.uint64))[0]) == hk ^ 1
+    k3 = int(base[1])
+    k3_twin = _unfmix64(int(oracle_mod.hash64(base[1:2])[0]) ^ 2)
+    run = ([k_rare] + [k_hot] * 300 + [k_rare] + [k_hot] * 200 +   # rare: not the last, then the last
+           [k3_twin] + [k3] * 500)                                  # twin: single copy before 500 others
+    keys = np.concatenate([base[2:20_000], np.array(run, dtype=np.uint64), base[20_000:]])
+    vals = np.arange(1, keys.size + 1, dtype=np.uint64)
+    t, o, r = _both(cuda_lib, oracle_mod, 1 << 17, keys, vals)
+    assert r == 0
+    assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), o.cells())
+    last = {}
+    for k, v in zip(keys.tolist(), vals.tolist()):
+        last[k] = v
+    import torch
+
+    q = np.array([k_hot, k_rare, k3, k3_twin], dtype=np.uint64)
+    got = torch.empty(4, dtype=torch.int64, device="cuda")
+    t.find(to_dev(q), got)
+    assert to_np_u64(got).tolist() == [last[int(k)] for k in q]
+    assert t.size()[0] == len(last)

@@ -164,3 +164,24 @@ def test_build_reserved_keys(oracle_mod):
     assert f.live == 12
     v, found = f.find(np.array([0, TOMB], dtype=np.uint64))
     assert found.all() and v.tolist() == [13, 12]
+
+
+def test_build_keeps_last_in_runs_mixing_keys(oracle_mod):
+    # two keys whose hashes share all B sort bits (a birthday collision found
+    # by search over a stream) form one run; interleaved copies must still
+    # give the dictionary of last values
+    B = oracle_mod.build_sort_bits(10)
+    ks = W.uniform_keys(1 << 18, start=0, seed=77)
+    top = oracle_mod.hash64(ks) >> np.uint64(64 - B)
+    u, first, counts = np.unique(top, return_index=True, return_counts=True)
+    j = int(np.nonzero(counts > 1)[0][0])
+    a = int(ks[first[j]])
+    b = int(ks[np.nonzero(top == u[j])[0][1]])
+    assert a != b
+    keys = np.array([a, b, b, a, b, a, a, b], dtype=np.uint64)
+    vals = np.arange(1, 9, dtype=np.uint64)
+    t = oracle_mod.OracleTable(1 << 10)
+    assert t.build(keys, vals) == 0
+    got, found = t.find(np.array([a, b], dtype=np.uint64))
+    assert found.all() and got.tolist() == [7, 8]
+    assert t.live == 2
