@@ -91,9 +91,10 @@ typedef enum {
  * 512 below load 0.6, else 1024).  alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).
  * iou_aggregate: 1 (default) folds equal keys of each window of 1024
  * insertOrUpdate or update operations in shared memory first (one table
- * operation per distinct key and window); 2 also combines equal keys within
- * each warp step before that for insertOrUpdate (faster only under extreme
- * skew); 0 probes every operation with the group kernel.  reuse_tombstones: 0 (default) = the paper's rule,
+ * operation per distinct key and window), and for insertOrUpdate also combines
+ * equal keys within each warp step in a window that follows a window with
+ * fewer distinct keys than a fifth of its operations; 2 always combines them
+ * (insertOrUpdate); 0 probes every operation with the group kernel.  reuse_tombstones: 0 (default) = the paper's rule,
  * an erased cell is never used again until a migration drops it (Sec. 3
  * "Deletions"); 1 = an insert / insert-or-update that finds its key absent
  * puts it into the first tombstone on its probe path (safe under phase

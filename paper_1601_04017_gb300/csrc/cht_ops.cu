@@ -106,7 +106,7 @@ cudaError_t launch_mode(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStre
     }
 }
 
-template <int MODE, bool WD, bool RE>
+template <int MODE, int WD, bool RE>
 cudaError_t launch_agg(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     constexpr size_t smem = agg_smem_bytes<MODE>();
     static std::atomic<int> occ{0};
@@ -137,22 +137,22 @@ cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, bool warp_dedup, i
     const bool re = a.reuse != 0;
     if (mode == kIouAdd) {
         if (re)
-            return warp_dedup ? launch_agg<kIouAdd, true, true>(a, ctas_per_sm, s)
-                              : launch_agg<kIouAdd, false, true>(a, ctas_per_sm, s);
-        return warp_dedup ? launch_agg<kIouAdd, true, false>(a, ctas_per_sm, s)
-                          : launch_agg<kIouAdd, false, false>(a, ctas_per_sm, s);
+            return warp_dedup ? launch_agg<kIouAdd, 2, true>(a, ctas_per_sm, s)
+                              : launch_agg<kIouAdd, 1, true>(a, ctas_per_sm, s);
+        return warp_dedup ? launch_agg<kIouAdd, 2, false>(a, ctas_per_sm, s)
+                          : launch_agg<kIouAdd, 1, false>(a, ctas_per_sm, s);
     }
     if (mode == kIouOverwrite) {
         if (re)
-            return warp_dedup ? launch_agg<kIouOverwrite, true, true>(a, ctas_per_sm, s)
-                              : launch_agg<kIouOverwrite, false, true>(a, ctas_per_sm, s);
-        return warp_dedup ? launch_agg<kIouOverwrite, true, false>(a, ctas_per_sm, s)
-                          : launch_agg<kIouOverwrite, false, false>(a, ctas_per_sm, s);
+            return warp_dedup ? launch_agg<kIouOverwrite, 2, true>(a, ctas_per_sm, s)
+                              : launch_agg<kIouOverwrite, 1, true>(a, ctas_per_sm, s);
+        return warp_dedup ? launch_agg<kIouOverwrite, 2, false>(a, ctas_per_sm, s)
+                          : launch_agg<kIouOverwrite, 1, false>(a, ctas_per_sm, s);
     }
     // update: equal keys fold the same way; no cell is filled, so neither the
     // warp pre-reduction nor tombstone reuse applies
-    if (mode == kUpdAdd) return launch_agg<kUpdAdd, false, false>(a, ctas_per_sm, s);
-    if (mode == kUpdOverwrite) return launch_agg<kUpdOverwrite, false, false>(a, ctas_per_sm, s);
+    if (mode == kUpdAdd) return launch_agg<kUpdAdd, 0, false>(a, ctas_per_sm, s);
+    if (mode == kUpdOverwrite) return launch_agg<kUpdOverwrite, 0, false>(a, ctas_per_sm, s);
     return cudaErrorInvalidValue;
 }
 

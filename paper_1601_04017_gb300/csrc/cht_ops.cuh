@@ -539,9 +539,12 @@ namespace cht {
 // atomicUpdate), whose result -- inserted or updated -- goes to the slot's
 // first operation; every other operation of the key reports "updated"
 // (linearized right after it).  Under skewed keys this turns millions of
-// atomics on one hot cell into one per window.  Variant WARP_DEDUP first
-// combines equal keys of a warp's load step with __match_any_sync, which
-// pays off only under extreme skew (many lanes on one shared-memory slot).
+// atomics on one hot cell into one per window.  A warp may first combine the
+// equal keys of its load step with __match_any_sync, which pays off only
+// under extreme skew (many lanes on one shared-memory slot): DEDUP 2 always
+// does, DEDUP 1 (insertOrUpdate's default) does it for a window when the
+// CTA's previous window had fewer distinct keys than a fifth of its
+// operations, DEDUP 0 (update) never.
 // ---------------------------------------------------------------------------
 constexpr int kAggBlock = 256;
 constexpr int kAggWindow = 1024;
@@ -633,7 +636,7 @@ constexpr size_t agg_smem_bytes() {
            ((MODE == kUpdAdd || MODE == kUpdOverwrite) ? size_t(kAggWindow) * 2 + kAggSlots : 0);
 }
 
-template <int MODE, bool WARP_DEDUP, bool kReuse>
+template <int MODE, int DEDUP, bool kReuse>
 __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
     pdl_enter();
     constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
@@ -649,14 +652,18 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
     const int tid = threadIdx.x;
     u64 n_ins = 0, n_reused = 0;
     u32 sbits = 0;
+    __shared__ u32 s_distinct[2];  // distinct keys of this CTA's window, by window parity
     for (int s = tid; s < kAggSlots; s += kAggBlock) {
         skey[s] = kEmpty;
         sval[s] = 0;
     }
+    if (tid < 2) s_distinct[tid] = 0;
     __syncthreads();
+    bool dedup = DEDUP == 2;
     const u64 nwin = (a.n + kAggWindow - 1) / kAggWindow;
     for (u64 w = blockIdx.x; w < nwin; w += gridDim.x) {
         const u64 w0 = w * kAggWindow;
+        const int par = int((w / gridDim.x) & 1);
         // fold the window's operations into the slots
 #pragma unroll
         for (int j = 0; j < kAggWindow / kAggBlock; ++j) {
@@ -679,9 +686,10 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
                     valid = false;
                 }
             }
-            // optionally, equal keys within the warp first: one lane per key goes on
-            const u32 vm = WARP_DEDUP ? __ballot_sync(0xffffffffu, valid) : 0u;
-            if (WARP_DEDUP && valid) {
+            // optionally, equal keys within the warp first: one lane per key goes
+            // on (dedup is the same for the whole block)
+            const u32 vm = dedup ? __ballot_sync(0xffffffffu, valid) : 0u;
+            if (dedup && valid) {
                 const u32 same = __match_any_sync(vm, key);
                 const int lane = tid & 31;
                 if (kAdd) {
@@ -717,6 +725,7 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
                     else sval[s] = d;
                     slead[s] = off;
                     if (kUpdate) sslot[off] = (unsigned short)s;
+                    if (DEDUP == 1) atomicAdd(&s_distinct[par], 1u);
                     break;
                 }
                 if (same) {
@@ -729,6 +738,13 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
             }
         }
         __syncthreads();
+        if (DEDUP == 1) {
+            // the next window of this CTA combines within warps if this one had
+            // few distinct keys; the other parity's counter is free to reset
+            const u64 ops = a.n - w0 < u64(kAggWindow) ? a.n - w0 : u64(kAggWindow);
+            dedup = u64(s_distinct[par]) * 5 < ops;
+            if (tid == 0) s_distinct[par ^ 1] = 0;
+        }
         // flush: one global operation per distinct key of the window
         for (int s = tid; s < kAggSlots; s += kAggBlock) {
             const u64 k = skey[s];
