@@ -154,7 +154,7 @@ def test_build_runs_mixing_keys(cuda_lib, oracle_mod):
     # Two keys whose hashes differ only in the lowest bit share every sort
     # bit: their copies form one run, in input order.  A copy of the rare key
     # followed by hundreds of copies of the other defers its survivor test to
-    # the jump pass (both outcomes: a later copy exists / does not).
+    # a CTA-wide scan of the run (both outcomes: a later copy exists / does not).
     base = W.uniform_keys(40_000, start=7_000_000, seed=23)
     hk = int(oracle_mod.hash64(base[:1])[0])
     k_hot = int(base[0])
