@@ -137,6 +137,8 @@ __device__ __forceinline__ void place_window_smem(u32* bm, unsigned short* map, 
         const u32 cand = mine ? c : (0x80000000u | u32(lane));
         const u32 m = __popc(__match_any_sync(0xffffffffu, cand) & below);
         u32 prop = cand;
+        // no shared candidate: every pending lane's candidate is its placement
+        const bool grouped = __any_sync(0xffffffffu, mine && m != 0u);
         if (mine && m != 0u && c < tl) {
             // the m-th free cell after c: drop c, then skip m - 1 free cells
             u32 r = m;
@@ -156,10 +158,14 @@ __device__ __forceinline__ void place_window_smem(u32* bm, unsigned short* map, 
                 bits = ~vbm[w];
             }
         }
-        // (every lane takes part in both votes: neither sits behind a branch)
-        const u32 psame = __match_any_sync(0xffffffffu, prop);
-        const u32 dups = __ballot_sync(0xffffffffu, mine && (psame & below) != 0u);
-        const u32 commit = pending & ((dups & (0u - dups)) - 1u);  // all pending lanes if dups == 0
+        // (every lane takes part in both votes: neither sits behind a lane
+        // branch; `grouped` is the same for the whole warp)
+        u32 commit = pending;
+        if (grouped) {
+            const u32 psame = __match_any_sync(0xffffffffu, prop);
+            const u32 dups = __ballot_sync(0xffffffffu, mine && (psame & below) != 0u);
+            commit = pending & ((dups & (0u - dups)) - 1u);  // all pending lanes if dups == 0
+        }
         if ((commit >> lane) & 1u) {
             if (prop < tl) {
                 atomicOr(&bm[prop >> 5], 1u << (prop & 31));
