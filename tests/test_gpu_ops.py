@@ -243,9 +243,50 @@ def test_host_arrays_match_device(cuda_lib, oracle_mod):
     # pinned host memory goes through the same staging
     pk = torch.from_numpy(q.view(np.int64)).pin_memory()
     pv = torch.zeros(q.size, dtype=torch.int64).pin_memory()
-    t.find(pk, pv)
+    pc = torch.zeros(q.size, dtype=torch.uint8).pin_memory()
+    t.find(pk, pv, pc)
     torch.cuda.synchronize()
     assert np.array_equal(pv.numpy().view(np.uint64), ev)
+    assert np.array_equal(pc.numpy(), ef)
+
+
+@pytest.mark.parametrize("growable", [False, True])
+def test_pinned_host_arrays(cuda_lib, oracle_mod, growable):
+    """Pinned host arrays as inputs and outputs of every operation type (the
+    growable table also takes its chunked growth path on them)."""
+    import torch
+
+    c = 1 << 12 if growable else 1 << 15
+    keys = W.uniform_keys(12000, seed=57)
+    vals = W.values_for(keys)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).pin_memory()  # noqa: E731
+    pk, pv = pin(keys), pin(vals)
+    pc = torch.full((keys.size,), 255, dtype=torch.uint8).pin_memory()
+    t = cuda_lib.Table(c, growable=growable)
+    o = oracle_mod.OracleTable(c, growable=growable)
+    t.insert(pk, pv, pc)
+    torch.cuda.synchronize()
+    assert np.array_equal(pc.numpy(), o.insert(keys, vals))
+    z = W.zipf_keys(20000, 1.0, 4000, seed=9)
+    pz, pones = pin(z), pin(np.ones(z.size, np.uint64))
+    zc = torch.full((z.size,), 255, dtype=torch.uint8).pin_memory()
+    t.insert_or_update(pz, pones, cuda_lib.ADD, zc)
+    torch.cuda.synchronize()
+    oc = ops_by_key(z, o.insert_or_update(z, np.ones(z.size, np.uint64), 1))
+    for k, cs in ops_by_key(z, zc.numpy()).items():  # one insertion per new key, as in the oracle
+        assert sum(c_[0] for c_ in cs) == sum(x[0] for x in oc[k])
+    ec = torch.full((4000,), 255, dtype=torch.uint8).pin_memory()
+    t.erase(pin(keys[:4000]), ec)
+    torch.cuda.synchronize()
+    assert np.array_equal(ec.numpy(), o.erase(keys[:4000]))
+    q = np.concatenate([keys, z])
+    pq = pin(q)
+    qv = torch.zeros(q.size, dtype=torch.int64).pin_memory()
+    qc = torch.zeros(q.size, dtype=torch.uint8).pin_memory()
+    t.find(pq, qv, qc)
+    torch.cuda.synchronize()
+    ev, ef = o.find(q)
+    assert np.array_equal(qv.numpy().view(np.uint64), ev) and np.array_equal(qc.numpy(), ef)
 
 
 def _tombstones(t):
