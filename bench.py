@@ -17,7 +17,7 @@ in HBM before the timed region; every input is far larger than the 129 MB L2.
 (the library stages them to the device and copies the results back).
 
 --impl reference times the CPU oracle (single thread) on a bounded sample of
-the same workload: the same recipe at 2^22 cells.
+the same workload: the same recipe at 2^23 cells.
 """
 from __future__ import annotations
 
@@ -172,10 +172,11 @@ def make_inputs(device: str):
 class StepRunner:
     """Runs one step; records per-call CUDA events when asked."""
 
-    def __init__(self, cht, inp, host: bool = False):
+    def __init__(self, cht, inp, host: bool = False, partition: int = 0):
         import torch
 
         self.cht, self.inp, self.host = cht, inp, host
+        self.tcfg = {"partition": partition}
         self.torch = torch
         wl = inp["wl"]
         n05, n09 = wl["counts"][0.5], wl["counts"][0.9]
@@ -217,7 +218,7 @@ class StepRunner:
             b.record(s)
             events.setdefault(name, []).append((a, b))
 
-        t = cht.Table(1 << LOG2C)
+        t = cht.Table(1 << LOG2C, config=self.tcfg)
         timed("insert_0.5", lambda: t.insert(self.keys[:n05], self.vals[:n05], self.codes[:n05]))
         timed("find_hit_0.5", lambda: t.find(self.h05, self.vout, self.codes[:nf]))
         timed("find_miss_0.5", lambda: t.find(self.miss, self.vout, self.codes[:nf]))
@@ -225,13 +226,13 @@ class StepRunner:
         timed("find_hit_0.9", lambda: t.find(self.h09, self.vout, self.codes[:nf]))
         timed("find_miss_0.9", lambda: t.find(self.miss, self.vout, self.codes[:nf]))
         for sv in ZIPF_S:
-            t2 = cht.Table(1 << LOG2C)
+            t2 = cht.Table(1 << LOG2C, config=self.tcfg)
             timed(f"iou_add_s{sv}", lambda: t2.insert_or_update(self.zipf[sv], self.ones, cht.ADD, self.codes))
             t2.destroy()
         timed("erase", lambda: t.erase(self.keys[:nf], self.codes[:nf]))
         timed("migrate_x2", lambda: t.migrate(2 << LOG2C))
         t.destroy()
-        tg = cht.Table(1 << GROW_LOG2C0, growable=True)
+        tg = cht.Table(1 << GROW_LOG2C0, growable=True, config=self.tcfg)
         timed("grow_insert", lambda: tg.insert(self.keys[:n05], self.vals[:n05], self.codes[:n05]))
         tg.destroy()
 
@@ -399,6 +400,63 @@ def latency_percentiles(cht, inp, reps: int):
     return out
 
 
+# Which kernel runs each timed call of the step (the automatic probe windows:
+# op_kernel<G lanes, V cells per lane, mode>).  The growing insert mixes
+# inserts and migrations and is left out of the per-kernel figures.
+CALL_KERNEL = {
+    "insert_0.5": "op_kernel<1,2,insert>",
+    "find_hit_0.5": "op_kernel<2,4,find>", "find_miss_0.5": "op_kernel<2,4,find>",
+    "insert_0.9": "op_kernel<4,4,insert>",
+    "find_hit_0.9": "op_kernel<4,4,find>", "find_miss_0.9": "op_kernel<4,4,find>",
+    "erase": "op_kernel<4,2,erase>",
+    "migrate_x2": "migrate_window_kernel",
+    **{f"iou_add_s{sv}": "iou_agg_kernel<insertOrUpdate add>" for sv in ZIPF_S},
+}
+
+
+def kernel_rooflines(breakdown, counts, bpo, peak, peak_kind):
+    """Per kernel: algorithmic bytes of all its calls in a step over their
+    summed CUDA-event time (= bytes per launch / mean launch time).  The
+    dominant kernel is the one with the largest summed time; the others are
+    listed after it."""
+    fam = {}
+    for name, row in breakdown.items():
+        k = CALL_KERNEL.get(name)
+        if k is None:
+            continue
+        if name == "migrate_x2":
+            b = algorithmic_bytes("migrate", gamma=2) * counts[name]
+        else:
+            b = bpo[name] * counts[name]
+        f = fam.setdefault(k, {"ms": 0.0, "bytes": 0.0, "calls": []})
+        f["ms"] += row["ms"]
+        f["bytes"] += b
+        f["calls"].append(name)
+    rows = []
+    for k, f in fam.items():
+        gbs = f["bytes"] / (f["ms"] * 1e-3) / 1e9
+        rows.append({"bound": "hbm", "kernel": k, "calls": f["calls"], "launches_per_step": len(f["calls"]),
+                     "ms_per_step": round(f["ms"], 4), "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(gbs / peak, 4), "peak_source": peak_kind,
+                     "bytes_per_launch": round(f["bytes"] / len(f["calls"]))})
+    rows.sort(key=lambda r: -r["ms_per_step"])
+    dom = dict(rows[0])
+    dom["traffic"] = None  # set from an ncu capture of the current kernel when one exists
+    return dom, rows[1:]
+
+
+def load_half_fractions(breakdown, peak):
+    """The load-0.5 figures the project aims at (>= 0.5 of the random-access
+    roofline for find and insert): the 2^28-cell step's calls and, when
+    measured, the 2^20-cell calls replayed from a CUDA graph."""
+    out = {"goal_frac": 0.5, "peak": peak, "unit": "GB/s"}
+    for name in ("insert_0.5", "find_hit_0.5", "find_miss_0.5"):
+        row = breakdown.get(name)
+        if row and "gbs" in row:
+            out[f"2p28_{name}"] = round(row["gbs"] / peak, 4)
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -408,7 +466,8 @@ def run_gpu(args):
 
     cht.load_library()
     inp = make_inputs("cuda")
-    runner = StepRunner(cht, inp)
+    pmode = {"auto": 0, "off": 1, "on": 2}[args.partition]
+    runner = StepRunner(cht, inp, partition=pmode)
     for _ in range(args.warmup):
         runner.step()
     torch.cuda.synchronize()
@@ -451,26 +510,13 @@ def run_gpu(args):
             row.update({"bytes_per_src_cell": 48, "gbs": round(gbs, 1),
                         "frac_of_" + peak_kind: round(gbs / peak, 4)})
         breakdown[name] = row
-    probe_rows = {k: v for k, v in breakdown.items() if k not in ("migrate_x2", "grow_insert")}
-    dom = max(probe_rows, key=lambda k: probe_rows[k]["ms"])
-    dom_t = probe_rows[dom]["ms"]
-    achieved = bpo[dom] * counts[dom] / (dom_t * 1e-3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            with open(tr_path) as f:
-                traffic = json.load(f).get(dom)
-        except (OSError, ValueError):
-            traffic = None
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": traffic}
+    roofline, roofline_others = kernel_rooflines(breakdown, counts, bpo, peak, peak_kind)
+    target = load_half_fractions(breakdown, peak)
 
     # end-to-end through the same API with pinned host arrays
     e2e = None
     if not args.no_e2e:
-        hrunner = StepRunner(cht, inp, host=True)
+        hrunner = StepRunner(cht, inp, host=True, partition=pmode)
         hrunner.step()
         torch.cuda.synchronize()
         barrier(pg)
@@ -485,6 +531,11 @@ def run_gpu(args):
         del hrunner
 
     lat = latency_percentiles(cht, inp, args.latency_reps) if args.latency_reps > 0 else None
+    if lat:
+        for name in ("insert", "find_hit", "find_miss"):
+            g = lat.get(f"{name}_graph")
+            if g:
+                target[f"2p20_{name}_graph"] = g["frac_of_roofline"]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_once()
@@ -499,11 +550,13 @@ def run_gpu(args):
                                    "2^26 keys for s in {0.5,1.0,1.25,1.5}, erase 2^27, migrate x2; "
                                    "growable table 2^12 cells taking 2^27 inserts (15 doublings)",
                        "capacity_cells": 1 << LOG2C, "ops_per_step": runner.ops_per_step,
+                       "partition": args.partition,
                        "l2": "inputs and table far larger than L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "probe_window": "auto by load: finds 2 lanes x 64 B below 0.6, 4 x 64 B above; "
                                        "inserts 1 x 32 B below 0.6, 4 x 64 B above"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "roofline_other_kernels": roofline_others, "target": target,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "breakdown": breakdown, "latency_config1": lat,
         }
         print(json.dumps(line), flush=True)
@@ -514,11 +567,12 @@ def run_gpu(args):
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline and the reference arm)
 # ----------------------------------------------------------------------------
-CPU_LOG2C = 22
+CPU_LOG2C = 23
+CPU_BASELINE_MIN_S = 10.0  # the cpu_baseline leg repeats the sample step for at least this long
 
 
 def cpu_sample_step(oracle, inp) -> tuple[int, float]:
-    """The bench step's recipe on a 2^22-cell oracle table; (ops, seconds)."""
+    """The bench step's recipe on a 2^23-cell oracle table; (ops, seconds)."""
     wl = inp["wl"]
     n05, n09 = wl["counts"][0.5], wl["counts"][0.9]
     ops = 0
@@ -555,9 +609,54 @@ def cpu_inputs():
     return {"wl": wl, "zipf": zipf}
 
 
-SAMPLE_DESC = ("the same step recipe at 2^22 cells: insert to load 0.5/0.9, 2^21 find hits + misses at "
-               "each load, 2^22 Zipf insertOrUpdate(add) per s over 2^20 keys, erase 2^21, migrate x2, "
-               "growable 2^12-cell table taking 2^21 inserts")
+SAMPLE_DESC = ("the same step recipe at 2^23 cells: insert to load 0.5/0.9, 2^22 find hits + misses at "
+               "each load, 2^23 Zipf insertOrUpdate(add) per s over 2^20 keys, erase 2^22, migrate x2, "
+               "growable 2^12-cell table taking 2^22 inserts")
+
+
+def host_cpu() -> dict:
+    """CPU model and logical core count of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+class PinnedToOneCore:
+    """Run the enclosed block with this process pinned to one core (the lowest
+    it may use), like `taskset -c <core>`; the oracle is single-threaded and
+    runs in this process.  The previous affinity is restored afterwards."""
+
+    def __enter__(self):
+        self.prev = None
+        self.core = None
+        if hasattr(os, "sched_getaffinity"):
+            try:
+                self.prev = os.sched_getaffinity(0)
+                self.core = min(self.prev)
+                os.sched_setaffinity(0, {self.core})
+            except OSError:
+                self.prev = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.prev is not None:
+            os.sched_setaffinity(0, self.prev)
 
 
 def cpu_baseline_once():
@@ -565,9 +664,14 @@ def cpu_baseline_once():
 
     oracle.build()
     inp = cpu_inputs()
-    ops, sec = cpu_sample_step(oracle, inp)
+    ops, sec, reps = 0, 0.0, 0
+    with PinnedToOneCore() as pin:
+        while sec < CPU_BASELINE_MIN_S and reps < 20:
+            o, t = cpu_sample_step(oracle, inp)
+            ops, sec, reps = ops + o, sec + t, reps + 1
     return {"value": round(ops / sec / 1e6, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": SAMPLE_DESC, "seconds": round(sec, 2)}
+            "sample": f"{reps} x " + SAMPLE_DESC, "seconds": round(sec, 2), "pinned_core": pin.core,
+            "compiler": "gcc -O3", **host_cpu()}
 
 
 def run_reference(args):
@@ -579,14 +683,15 @@ def run_reference(args):
 
     oracle.build()
     inp = cpu_inputs()
-    for _ in range(args.warmup):
-        cpu_sample_step(oracle, inp)
     tot_ops, tot_s, per = 0, 0.0, []
-    for _ in range(args.steps):
-        ops, sec = cpu_sample_step(oracle, inp)
-        tot_ops += ops
-        tot_s += sec
-        per.append(sec)
+    with PinnedToOneCore() as pin:
+        for _ in range(args.warmup):
+            cpu_sample_step(oracle, inp)
+        for _ in range(args.steps):
+            ops, sec = cpu_sample_step(oracle, inp)
+            tot_ops += ops
+            tot_s += sec
+            per.append(sec)
     value = tot_ops / tot_s / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
@@ -594,7 +699,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": {"workload": SAMPLE_DESC, "capacity_cells": 1 << CPU_LOG2C},
         "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": SAMPLE_DESC},
+                         "sample": SAMPLE_DESC, "pinned_core": pin.core, "compiler": "gcc -O3", **host_cpu()},
         "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -1088,7 +1193,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--partition", default="auto", choices=["auto", "off", "on"],
+                    help="table option for every table of the step: hash-partitioned execution of large "
+                         "batches (auto = the library's rule)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-reps", type=int, default=100)

@@ -106,7 +106,18 @@ typedef enum {
  * CHT_STATUS_RESERVED bit; 1 = the two keys are stored in two special slots
  * beside the table and behave like any other key (every operation, export,
  * and the live count of cht_size include them; they never occupy a cell and
- * migrations leave them alone). */
+ * migrations leave them alone).  partition: how a large batch meets a table
+ * larger than L2 (Sec. 4.5 "Bulk Operations": sort the batch by hash and
+ * co-partition it with the table): 0 (default) = automatic, 1 = never, 2 =
+ * always (tables of at least 256 cells, batches below 2^32 operations).  A
+ * partitioned call first reorders the batch by the top 8 bits of the hash
+ * (which 1/256 of the table each probe starts in), runs the operation over the
+ * reordered batch in order so the table lines in use stay in L2, and puts the
+ * results back into the caller's order; it takes about 19 bytes of
+ * stream-ordered device scratch per operation for the duration of the call.
+ * Results are the same either way.  Automatic: tables of at least 2^22 cells
+ * (64 MiB) and batches of at least 2^20 operations and a sixteenth of the
+ * capacity. */
 typedef struct {
     int group_width;
     int lane_cells;
@@ -116,6 +127,7 @@ typedef struct {
     int iou_aggregate;
     int reuse_tombstones;
     int full_key_space;
+    int partition;
 } cht_config;
 
 /* Create a table of at least `capacity` cells (rounded up to a power of two,

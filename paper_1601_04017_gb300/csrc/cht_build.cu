@@ -608,6 +608,9 @@ PlaceArgs place_args(const Cell* sorted, u64 n, u32 log2c, void* scratch, BuildE
 
 u64 build_scratch_bytes(u64 n) { return Layout(n).total; }
 
+u64 scan_partials(u64 m) { return (m + kScanChunk - 1) / kScanChunk; }
+cudaError_t scan_exclusive_u32(u32* data, u64 m, u32* part, cudaStream_t s) { return scan_exclusive(data, m, part, s); }
+
 cudaError_t launch_build_sort(const u64* keys, const u64* vals, u64 n, u32 log2c, int full_keys, void* scratch,
                               const Cell** sorted, BuildExtra** ex_out, cudaStream_t s) {
     const u32 B = build_sort_bits(log2c);

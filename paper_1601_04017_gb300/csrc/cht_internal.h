@@ -29,6 +29,11 @@ struct OpArgs {
     unsigned char* codes; // per-op result codes (nullable)
     u64 n;
     DevState* st;
+    // 0: each warp takes one contiguous slice of the batch; else warps take
+    // consecutive pieces of `chunk` operations in batch order (grid-stride),
+    // so the operations in flight at any moment are a narrow range of the
+    // batch (the hash-partitioned path relies on it)
+    u32 chunk = 0;
 };
 
 // Launch one batched operation. group_width in {1,2,4,8,16,32}; lane_cells
@@ -83,6 +88,28 @@ cudaError_t launch_build_count(const Cell* sorted, u64 n, u32 log2c, void* scrat
                                cudaStream_t s);
 cudaError_t launch_build_place(const Cell* sorted, u64 n, Cell* cells, u32 log2c, void* scratch, BuildExtra* ex,
                                DevState* st, const u64* vals, cudaStream_t s);
+
+// Exclusive scan of m u32 in place (three kernels); `part` holds
+// scan_partials(m) u32.
+u64 scan_partials(u64 m);
+cudaError_t scan_exclusive_u32(u32* data, u64 m, u32* part, cudaStream_t s);
+
+// Hash-partitioned execution of one large batch (cht_bulk.cu, Sec. 4.5): the
+// operations are reordered by the top 8 bits of their hash (the home slot's
+// top bits, i.e. which 1/256 of the table they touch), the operation kernel
+// runs over them in that order, and the per-operation results are put back
+// into the caller's order.  `run` launches the operation kernel on the
+// reordered arguments it is given.  Scratch: partition_scratch_bytes(n, ...)
+// bytes, 256-byte aligned.
+struct PartitionIO {
+    bool vals;       // the operation reads a value per key
+    bool vals_out;   // it writes a found value per key (find)
+    bool codes;      // it writes a result code per key
+};
+u64 partition_scratch_bytes(u64 n, PartitionIO io);
+typedef cudaError_t (*PartitionRun)(const OpArgs& a, void* ctx, cudaStream_t s);
+cudaError_t launch_partitioned(const OpArgs& a, PartitionIO io, void* scratch, PartitionRun run, void* ctx,
+                               cudaStream_t s);
 
 // Compact the live cells into keys_out / vals_out (max_n entries); the count
 // lands in st->export_pos, which must be zero on entry.
@@ -214,5 +241,9 @@ namespace cht {
 // effective width a find would use now.
 void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int* device,
                 int* group_width, int* lane_cells, int* ctas_per_sm, int* full_keys);
+
+// Record the stream of a call's work on the table, as every entry point does:
+// cht_destroy and later migrations order the release of the cells after it.
+void table_note_stream(cht_table* h, cudaStream_t s);
 
 }  // namespace cht

@@ -68,6 +68,9 @@ extern "C" cht_status cht_find_noalloc(cht_handle h, const uint64_t* keys, uint6
     cht_status r = CHT_OK;
     unsigned char* base = nullptr;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the find reads the cells on s: cht_destroy (and a migration that frees
+    // the cells) must order itself after it, as after every other call
+    cht::table_note_stream(h, s);
     if ((r = scratch_address(device, &base)) == CHT_OK) {
         cht::u64* s_keys = reinterpret_cast<cht::u64*>(base);
         cht::u64* s_vals = s_keys + kNoallocMaxKeys;

@@ -511,15 +511,18 @@ __device__ __forceinline__ void pdl_enter() {
 template <int G, int V, int MODE, int kFlags>
 __global__ void __launch_bounds__(kOpBlock, op_min_blocks<G, V>()) op_kernel(OpArgs a) {
     pdl_enter();
-    // each warp owns a contiguous slice of the batch
+    // each warp owns a contiguous slice of the batch, or (a.chunk != 0) the
+    // pieces warp, warp + nwarps, ... of a.chunk operations each, so that the
+    // whole grid moves through the batch in order
     const u64 warp = (u64(blockIdx.x) * kOpBlock + threadIdx.x) >> 5;
     const u64 nwarps = (u64(gridDim.x) * kOpBlock) >> 5;
-    const u64 per = (a.n + nwarps - 1) / nwarps;
-    const u64 begin = warp * per;
-    const u64 end = begin + per < a.n ? begin + per : a.n;
+    const u64 per = a.chunk ? u64(a.chunk) : (a.n + nwarps - 1) / nwarps;
     u64 n_ins = 0, n_del = 0;
     u32 sbits = 0;
-    warp_ops<G, V, MODE, false, false, kFlags>(a, begin, end, n_ins, n_del, sbits);
+    for (u64 begin = warp * per; begin < a.n; begin += nwarps * per) {
+        const u64 end = begin + per < a.n ? begin + per : a.n;
+        warp_ops<G, V, MODE, false, false, kFlags>(a, begin, end, n_ins, n_del, sbits);
+    }
     warp_flush_counters(a.st, n_ins, n_del, sbits);
 }
 

@@ -170,6 +170,7 @@ cht_config default_config() {
     c.iou_aggregate = 1;
     c.reuse_tombstones = 0;
     c.full_key_space = 0;
+    c.partition = 0;
     return c;
 }
 
@@ -185,6 +186,7 @@ bool valid_config(const cht_config& c) {
     if (c.iou_aggregate < 0 || c.iou_aggregate > 2) return false;
     if (c.reuse_tombstones < 0 || c.reuse_tombstones > 1) return false;
     if (c.full_key_space < 0 || c.full_key_space > 1) return false;
+    if (c.partition < 0 || c.partition > 2) return false;
     return true;
 }
 
@@ -328,6 +330,46 @@ Width pick_width(const cht_table* h, cht::Mode mode, u64 n) {
     return w;
 }
 
+// Operations per in-order piece of a warp on a partitioned batch: the grid
+// then has about (resident warps x kOrderedChunk) operations in flight, a
+// narrow range of the reordered batch and so of the table.
+constexpr u32 kOrderedChunk = 64;
+
+bool aggregated(const cht_table* h, cht::Mode mode) {
+    return (mode == cht::kIouAdd || mode == cht::kIouOverwrite || mode == cht::kUpdAdd ||
+            mode == cht::kUpdOverwrite) &&
+           h->cfg.iou_aggregate != 0;
+}
+
+// The hash-partitioned path (Sec. 4.5): for batches that touch much of a
+// table too large for L2.  Automatic rule: at least 2^22 cells (64 MiB), at
+// least 2^20 operations and a sixteenth of the capacity.
+bool use_partition(const cht_table* h, u64 n) {
+    if (h->cfg.partition == 1 || n >= (1ull << 32) || h->log2c < 8) return false;
+    if (h->cfg.partition == 2) return true;
+    return h->log2c >= 22 && n >= (1ull << 20) && n >= (h->cap() >> 4);
+}
+
+struct KernelCtx {
+    const cht_table* h;
+    cht::Mode mode;
+    u64 n;  // batch size for the width choice
+};
+
+cudaError_t run_kernel(const cht::OpArgs& a, void* ctx, cudaStream_t s) {
+    const KernelCtx* k = static_cast<const KernelCtx*>(ctx);
+    if (aggregated(k->h, k->mode))
+        return cht::launch_iou_aggregated(k->mode, a, k->h->cfg.iou_aggregate == 2, k->h->cfg.ctas_per_sm, s);
+    const Width w = pick_width(k->h, k->mode, k->n);
+    return cht::launch_op(k->mode, a, w.g, w.v, k->h->cfg.ctas_per_sm, s);
+}
+
+cudaError_t run_kernel_ordered(const cht::OpArgs& a, void* ctx, cudaStream_t s) {
+    cht::OpArgs b = a;
+    b.chunk = kOrderedChunk;  // (the aggregation kernel walks its windows in order anyway)
+    return run_kernel(b, ctx, s);
+}
+
 cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals, u64* vals_out,
                   unsigned char* codes, u64 n, cudaStream_t s) {
     cht::OpArgs a;
@@ -341,11 +383,20 @@ cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals
     a.codes = codes;
     a.n = n;
     a.st = h->st;
-    if ((mode == cht::kIouAdd || mode == cht::kIouOverwrite || mode == cht::kUpdAdd || mode == cht::kUpdOverwrite) &&
-        h->cfg.iou_aggregate)
-        return cuda_status(cht::launch_iou_aggregated(mode, a, h->cfg.iou_aggregate == 2, h->cfg.ctas_per_sm, s));
-    const Width w = pick_width(h, mode, n);
-    return cuda_status(cht::launch_op(mode, a, w.g, w.v, h->cfg.ctas_per_sm, s));
+    KernelCtx ctx{h, mode, n};
+    if (n == 0) return CHT_OK;
+    if (!use_partition(h, n)) return cuda_status(run_kernel(a, &ctx, s));
+    cht::PartitionIO io;
+    io.vals = cht::mode_has_vals(mode);
+    io.vals_out = vals_out != nullptr;
+    io.codes = codes != nullptr;
+    const u64 bytes = cht::partition_scratch_bytes(n, io);
+    void* scratch = nullptr;
+    cht_status r = lib_alloc(&scratch, bytes, s);
+    if (r != CHT_OK) return r;
+    const cudaError_t e = cht::launch_partitioned(a, io, scratch, run_kernel_ordered, &ctx, s);
+    lib_free(scratch, bytes, s);
+    return cuda_status(e);
 }
 
 // insert / insert_or_update with the growth policy of growable tables.
@@ -631,6 +682,8 @@ void table_view(const cht_table* h, Cell** cells, u32* log2c, DevState** st, int
     *ctas_per_sm = h->cfg.ctas_per_sm;
     *full_keys = h->cfg.full_key_space;
 }
+
+void table_note_stream(cht_table* h, cudaStream_t s) { h->last = s; }
 
 }  // namespace cht
 

@@ -143,3 +143,34 @@ def test_hash_full_avalanche(oracle_mod):
         worst = max(worst, float(np.abs(p - 0.5).max()))
     # binomial sd at n = 4096 is 0.0078; 0.05 is > 6 sd
     assert worst < 0.05, worst
+
+
+# MurmurHash3's fmix64 multipliers and their published inverses modulo 2^64
+# (the pair used to invert the finalizer).  The test below runs the inverse
+# written with the INVERSE constants, so it does not restate the oracle's
+# forward formula: a changed multiplier or shift in the oracle's hash makes
+# hash(unfmix(h)) differ from h.
+_FMIX_M1, _FMIX_M2 = 0xFF51AFD7ED558CCD, 0xC4CEB9FE1A85EC53
+_FMIX_INV1, _FMIX_INV2 = 0x4F74430C22A54005, 0x9CB4B2F8129337DB
+
+
+def _unfmix64(h: int) -> int:
+    m = (1 << 64) - 1
+    x = h
+    x ^= x >> 33
+    x = (x * _FMIX_INV2) & m
+    x ^= x >> 33
+    x = (x * _FMIX_INV1) & m
+    x ^= x >> 33
+    return x
+
+
+def test_hash_is_murmur3_fmix64_fixed_vectors(oracle_mod):
+    assert (_FMIX_M1 * _FMIX_INV1) % (1 << 64) == 1
+    assert (_FMIX_M2 * _FMIX_INV2) % (1 << 64) == 1
+    outs = [0, 1, 2, 3, 0x8000000000000000, 0x0123456789ABCDEF, 0xFEDCBA9876543210,
+            0xFFFFFFFFFFFFFFFF, 0xDEADBEEFCAFEBABE, 1 << 32, (1 << 32) - 1, 0x5555555555555555]
+    ins = np.array([_unfmix64(h) for h in outs], dtype=np.uint64)
+    got = oracle_mod.hash64(ins)
+    assert [int(x) for x in got] == outs
+    assert int(ins[0]) == 0  # the finalizer fixes 0

@@ -48,10 +48,14 @@ def test_find_noalloc_matches_find(cuda_lib):
         # allocation-free entry point (host arrays, staged through its scratch)
         got_v = np.full(n, 7, np.uint64)
         got_f = np.full(n, 9, np.uint8)
+        torch.cuda.synchronize()
         before = cuda_lib.memory_in_use()
+        free_before = torch.cuda.mem_get_info()[0]
         assert _lib_call(lib, t, q, got_v, got_f, stream) == cuda_lib.CHT_OK
         torch.cuda.synchronize()
         assert cuda_lib.memory_in_use() == before
+        if call > 0:  # after the first call (module and scratch set up): no device bytes taken at all
+            assert torch.cuda.mem_get_info()[0] == free_before
         assert np.array_equal(got_v, ref_v.cpu().numpy().view(np.uint64))
         assert np.array_equal(got_f, ref_f.cpu().numpy())
         assert (got_f[: n // 2] == 1).all() and got_f[-1] == 3
@@ -66,3 +70,31 @@ def test_find_noalloc_matches_find(cuda_lib):
     out_v = np.zeros(big.size, np.uint64)
     assert _lib_call(lib, t, big, out_v, None, stream) == cuda_lib.CHT_ERR_INVALID_ARG
     t.destroy()
+
+
+def test_find_noalloc_orders_destroy(cuda_lib):
+    """A table destroyed right after an allocation-free find issued on another
+    stream is released only once that find has finished: cht_destroy waits for
+    the stream of the table's last call, and the find counts as one."""
+    import torch
+
+    c = 1 << 18
+    keys = W.uniform_keys(100_000, seed=92)
+    vals = W.values_for(keys)
+    t = cuda_lib.Table(c)
+    t.insert(torch.from_numpy(keys.view(np.int64)).cuda(), torch.from_numpy(vals.view(np.int64)).cuda())
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    n = cuda_lib.cht.NOALLOC_MAX_KEYS
+    dq = torch.from_numpy(keys[:n].view(np.int64)).cuda()
+    dv = torch.zeros(n, dtype=torch.int64, device="cuda")
+    df = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(2_000_000)  # keep the side stream busy, so the find is still queued
+        cuda_lib.cht.find_noalloc(t, dq, dv, df, stream=side)
+    t.destroy()
+    assert side.query(), "cht_destroy returned before the find on the other stream finished"
+    torch.cuda.synchronize()
+    assert np.array_equal(dv.cpu().numpy().view(np.uint64), vals[:n])
+    assert (df.cpu().numpy() == 1).all()
