@@ -457,6 +457,27 @@ def load_half_fractions(breakdown, peak):
     return out
 
 
+def pinned_copy_gbs(nbytes: int = 1 << 32) -> dict:
+    """Plain cudaMemcpyAsync bandwidth between pinned host memory and the
+    device on this machine (one 4 GiB copy each way, after one warm-up)."""
+    import torch
+
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    out = {}
+    for name, dst, src in (("h2d", d, h), ("d2h", h, d)):
+        dst.copy_(src, non_blocking=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        dst.copy_(src, non_blocking=True)
+        b.record(s)
+        b.synchronize()
+        out[name] = round(nbytes / (a.elapsed_time(b) * 1e-3) / 1e9, 1)
+    del h, d
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -466,7 +487,7 @@ def run_gpu(args):
 
     cht.load_library()
     inp = make_inputs("cuda")
-    pmode = {"auto": 0, "off": 1, "on": 2}[args.partition]
+    pmode = {"off": 0, "on": 1}[args.partition]
     runner = StepRunner(cht, inp, partition=pmode)
     for _ in range(args.warmup):
         runner.step()
@@ -527,7 +548,8 @@ def run_gpu(args):
         el = time.perf_counter() - t0
         el = max_over_ranks(pg, el, device="cuda")
         e2e = {"value": round(hrunner.ops_per_step * max(1, args.e2e_steps) * world / el / 1e6, 1),
-               "unit": UNIT, "h2d_bytes_per_step": hrunner.h2d, "d2h_bytes_per_step": hrunner.d2h}
+               "unit": UNIT, "h2d_bytes_per_step": hrunner.h2d, "d2h_bytes_per_step": hrunner.d2h,
+               "steps": max(1, args.e2e_steps), "pinned_copy_gbs": pinned_copy_gbs()}
         del hrunner
 
     lat = latency_percentiles(cht, inp, args.latency_reps) if args.latency_reps > 0 else None
@@ -718,6 +740,7 @@ def run_case(args):
     cht.load_library()
     log2c, load = args.case_log2c, args.case_load
     c = 1 << log2c
+    tcfg = {"partition": {"off": 0, "on": 1}[args.partition]}
     s = torch.cuda.current_stream()
 
     def tm(fn):
@@ -728,13 +751,13 @@ def run_case(args):
         b.synchronize()
         return round(a.elapsed_time(b), 4)
 
-    out = {"case": args.case, "log2c": log2c, "load": load}
+    out = {"case": args.case, "log2c": log2c, "load": load, "partition": args.partition}
     if args.case == "shrink":
         # the same shrink once untimed, so the timed one does not include the
         # memory pool's first growth to these sizes
         wl = W.bounded_workload(log2c, loads=(load,), n_find=c // 2, backend="cuda")
         n = wl["counts"][load]
-        t = cht.Table(c)
+        t = cht.Table(c, config=tcfg)
         t.insert(wl["keys"][:n], wl["vals"][:n])
         t.erase(wl["keys"][: n - n // 8])
         t.migrate(c // 4)
@@ -743,7 +766,7 @@ def run_case(args):
     if args.case in ("find", "insert", "migrate", "shrink"):
         wl = W.bounded_workload(log2c, loads=(load,), n_find=c // 2, backend="cuda")
         n = wl["counts"][load]
-        t = cht.Table(c)
+        t = cht.Table(c, config=tcfg)
         codes = torch.empty(n, dtype=torch.uint8, device="cuda")
         out["insert_ms"] = tm(lambda: t.insert(wl["keys"][:n], wl["vals"][:n], codes))
         if args.case == "find":
@@ -767,7 +790,7 @@ def run_case(args):
         wl = W.bounded_workload(log2c, loads=(load,), n_find=1 << 20, backend="cuda")
         n = wl["counts"][load]
         k, v = wl["keys"][:n], wl["vals"][:n]
-        t = cht.Table(c)
+        t = cht.Table(c, config=tcfg)
         for timed in (False, True):
             t.clear()
             ms_b = tm(lambda: t.build(k, v))
@@ -804,7 +827,7 @@ def run_case(args):
         # c/2 operations per run draw keys Zipf(s) over those N ranks.
         nr = c // 4
         present = W.rank_to_key(torch.arange(1, nr + 1, dtype=torch.int64, device="cuda"), backend="cuda")
-        t = cht.Table(c)
+        t = cht.Table(c, config=tcfg)
         t.insert(present, present)
         vout = torch.empty(c // 2, dtype=torch.int64, device="cuda")
         codes = torch.empty(c // 2, dtype=torch.uint8, device="cuda")
@@ -822,7 +845,7 @@ def run_case(args):
         z = W.zipf_keys(c, args.case_s, min(ZIPF_RANKS, c // 4), W.SEED_ZIPF, backend="cuda")
         ones = torch.ones(c, dtype=torch.int64, device="cuda")
         codes = torch.empty(c, dtype=torch.uint8, device="cuda")
-        t = cht.Table(c)
+        t = cht.Table(c, config=tcfg)
         out["iou_ms"] = tm(lambda: t.insert_or_update(z, ones, cht.ADD, codes))
         t.destroy()
     elif args.case == "window":
@@ -1130,10 +1153,23 @@ def run_serving(args):
                                     vp + 8 * o if op in (W.OP_INSERT, W.OP_IOU_ADD) else None, n,
                                     op_ + 8 * o if op == W.OP_FIND else None, cp + o))
 
-    def run(arrivals):
+    def fresh_tables():
         tables = [cht.Table(1024, growable=True) for _ in range(256)]
         for t in tables:
             t.set_config(reuse_tombstones=args.serving_reuse_tombstones)
+        return tables
+
+    def contents(tables):
+        out = []
+        for t in tables:
+            k, v = t.export()
+            k, v = k.cpu().numpy().view(np.uint64), v.cpu().numpy().view(np.uint64)
+            o = np.argsort(k)
+            out.append((k[o], v[o]))
+        return out
+
+    def run(arrivals, keep=False):
+        tables = fresh_tables()
         srv = cht.Server(tables, memory_cap_bytes=64 << 30, arena_bytes=1 << 30, max_inflight_steps=2,
                          stage_inputs=args.serving_stage_inputs)
         lat, mk = srv.replay(reqs, arrivals)
@@ -1142,10 +1178,74 @@ def run_serving(args):
         prof["trace"] = srv.trace()
         grown = sum(t.size()[2] for t in tables) * 16
         srv.destroy()
+        if keep:
+            prof["contents"] = contents(tables)
         for t in tables:
             t.destroy()
         torch.cuda.synchronize()
         return lat, mk, steps, done, grown, prof
+
+    # The baseline: the same requests as single calls (one cht_* call per
+    # request, in arrival order, each waiting for its arrival time), results in
+    # their own arrays.  Latency = completion (a CUDA event after the call)
+    # minus arrival.
+    base_vout, base_codes = buf(torch.int64), buf(torch.uint8)
+    s_cur = torch.cuda.current_stream()
+
+    def single_calls(arrivals):
+        tables = fresh_tables()
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(nreq)]
+        ev0 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev0.record(s_cur)
+        for r in range(nreq):
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[r]:
+                    pass
+            o, n, op = int(wl["offsets"][r]), int(wl["n"][r]), int(wl["op"][r])
+            t = tables[int(wl["table"][r])]
+            k = keys_h[o:o + n]
+            if op == W.OP_FIND:
+                t.find(k, base_vout[o:o + n], base_codes[o:o + n])
+            elif op == W.OP_INSERT:
+                t.insert(k, vals_h[o:o + n], base_codes[o:o + n])
+            elif op == W.OP_IOU_ADD:
+                t.insert_or_update(k, vals_h[o:o + n], cht.ADD, base_codes[o:o + n])
+            else:
+                t.erase(k, base_codes[o:o + n])
+            ends[r].record(s_cur)
+        torch.cuda.synchronize()
+        mk = time.perf_counter() - t0
+        done_s = np.array([ev0.elapsed_time(e) * 1e-3 for e in ends])
+        lat = done_s - (arrivals if arrivals is not None else 0.0)
+        res = {"contents": contents(tables)}
+        for t in tables:
+            t.destroy()
+        return lat, mk, res
+
+    def same_results(served_vout, served_codes, served_contents, base_contents):
+        """Finds bit-exact per operation; insert / insertOrUpdate / erase codes
+        summed per (request, key) (which of equal keys in a request reports
+        the change is free); every final table equal."""
+        ops = wl["op"]
+        rid = np.repeat(np.arange(nreq), wl["n"])
+        is_find = ops[rid] == W.OP_FIND
+        sv, sc = served_vout.cpu().numpy(), served_codes.cpu().numpy()
+        bv, bc = base_vout.cpu().numpy(), base_codes.cpu().numpy()
+        if not (np.array_equal(sv[is_find], bv[is_find]) and np.array_equal(sc[is_find], bc[is_find])):
+            return False
+        m = ~is_find
+        kk = keys_h.cpu().numpy().view(np.uint64)[m]
+        rr = rid[m]
+        order = np.lexsort((kk, rr))
+        kk, rr = kk[order], rr[order]
+        starts = np.concatenate([[0], np.nonzero((kk[1:] != kk[:-1]) | (rr[1:] != rr[:-1]))[0] + 1])
+        if not np.array_equal(np.add.reduceat(sc[m][order].astype(np.int64), starts),
+                              np.add.reduceat(bc[m][order].astype(np.int64), starts)):
+            return False
+        return all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+                   for a, b in zip(served_contents, base_contents))
 
     def breakdown(prof, mk, name):
         tr = prof["trace"]
@@ -1159,9 +1259,10 @@ def run_serving(args):
                 "engine_us_per_round_p50_p90": [round(float(np.percentile(per_round, q)), 2) for q in (50, 90)],
                 "recut_steps": int(tr["recut"].sum()), "largest_table_log2": int(tr["max_table_log2"].max())}
 
-    lat0, mk0, steps0, done0, grown, prof0 = run(np.zeros(nreq))
+    lat0, mk0, steps0, done0, grown, prof0 = run(np.zeros(nreq), keep=True)
     assert done0 == nreq
     cap_rps = nreq / mk0
+    cap_vout, cap_codes = vout_h.clone(), codes_h.clone()
     out = {"workload": "serving: 256 growable tables (key universes log-uniform 2^10..2^24), requests of 1..65536 "
                        "ops (log-uniform), table ~ Zipf(1.0), find/insert/insertOrUpdate(add)/erase "
                        f"{'/'.join(str(round(100 * x)) for x in args.serving_mix)}, "
@@ -1184,6 +1285,22 @@ def run_serving(args):
                                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
                                "max_ms": round(float(lat.max()) * 1e3, 3),
                                "time": breakdown(prof, mk, f"load_{frac}")}
+    if not args.no_serving_baseline:
+        blat, bmk, bres = single_calls(None)
+        same = same_results(cap_vout, cap_codes, prof0["contents"], bres["contents"])
+        out["single_calls"] = {"what": "the same requests, one cht_* call each in arrival order (no server)",
+                               "capacity": {"makespan_s": round(bmk, 4), "mops": round(total / bmk / 1e6, 1),
+                                            "requests_per_s": round(nreq / bmk, 1),
+                                            "p50_ms": round(float(np.percentile(blat, 50)) * 1e3, 3),
+                                            "p99_ms": round(float(np.percentile(blat, 99)) * 1e3, 3)},
+                               "results_equal_served": bool(same)}
+        for frac in args.serving_loads:
+            arr = W.poisson_arrivals(nreq, frac * cap_rps)
+            blat, bmk, _ = single_calls(arr)
+            out["single_calls"][f"load_{frac}"] = {
+                "offered_requests_per_s": round(frac * cap_rps, 1), "makespan_s": round(bmk, 4),
+                "mops": round(total / bmk / 1e6, 1), "p50_ms": round(float(np.percentile(blat, 50)) * 1e3, 3),
+                "p99_ms": round(float(np.percentile(blat, 99)) * 1e3, 3)}
     print(json.dumps(out), flush=True)
 
 
@@ -1194,9 +1311,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--partition", default="auto", choices=["auto", "off", "on"],
-                    help="table option for every table of the step: hash-partitioned execution of large "
-                         "batches (auto = the library's rule)")
+    ap.add_argument("--partition", default="off", choices=["off", "on"],
+                    help="table option for every table of the step: hash-partitioned execution of the batches")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-reps", type=int, default=100)
@@ -1225,6 +1341,8 @@ def main():
                     help="table option: inserts take the first tombstone on their path")
     ap.add_argument("--serving-mix", type=float, nargs=4, default=[0.5, 0.3, 0.15, 0.05],
                     help="find / insert / insertOrUpdate(add) / erase fractions of the requests")
+    ap.add_argument("--no-serving-baseline", action="store_true",
+                    help="skip the single-call baseline of the serving workload")
     ap.add_argument("--serving-trace", default="",
                     help="save each run's per-step server trace to <prefix>_<run>.npy")
     ap.add_argument("--serving-arrays", default="pinned", choices=["pinned", "device"],

@@ -106,18 +106,18 @@ typedef enum {
  * CHT_STATUS_RESERVED bit; 1 = the two keys are stored in two special slots
  * beside the table and behave like any other key (every operation, export,
  * and the live count of cht_size include them; they never occupy a cell and
- * migrations leave them alone).  partition: how a large batch meets a table
- * larger than L2 (Sec. 4.5 "Bulk Operations": sort the batch by hash and
- * co-partition it with the table): 0 (default) = automatic, 1 = never, 2 =
- * always (tables of at least 256 cells, batches below 2^32 operations).  A
- * partitioned call first reorders the batch by the top 8 bits of the hash
- * (which 1/256 of the table each probe starts in), runs the operation over the
- * reordered batch in order so the table lines in use stay in L2, and puts the
- * results back into the caller's order; it takes about 19 bytes of
- * stream-ordered device scratch per operation for the duration of the call.
- * Results are the same either way.  Automatic: tables of at least 2^22 cells
- * (64 MiB) and batches of at least 2^20 operations and a sixteenth of the
- * capacity. */
+ * migrations leave them alone).  partition: 1 = run a batch hash-partitioned
+ * (Sec. 4.5 "Bulk Operations": sort the batch by hash and co-partition it
+ * with the table; tables of at least 256 cells, batches below 2^32
+ * operations): the batch is first reordered by the top 8 bits of the hash
+ * (which 1/256 of the table each probe starts in), the operation runs over
+ * the reordered batch in order so the table lines in use stay in L2, and the
+ * results are put back into the caller's order; about 19 bytes of
+ * stream-ordered device scratch per operation for the call.  0 (default) =
+ * the direct kernel.  Results are the same either way.  Measured on GB300
+ * (2^26 cells, 2^25 operations): the reorder and the gather cost about 16 ns
+ * per operation, more than the L2 locality saves except for misses at load
+ * 0.9 (4.46 vs 4.97 ms), so it is off by default. */
 typedef struct {
     int group_width;
     int lane_cells;
@@ -167,6 +167,27 @@ cht_status cht_insert(cht_handle h, const uint64_t *keys, const uint64_t *vals, 
  * then synchronizes `stream` once).  keys / vals: n u64 each, host or device;
  * the scratch (about 32 B per pair) is freed stream-ordered. */
 cht_status cht_build(cht_handle h, const uint64_t *keys, const uint64_t *vals, uint64_t n,
+                     cht_stream_t stream);
+
+/* Bulk merge of a batch into a table that may hold elements (Sec. 4.5: sort
+ * the batch by hash, keep the last of equal keys, and merge batch and table
+ * into a new table).  The new table is the sorted placement of the table's
+ * live elements, in cell index order, followed by the batch in input order:
+ * ordered by the top B hash bits as in cht_build (ties in that order), all
+ * but the last of equal keys dropped -- so a batch element replaces the
+ * table's element of the same key and the last of equal batch keys wins --
+ * and placed as inserting them one by one in that order would; tombstones are
+ * dropped.  The layout is deterministic given the table's cells.  A growable
+ * table takes the smallest capacity >= c with live + n <= alpha * c'; a
+ * bounded one keeps c and returns CHT_ERR_TABLE_FULL, table unchanged, if no
+ * empty cell would remain.  Keys 0 / ~0 of the batch: the special slots (last
+ * value) with the full key space on, else skipped with the RESERVED status
+ * bit; slots the batch does not name keep their content.  live + n < 2^32.
+ * The call reads the live count back (one synchronization of `stream`);
+ * scratch of about 48 B per element of the concatenation plus the new cells
+ * are allocated stream-ordered, the old cells freed stream-ordered.  keys /
+ * vals: n u64 each, host or device. */
+cht_status cht_merge(cht_handle h, const uint64_t *keys, const uint64_t *vals, uint64_t n,
                      cht_stream_t stream);
 
 /* find (Sec. 3 "Lookup", copy semantics): vals_out[i] = the value stored
@@ -345,8 +366,12 @@ cht_status cht_plan_destroy(cht_plan_handle p);
  * migrated, stream-ordered, to the smallest capacity that holds them all.  A
  * request larger than a step (max_step_ops) or than the free arena is
  * admitted in parts; later requests on its table wait for the rest.
- * Admission keeps the tables plus the arena within memory_cap_bytes; a
- * request whose table can never fit is rejected (CHT_ERR_OOM). */
+ * Admission keeps the tables plus the arena within memory_cap_bytes and every
+ * growth within the device's free memory: before a step grows a table it asks
+ * the device for its free bytes (cudaMemGetInfo, plus what the stream-ordered
+ * pool holds unused) and admits the growth only if hbm_reserve_bytes remain
+ * free afterwards; otherwise the table's requests wait for steps in flight to
+ * finish.  A request whose table can never fit is rejected (CHT_ERR_OOM). */
 typedef struct cht_server *cht_server_handle;
 
 typedef struct {
@@ -361,6 +386,8 @@ typedef struct {
                                     pageable-memory access -- NVLink-C2C on Grace) in
                                     place and stages only the others through the
                                     arena; 1: stage every request through the arena */
+    uint64_t hbm_reserve_bytes;  /* device memory to leave free when admitting a
+                                    growth (0 = 1 GiB) */
 } cht_server_config;
 
 /* A request's arrays must stay alive and unchanged until it completes, and

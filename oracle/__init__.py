@@ -64,6 +64,7 @@ def _load():
             "or_migrate": (ctypes.c_int, [p, u64]),
             "or_insert": (None, [p, p, p, u64, p]),
             "or_build": (ctypes.c_int, [p, p, p, u64]),
+            "or_merge": (ctypes.c_int, [p, p, p, u64]),
             "or_build_sort_bits": (ctypes.c_uint, [ctypes.c_uint]),
             "or_insert_or_update": (None, [p, p, p, u64, ctypes.c_int, p]),
             "or_update": (None, [p, p, p, u64, ctypes.c_int, p]),
@@ -186,6 +187,19 @@ class OracleTable:
         k, v = _u64(keys), _u64(vals)
         assert k.shape == v.shape
         return int(self._lib.or_build(self._t, _ptr(k), _ptr(v), k.size))
+
+    def merge(self, keys, vals) -> int:
+        """Bulk merge of a batch into this (possibly non-empty) table (Sec. 4.5).
+
+        The new table is the sorted placement of the live elements (cell index
+        order) followed by the batch, keeping the last of equal keys: batch
+        values replace the table's, the last of equal batch keys wins.
+        0 = merged; 1 = merged, reserved keys skipped; -2 = no empty cell would
+        remain (table unchanged); -1 = out of memory.
+        """
+        k, v = _u64(keys), _u64(vals)
+        assert k.shape == v.shape
+        return int(self._lib.or_merge(self._t, _ptr(k), _ptr(v), k.size))
 
     def insert_or_update(self, keys, vals, op: int = ADD) -> np.ndarray:
         k, v = _u64(keys), _u64(vals)

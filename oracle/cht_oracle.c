@@ -557,6 +557,70 @@ int or_load_cells(or_table *t, const uint64_t *cells, uint64_t c)
     return 0;
 }
 
+/* Bulk merge of a batch into a non-empty table (Sec. 4.5: integer-sort the
+ * batch by hash, keep the last of equal keys, and merge batch and table into
+ * a new table, each element placed from max(home, previous position) on).
+ * Reading taken here (the paper's text stops mid-sentence): the new table is
+ * the sorted placement of the table's live elements followed by the batch --
+ * the table's elements in cell index order, then the batch in input order,
+ * ordered by the top B hash bits with ties in that order, all but the last of
+ * equal keys dropped (so a batch element replaces the table's element of the
+ * same key, and the last of equal batch elements wins), placed as or_build
+ * places them.  Tombstones are dropped (a new table).  Capacity: a growable
+ * table takes the smallest power of two c' >= c with live + n <= floor(alpha
+ * c'); a bounded table keeps c.  Keys 0 / ~0 of the batch: the special slots
+ * (last value) with the full key space on, else skipped (result 1); slots the
+ * batch does not touch keep their content.  -2: no empty cell would remain
+ * (table unchanged); -1: out of memory (unchanged). */
+int or_merge(or_table *t, const uint64_t *keys, const uint64_t *vals, uint64_t n)
+{
+    const uint64_t live = t->I - t->D, tot = live + n;
+    uint64_t *k = (uint64_t *)malloc((tot ? tot : 1) * sizeof(uint64_t));
+    uint64_t *v = (uint64_t *)malloc((tot ? tot : 1) * sizeof(uint64_t));
+    or_table *nt = or_create(t->cap, t->growable, t->alpha);
+    if (!k || !v || !nt) {
+        free(k);
+        free(v);
+        or_destroy(nt);
+        return -1;
+    }
+    nt->full_keys = t->full_keys;
+    nt->reuse_tombstones = t->reuse_tombstones;
+    uint64_t m = 0;
+    for (uint64_t i = 0; i < t->cap; ++i) {
+        const uint64_t key = t->cells[i].key;
+        if (key == OR_EMPTY || key == OR_TOMB) continue;
+        k[m] = key;
+        v[m] = t->cells[i].val;
+        ++m;
+    }
+    for (uint64_t j = 0; j < n; ++j, ++m) {
+        k[m] = keys[j];
+        v[m] = vals[j];
+    }
+    const int r = or_build(nt, k, v, m);
+    free(k);
+    free(v);
+    if (r < 0) {
+        or_destroy(nt);
+        return r;
+    }
+    free(t->cells);
+    t->cells = nt->cells;
+    t->cap = nt->cap;
+    t->log2c = nt->log2c;
+    t->I = nt->I;
+    t->D = 0;
+    t->probes += nt->probes;
+    for (int sl = 0; sl < 2; ++sl)
+        if (nt->sp_present[sl]) {
+            t->sp_present[sl] = 1;
+            t->sp_val[sl] = nt->sp_val[sl];
+        }
+    free(nt);
+    return r;
+}
+
 static int cmp_u64(const void *a, const void *b)
 {
     uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;

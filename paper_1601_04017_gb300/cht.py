@@ -63,7 +63,8 @@ class BatchOp(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("memory_cap_bytes", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64),
                 ("max_inflight_steps", ctypes.c_uint32), ("max_step_requests", ctypes.c_uint32),
-                ("max_step_ops", ctypes.c_uint64), ("stage_inputs", ctypes.c_int)]
+                ("max_step_ops", ctypes.c_uint64), ("stage_inputs", ctypes.c_int),
+                ("hbm_reserve_bytes", ctypes.c_uint64)]
 
 
 class Request(ctypes.Structure):
@@ -112,6 +113,7 @@ def load_library(build: bool = True):
             "cht_get_config": (i32, [p, ctypes.POINTER(ChtConfig)]),
             "cht_insert": (i32, [p, p, p, u64, p, p]),
             "cht_build": (i32, [p, p, p, u64, p]),
+            "cht_merge": (i32, [p, p, p, u64, p]),
             "cht_find": (i32, [p, p, u64, p, p, p]),
             "cht_insert_or_update": (i32, [p, p, p, u64, i32, p, p]),
             "cht_update": (i32, [p, p, p, u64, i32, p, p]),
@@ -263,6 +265,13 @@ class Table:
         vp, _, _ = _ptr(vals, 8, n, "vals")
         _check(self._lib.cht_build(self._h, kp, vp, n, _stream(stream)), "cht_build")
 
+    def merge(self, keys, vals, stream=None):
+        """Bulk merge of a batch into this table (Sec. 4.5): batch values replace
+        the table's, the last of equal batch keys wins; a new, sorted layout."""
+        kp, n, _ = _ptr(keys, 8, what="keys")
+        vp, _, _ = _ptr(vals, 8, n, "vals")
+        _check(self._lib.cht_merge(self._h, kp, vp, n, _stream(stream)), "cht_merge")
+
     def find(self, keys, vals_out, found=None, stream=None):
         kp, n, _ = _ptr(keys, 8, what="keys")
         vp, _, _ = _ptr(vals_out, 8, n, "vals_out")
@@ -409,11 +418,11 @@ class Server:
     """
 
     def __init__(self, tables, memory_cap_bytes=0, arena_bytes=0, max_inflight_steps=0, max_step_requests=0,
-                 max_step_ops=0, stage_inputs=0, stream=None):
+                 max_step_ops=0, stage_inputs=0, hbm_reserve_bytes=0, stream=None):
         self._lib = load_library()
         arr = (ctypes.c_void_p * len(tables))(*[t._h.value for t in tables])
         cfg = ServerConfig(int(memory_cap_bytes), int(arena_bytes), int(max_inflight_steps),
-                           int(max_step_requests), int(max_step_ops), int(stage_inputs))
+                           int(max_step_requests), int(max_step_ops), int(stage_inputs), int(hbm_reserve_bytes))
         h = ctypes.c_void_p()
         _check(self._lib.cht_server_create(arr, len(tables), ctypes.byref(cfg), _stream(stream), ctypes.byref(h)),
                "cht_server_create")

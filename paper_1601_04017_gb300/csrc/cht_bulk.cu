@@ -222,12 +222,70 @@ __global__ void __launch_bounds__(kPThreads) part_gather_kernel(const unsigned s
     }
 }
 
+// ---------------------------------------------------------------------------
+// Live cells in cell index order (the table side of a bulk merge): per chunk
+// of kCompactChunk cells a count, an exclusive scan of the counts, then each
+// chunk's live cells written in order from its offset.
+// ---------------------------------------------------------------------------
+constexpr u32 kCompactChunk = 4096;
+constexpr u32 kCompactPerWarp = kCompactChunk / kPWarps;  // 512 cells, 16 windows of 32
+
+__device__ __forceinline__ bool live_key(u64 k) { return k != kEmpty && k != kTomb; }
+
+__global__ void __launch_bounds__(kPThreads) live_count_kernel(const Cell* cells, u64 c, u32* counts) {
+    __shared__ u32 wsum[kPWarps];
+    const u64 base = u64(blockIdx.x) * kCompactChunk;
+    u32 cnt = 0;
+    for (u32 j = threadIdx.x; j < kCompactChunk; j += kPThreads) {
+        const u64 i = base + j;
+        if (i < c && live_key(cells[i].key)) ++cnt;
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 t = 0;
+        for (int w = 0; w < kPWarps; ++w) t += wsum[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kPThreads) live_write_kernel(const Cell* cells, u64 c, const u32* offs,
+                                                               u64* keys_out, u64* vals_out) {
+    __shared__ u32 wcount[kPWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const u32 below = (1u << lane) - 1u;
+    const u64 base = u64(blockIdx.x) * kCompactChunk + u64(w) * kCompactPerWarp;
+    u32 cnt = 0;
+    for (u32 j = 0; j < kCompactPerWarp; j += 32) {
+        const u64 i = base + j + lane;
+        cnt += __popc(__ballot_sync(0xffffffffu, i < c && live_key(cells[i].key)));
+    }
+    if (lane == 0) wcount[w] = cnt;
+    __syncthreads();
+    u64 out = offs[blockIdx.x];
+    for (int x = 0; x < w; ++x) out += wcount[x];
+    for (u32 j = 0; j < kCompactPerWarp; j += 32) {
+        const u64 i = base + j + lane;
+        u64 k = 0, v = 0;
+        if (i < c) ld_cell_nc(cells + i, k, v);
+        const bool lv = i < c && live_key(k);
+        const u32 m = __ballot_sync(0xffffffffu, lv);
+        if (lv) {
+            const u64 o = out + __popc(m & below);
+            keys_out[o] = k;
+            vals_out[o] = v;
+        }
+        out += __popc(m);
+    }
+}
+
 u64 align256(u64 x) { return (x + 255) & ~u64(255); }
 
 // Scratch layout of one partitioned call.
 struct PLayout {
     u64 ntiles, hist_n, parts;
-    u64 o_hist, o_part, o_keys, o_vals, o_vout, o_codes, o_pos, total;
+    u64 o_hist, o_part, o_keys, o_vals, o_vout, o_codes, o_pos, o_ticket, total;
     PLayout(u64 n, PartitionIO io) {
         ntiles = (n + kPTile - 1) / kPTile;
         hist_n = u64(kPBins) * ntiles + 1;  // + the sentinel
@@ -247,6 +305,8 @@ struct PLayout {
         if (io.codes) o = align256(o + n);
         o_pos = o;
         o = align256(o + n * 2);
+        o_ticket = o;
+        o = align256(o + 8);
         total = o;
     }
 };
@@ -254,6 +314,27 @@ struct PLayout {
 }  // namespace
 
 u64 partition_scratch_bytes(u64 n, PartitionIO io) { return PLayout(n, io).total; }
+
+u64 compact_scratch_bytes(u32 log2c) {
+    const u64 nchunks = ((1ull << log2c) + kCompactChunk - 1) / kCompactChunk;
+    return align256((nchunks + 1) * 4) + align256(scan_partials(nchunks + 1) * 4);
+}
+
+cudaError_t launch_compact_live(const Cell* cells, u32 log2c, u64* keys_out, u64* vals_out, void* scratch,
+                                cudaStream_t s) {
+    const u64 c = 1ull << log2c;
+    const u64 nchunks = (c + kCompactChunk - 1) / kCompactChunk;
+    u32* counts = static_cast<u32*>(scratch);
+    u32* part = reinterpret_cast<u32*>(static_cast<unsigned char*>(scratch) + align256((nchunks + 1) * 4));
+    live_count_kernel<<<unsigned(nchunks), kPThreads, 0, s>>>(cells, c, counts);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = scan_exclusive_u32(counts, nchunks, part, s)) != cudaSuccess) return e;
+    live_write_kernel<<<unsigned(nchunks), kPThreads, 0, s>>>(cells, c, counts, keys_out, vals_out);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_partitioned(const OpArgs& a, PartitionIO io, void* scratch, PartitionRun run, void* ctx,
                                cudaStream_t s) {
@@ -308,6 +389,8 @@ cudaError_t launch_partitioned(const OpArgs& a, PartitionIO io, void* scratch, P
     b.vals = pvals;
     b.vals_out = pvout;
     b.codes = pcodes;
+    b.ticket = reinterpret_cast<unsigned long long*>(base + L.o_ticket);
+    if ((e = cudaMemsetAsync(b.ticket, 0, 8, s)) != cudaSuccess) return e;
     if ((e = run(b, ctx, s)) != cudaSuccess) return e;
 
     if (io.vals_out || io.codes) {

@@ -30,10 +30,14 @@ struct OpArgs {
     u64 n;
     DevState* st;
     // 0: each warp takes one contiguous slice of the batch; else warps take
-    // consecutive pieces of `chunk` operations in batch order (grid-stride),
-    // so the operations in flight at any moment are a narrow range of the
-    // batch (the hash-partitioned path relies on it)
+    // consecutive pieces of `chunk` operations in batch order from a ticket
+    // counter (`ticket`, zero before the launch; the aggregation kernel takes
+    // its windows from it too), so the operations in flight at any moment
+    // are a narrow range of the batch -- the hash-partitioned path relies on
+    // it.  A static grid-stride order would let warps drift apart over the
+    // hundreds of pieces each runs.
     u32 chunk = 0;
+    unsigned long long* ticket = nullptr;
 };
 
 // Launch one batched operation. group_width in {1,2,4,8,16,32}; lane_cells
@@ -110,6 +114,13 @@ u64 partition_scratch_bytes(u64 n, PartitionIO io);
 typedef cudaError_t (*PartitionRun)(const OpArgs& a, void* ctx, cudaStream_t s);
 cudaError_t launch_partitioned(const OpArgs& a, PartitionIO io, void* scratch, PartitionRun run, void* ctx,
                                cudaStream_t s);
+
+// The live cells (neither empty nor tombstone) in cell index order into
+// keys_out / vals_out (deterministic; the bulk merge's table side).  Scratch:
+// compact_scratch_bytes(log2c).
+u64 compact_scratch_bytes(u32 log2c);
+cudaError_t launch_compact_live(const Cell* cells, u32 log2c, u64* keys_out, u64* vals_out, void* scratch,
+                                cudaStream_t s);
 
 // Compact the live cells into keys_out / vals_out (max_n entries); the count
 // lands in st->export_pos, which must be zero on entry.
@@ -223,6 +234,10 @@ cht_status table_read_counts(cht_table* h, u64* I, u64* D, cudaStream_t s);
 cht_status table_migrate_to(cht_table* h, u32 new_log2, u64 live, cudaStream_t s);
 cht_status runtime_alloc(void** p, u64 bytes, cudaStream_t s);
 void runtime_free(void* p, u64 bytes, cudaStream_t s);
+
+// Device memory available to new allocations of this library on `device`:
+// the driver's free bytes plus what the stream-ordered pool holds unused.
+u64 device_free_bytes(int device);
 
 // Kernel launches issued so far (process-wide).
 void count_launch();

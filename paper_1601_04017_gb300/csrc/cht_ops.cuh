@@ -199,6 +199,7 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
     constexpr bool kHasVals = mode_has_vals(MODE);
     constexpr bool kInsLike = mode_fills(MODE);  // modes that may fill a cell
     constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
+    constexpr bool kCasFirst = MODE == kInsert && G == 1 && kFlags == 0;
 
     const u64 cap = 1ull << a.log2c;
     const u64 cmask = cap - 1;
@@ -321,6 +322,34 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
                     if (gl == 0) op_code<kStaged>(a, sg, idx, kNo);
                     active = false;
                 }
+            }
+        }
+
+        // ---- insert, one lane per key (the window of short probes at low
+        // load): the home cell's 16-byte CAS is a fresh key's first probe
+        // step.  It claims an empty home at once, and a taken home comes back
+        // as the CAS's result, so most keys need one round trip instead of a
+        // load followed by the CAS.  (Tombstone reuse needs the first
+        // tombstone of the path, so tables with table options keep the plain
+        // loop.)
+        if (kCasFirst && fresh && active) {
+            Cell expect;
+            expect.key = kEmpty;
+            expect.val = 0;
+            Cell desired;
+            desired.key = key;
+            desired.val = d;
+            const Cell old = cas_cell(a.cells + pos, expect, desired);
+            if (old.key == kEmpty && old.val == 0) {
+                op_code<kStaged>(a, sg, idx, kYes);
+                ++n_ins;
+                active = false;
+            } else if (old.key == key) {
+                op_code<kStaged>(a, sg, idx, kNo);
+                active = false;
+            } else {
+                probed = 1;
+                pos = (pos + 1) & cmask;
             }
         }
 
@@ -511,17 +540,28 @@ __device__ __forceinline__ void pdl_enter() {
 template <int G, int V, int MODE, int kFlags>
 __global__ void __launch_bounds__(kOpBlock, op_min_blocks<G, V>()) op_kernel(OpArgs a) {
     pdl_enter();
-    // each warp owns a contiguous slice of the batch, or (a.chunk != 0) the
-    // pieces warp, warp + nwarps, ... of a.chunk operations each, so that the
-    // whole grid moves through the batch in order
-    const u64 warp = (u64(blockIdx.x) * kOpBlock + threadIdx.x) >> 5;
-    const u64 nwarps = (u64(gridDim.x) * kOpBlock) >> 5;
-    const u64 per = a.chunk ? u64(a.chunk) : (a.n + nwarps - 1) / nwarps;
+    // each warp owns a contiguous slice of the batch, or (a.chunk != 0) takes
+    // pieces of a.chunk operations in batch order from the ticket counter, so
+    // that the whole grid moves through the batch together
     u64 n_ins = 0, n_del = 0;
     u32 sbits = 0;
-    for (u64 begin = warp * per; begin < a.n; begin += nwarps * per) {
+    if (a.chunk == 0) {
+        const u64 warp = (u64(blockIdx.x) * kOpBlock + threadIdx.x) >> 5;
+        const u64 nwarps = (u64(gridDim.x) * kOpBlock) >> 5;
+        const u64 per = (a.n + nwarps - 1) / nwarps;
+        const u64 begin = warp * per;
         const u64 end = begin + per < a.n ? begin + per : a.n;
         warp_ops<G, V, MODE, false, false, kFlags>(a, begin, end, n_ins, n_del, sbits);
+    } else {
+        for (;;) {
+            u64 piece = 0;
+            if ((threadIdx.x & 31) == 0) piece = atomicAdd(a.ticket, 1ull);
+            piece = __shfl_sync(0xffffffffu, piece, 0);
+            const u64 begin = piece * a.chunk;
+            if (begin >= a.n) break;
+            const u64 end = begin + a.chunk < a.n ? begin + a.chunk : a.n;
+            warp_ops<G, V, MODE, false, false, kFlags>(a, begin, end, n_ins, n_del, sbits);
+        }
     }
     warp_flush_counters(a.st, n_ins, n_del, sbits);
 }
@@ -664,9 +704,20 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
     __syncthreads();
     bool dedup = DEDUP == 2;
     const u64 nwin = (a.n + kAggWindow - 1) / kAggWindow;
-    for (u64 w = blockIdx.x; w < nwin; w += gridDim.x) {
+    // windows: blockIdx.x, + gridDim.x, ... or, with a ticket counter, the
+    // next window in batch order (every window already ends in a barrier,
+    // which publishes the next ticket to the block)
+    __shared__ u64 s_next[2];
+    u64 w = blockIdx.x;
+    if (a.ticket) {
+        if (tid == 0) s_next[0] = atomicAdd(a.ticket, 1ull);
+        __syncthreads();
+        w = s_next[0];
+    }
+    for (u32 round = 0; w < nwin; ++round) {
         const u64 w0 = w * kAggWindow;
-        const int par = int((w / gridDim.x) & 1);
+        const int par = int(round & 1);
+        if (a.ticket && tid == 0) s_next[(round + 1) & 1] = atomicAdd(a.ticket, 1ull);
         // fold the window's operations into the slots
 #pragma unroll
         for (int j = 0; j < kAggWindow / kAggBlock; ++j) {
@@ -766,6 +817,7 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
             }
             __syncthreads();
         }
+        w = a.ticket ? s_next[(round + 1) & 1] : w + gridDim.x;
     }
     constexpr u32 FULL = 0xffffffffu;
     for (int o = 16; o > 0; o >>= 1) {

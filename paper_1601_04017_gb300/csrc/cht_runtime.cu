@@ -186,7 +186,7 @@ bool valid_config(const cht_config& c) {
     if (c.iou_aggregate < 0 || c.iou_aggregate > 2) return false;
     if (c.reuse_tombstones < 0 || c.reuse_tombstones > 1) return false;
     if (c.full_key_space < 0 || c.full_key_space > 1) return false;
-    if (c.partition < 0 || c.partition > 2) return false;
+    if (c.partition < 0 || c.partition > 1) return false;
     return true;
 }
 
@@ -333,7 +333,7 @@ Width pick_width(const cht_table* h, cht::Mode mode, u64 n) {
 // Operations per in-order piece of a warp on a partitioned batch: the grid
 // then has about (resident warps x kOrderedChunk) operations in flight, a
 // narrow range of the reordered batch and so of the table.
-constexpr u32 kOrderedChunk = 64;
+constexpr u32 kOrderedChunk = 128;
 
 bool aggregated(const cht_table* h, cht::Mode mode) {
     return (mode == cht::kIouAdd || mode == cht::kIouOverwrite || mode == cht::kUpdAdd ||
@@ -341,13 +341,9 @@ bool aggregated(const cht_table* h, cht::Mode mode) {
            h->cfg.iou_aggregate != 0;
 }
 
-// The hash-partitioned path (Sec. 4.5): for batches that touch much of a
-// table too large for L2.  Automatic rule: at least 2^22 cells (64 MiB), at
-// least 2^20 operations and a sixteenth of the capacity.
+// The hash-partitioned path (Sec. 4.5), a table option (partition = 1).
 bool use_partition(const cht_table* h, u64 n) {
-    if (h->cfg.partition == 1 || n >= (1ull << 32) || h->log2c < 8) return false;
-    if (h->cfg.partition == 2) return true;
-    return h->log2c >= 22 && n >= (1ull << 20) && n >= (h->cap() >> 4);
+    return h->cfg.partition == 1 && n < (1ull << 32) && h->log2c >= 8;
 }
 
 struct KernelCtx {
@@ -463,6 +459,25 @@ cht_status run_modify(cht_table* h, cht::Mode mode, const u64* keys, const u64* 
 namespace cht {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+u64 device_free_bytes(int device) {
+    DeviceGuard g(device);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    u64 pooled = 0;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        unsigned long long reserved = 0, used = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+            pooled = reserved - used;
+    }
+    cudaGetLastError();
+    return u64(free_b) + pooled;
+}
 
 int sm_count() {
     static std::atomic<int> cached[64];
@@ -747,6 +762,151 @@ cht_status cht_get_config(cht_handle h, cht_config* cfg) {
     return CHT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined staging of host arrays.  A call with host arrays larger than one
+// piece is cut into pieces of kPipeChunk operations that cycle through
+// kPipeSlots device slots: piece i+1 is copied in on a copy stream while piece
+// i runs on the caller's stream and piece i-1's results are copied out on a
+// second copy stream.  Pieces of one batch run one after another on the
+// caller's stream, which is one linearization of the batch (phase semantics
+// hold per piece and across them).  Device arrays are used in place.  The
+// slots (about 100 MB per slot) are allocated on a device's first pipelined
+// call and kept until the process exits; calls on one device take the slots
+// one after another (a host lock around the enqueueing, events on the GPU).
+// ---------------------------------------------------------------------------
+constexpr u64 kPipeChunk = 1ull << 22;
+constexpr int kPipeSlots = 3;
+
+struct PipeSlot {
+    u64* keys = nullptr;
+    u64* vals = nullptr;
+    u64* vout = nullptr;
+    unsigned char* codes = nullptr;
+    cudaEvent_t loaded = nullptr;    // its inputs are on the device
+    cudaEvent_t consumed = nullptr;  // the kernel that read them is done
+    cudaEvent_t drained = nullptr;   // its results are back in host memory
+};
+
+struct DevPipe {
+    std::mutex mu;
+    bool tried = false, ok = false;
+    cudaStream_t cin = nullptr, cout = nullptr;
+    cudaEvent_t start = nullptr;  // the work on the caller's stream before a call
+    PipeSlot slot[kPipeSlots];
+    int next = 0;
+};
+DevPipe g_pipe[64];
+
+bool pipe_ready(int dev) {
+    DevPipe& P = g_pipe[dev];
+    if (P.tried) return P.ok;
+    P.tried = true;
+    const u64 per = kPipeChunk * (8 + 8 + 8 + 1);
+    if (cudaStreamCreateWithFlags(&P.cin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&P.cout, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P.start, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    unsigned char* mem = nullptr;
+    if (cudaMalloc(&mem, per * kPipeSlots) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    g_mem_in_use.fetch_add(per * kPipeSlots);
+    for (int i = 0; i < kPipeSlots; ++i) {
+        PipeSlot& q = P.slot[i];
+        unsigned char* b = mem + i * per;
+        q.keys = reinterpret_cast<u64*>(b);
+        q.vals = q.keys + kPipeChunk;
+        q.vout = q.vals + kPipeChunk;
+        q.codes = reinterpret_cast<unsigned char*>(q.vout + kPipeChunk);
+        if (cudaEventCreateWithFlags(&q.loaded, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&q.consumed, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&q.drained, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    P.ok = true;
+    return true;
+}
+
+// One piece's work: the batch's operations [lo, lo + m) with device arrays.
+typedef cht_status (*PieceFn)(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals, u64* vout,
+                              unsigned char* codes, u64 m, cudaStream_t s);
+
+cht_status piece_modify(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals, u64*, unsigned char* codes,
+                        u64 m, cudaStream_t s) {
+    return run_modify(h, mode, keys, vals, codes, m, s);
+}
+
+cht_status piece_launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals, u64* vout,
+                        unsigned char* codes, u64 m, cudaStream_t s) {
+    return launch(h, mode, keys, vals, vout, codes, m, s);
+}
+
+// Runs the call through the pipeline if some array is in host memory and the
+// batch is larger than one piece; *handled = false otherwise (the caller
+// then stages the plain way).
+cht_status pipelined(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals, u64* vout,
+                     unsigned char* codes, u64 n, cudaStream_t s, PieceFn fn, bool* handled) {
+    *handled = false;
+    const bool hk = is_host_pointer(keys), hv = vals && is_host_pointer(vals);
+    const bool ho = vout && is_host_pointer(vout), hc = codes && is_host_pointer(codes);
+    if (n <= kPipeChunk || !(hk || hv || ho || hc) || h->device < 0 || h->device >= 64) return CHT_OK;
+    DevPipe& P = g_pipe[h->device];
+    std::lock_guard<std::mutex> lk(P.mu);
+    if (!pipe_ready(h->device)) return CHT_OK;
+    *handled = true;
+    // the copies in wait for the work already on s (it may write the inputs)
+    if (cudaEventRecord(P.start, s) != cudaSuccess || cudaStreamWaitEvent(P.cin, P.start, 0) != cudaSuccess)
+        return CHT_ERR_CUDA;
+    bool used[kPipeSlots] = {};
+    cht_status r = CHT_OK;
+    for (u64 lo = 0; lo < n && r == CHT_OK; lo += kPipeChunk) {
+        const u64 m = n - lo < kPipeChunk ? n - lo : kPipeChunk;
+        PipeSlot& q = P.slot[P.next];
+        used[P.next] = true;
+        P.next = (P.next + 1) % kPipeSlots;
+        // inputs: wait until the slot's previous kernel has read its inputs
+        if (cudaStreamWaitEvent(P.cin, q.consumed, 0) != cudaSuccess) return CHT_ERR_CUDA;
+        const u64* dk = keys + lo;
+        const u64* dv = vals ? vals + lo : nullptr;
+        if (hk) {
+            if (cudaMemcpyAsync(q.keys, keys + lo, m * 8, cudaMemcpyHostToDevice, P.cin) != cudaSuccess)
+                return CHT_ERR_CUDA;
+            dk = q.keys;
+        }
+        if (hv) {
+            if (cudaMemcpyAsync(q.vals, vals + lo, m * 8, cudaMemcpyHostToDevice, P.cin) != cudaSuccess)
+                return CHT_ERR_CUDA;
+            dv = q.vals;
+        }
+        if (cudaEventRecord(q.loaded, P.cin) != cudaSuccess) return CHT_ERR_CUDA;
+        // the kernel: after its inputs, and after the slot's previous results left
+        if (cudaStreamWaitEvent(s, q.loaded, 0) != cudaSuccess || cudaStreamWaitEvent(s, q.drained, 0) != cudaSuccess)
+            return CHT_ERR_CUDA;
+        u64* dvo = vout ? (ho ? q.vout : vout + lo) : nullptr;
+        unsigned char* dc = codes ? (hc ? q.codes : codes + lo) : nullptr;
+        r = fn(h, mode, dk, dv, dvo, dc, m, s);
+        if (cudaEventRecord(q.consumed, s) != cudaSuccess) return CHT_ERR_CUDA;
+        // results back once the kernel is done
+        if (ho || hc) {
+            if (cudaStreamWaitEvent(P.cout, q.consumed, 0) != cudaSuccess) return CHT_ERR_CUDA;
+            if (ho && cudaMemcpyAsync(vout + lo, q.vout, m * 8, cudaMemcpyDeviceToHost, P.cout) != cudaSuccess)
+                return CHT_ERR_CUDA;
+            if (hc && cudaMemcpyAsync(codes + lo, q.codes, m, cudaMemcpyDeviceToHost, P.cout) != cudaSuccess)
+                return CHT_ERR_CUDA;
+            if (cudaEventRecord(q.drained, P.cout) != cudaSuccess) return CHT_ERR_CUDA;
+        }
+    }
+    // the call completes on s when every result is back
+    for (int i = 0; i < kPipeSlots; ++i)
+        if (used[i] && cudaStreamWaitEvent(s, P.slot[i].drained, 0) != cudaSuccess) return CHT_ERR_CUDA;
+    return r;
+}
+
 static cht_status modify_call(cht_handle h, cht::Mode mode, const uint64_t* keys, const uint64_t* vals,
                               uint64_t n, uint8_t* codes, cht_stream_t stream) {
     if (!h || (n > 0 && (!keys || !vals))) return CHT_ERR_INVALID_ARG;
@@ -754,10 +914,14 @@ static cht_status modify_call(cht_handle h, cht::Mode mode, const uint64_t* keys
     DeviceGuard g(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     h->last = s;
+    bool piped = false;
+    cht_status r = pipelined(h, mode, reinterpret_cast<const u64*>(keys), reinterpret_cast<const u64*>(vals), nullptr, codes, n,
+                                 s, piece_modify, &piped);
+    if (piped) return r;
     Staging stg(s);
     const void *dk, *dv;
     void* dc;
-    cht_status r = stg.in(keys, n * 8, &dk);
+    r = stg.in(keys, n * 8, &dk);
     if (r == CHT_OK) r = stg.in(vals, n * 8, &dv);
     if (r == CHT_OK) r = stg.out(codes, n, &dc);
     if (r != CHT_OK) return r;
@@ -787,10 +951,15 @@ cht_status cht_update(cht_handle h, const uint64_t* keys, const uint64_t* vals, 
     DeviceGuard g(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     h->last = s;
+    const cht::Mode um = op == CHT_ADD ? cht::kUpdAdd : cht::kUpdOverwrite;
+    bool piped = false;
+    cht_status r = pipelined(h, um, reinterpret_cast<const u64*>(keys), reinterpret_cast<const u64*>(vals), nullptr, updated,
+                                 n, s, piece_launch, &piped);
+    if (piped) return r;
     Staging stg(s);
     const void *dk, *dv;
     void* dc;
-    cht_status r = stg.in(keys, n * 8, &dk);
+    r = stg.in(keys, n * 8, &dk);
     if (r == CHT_OK) r = stg.in(vals, n * 8, &dv);
     if (r == CHT_OK) r = stg.out(updated, n, &dc);
     if (r != CHT_OK) return r;
@@ -862,6 +1031,83 @@ cht_status cht_build(cht_handle h, const uint64_t* keys, const uint64_t* vals, u
     return stg.finish();
 }
 
+cht_status cht_merge(cht_handle h, const uint64_t* keys, const uint64_t* vals, uint64_t n, cht_stream_t stream) {
+    if (!h || (n > 0 && (!keys || !vals))) return CHT_ERR_INVALID_ARG;
+    if (n == 0) return CHT_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last = s;
+    // the live count sizes the table side of the concatenation (one read)
+    DevState ds;
+    cht_status r = read_state(h, &ds, s);
+    if (r != CHT_OK) return r;
+    const u64 live = ds.I - ds.D, tot = live + n;
+    if (tot >= (1ull << 32)) return CHT_ERR_INVALID_ARG;
+    Staging stg(s);
+    const void *dk, *dv;
+    r = stg.in(keys, n * 8, &dk);
+    if (r == CHT_OK) r = stg.in(vals, n * 8, &dv);
+    if (r != CHT_OK) return r;
+    // a growable table takes the capacity that holds live + n at alpha
+    u32 nl = h->log2c;
+    if (h->growable)
+        while (double(tot) > h->cfg.alpha * double(1ull << nl) && nl < kMaxLog2) ++nl;
+    const u64 ncap = 1ull << nl, cbytes = ncap * sizeof(Cell);
+    // scratch: the concatenation (keys, values), the compaction's counts, the build's buffers
+    const u64 cat_bytes = (tot * 8 + 255) & ~255ull;
+    const u64 cmp_bytes = cht::compact_scratch_bytes(h->log2c);
+    const u64 bld_bytes = cht::build_scratch_bytes(tot);
+    const u64 sbytes = 2 * cat_bytes + cmp_bytes + bld_bytes;
+    unsigned char* scratch = nullptr;
+    Cell* cells = nullptr;
+    r = lib_alloc(reinterpret_cast<void**>(&scratch), sbytes, s);
+    if (r != CHT_OK) return r;
+    r = lib_alloc(reinterpret_cast<void**>(&cells), cbytes, s);
+    if (r != CHT_OK) {
+        lib_free(scratch, sbytes, s);
+        return r;
+    }
+    u64* ck = reinterpret_cast<u64*>(scratch);
+    u64* cv = reinterpret_cast<u64*>(scratch + cat_bytes);
+    void* cmp = scratch + 2 * cat_bytes;
+    void* bld = scratch + 2 * cat_bytes + cmp_bytes;
+    // the table's live elements in cell index order, then the batch
+    cudaError_t e = cht::launch_compact_live(h->cells, h->log2c, ck, cv, cmp, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ck + live, dk, n * 8, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cv + live, dv, n * 8, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cells, 0, cbytes, s);
+    const Cell* sorted = nullptr;
+    cht::BuildExtra* ex = nullptr;
+    if (e == cudaSuccess)
+        e = cht::launch_build_sort(ck, cv, tot, nl, h->cfg.full_key_space, bld, &sorted, &ex, s);
+    if (e == cudaSuccess) e = cht::launch_build_count(sorted, tot, nl, bld, ex, s);
+    if (e == cudaSuccess && tot >= ncap) {
+        // only tot >= c' can leave no empty cell: check before touching the table
+        u64 S = 0;
+        e = cudaMemcpyAsync(&S, &ex->S, sizeof(u64), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && S >= ncap) {
+            lib_free(cells, cbytes, s);
+            lib_free(scratch, sbytes, s);
+            stg.finish();
+            return CHT_ERR_TABLE_FULL;
+        }
+    }
+    // the finish kernel sets I = survivors, D = 0 and the special slots the batch names
+    if (e == cudaSuccess) e = cht::launch_build_place(sorted, tot, cells, nl, bld, ex, h->st, cv, s);
+    lib_free(scratch, sbytes, s);
+    if (e != cudaSuccess) {
+        lib_free(cells, cbytes, s);
+        return cuda_status(e);
+    }
+    lib_free(h->cells, h->cap() * sizeof(Cell), s);
+    h->cells = cells;
+    h->log2c = nl;
+    h->i_bound = tot;
+    h->i_exact = false;
+    return stg.finish();
+}
+
 cht_status cht_find(cht_handle h, const uint64_t* keys, uint64_t n, uint64_t* vals_out, uint8_t* found,
                     cht_stream_t stream) {
     if (!h || (n > 0 && (!keys || !vals_out))) return CHT_ERR_INVALID_ARG;
@@ -869,10 +1115,14 @@ cht_status cht_find(cht_handle h, const uint64_t* keys, uint64_t n, uint64_t* va
     DeviceGuard g(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     h->last = s;
+    bool piped = false;
+    cht_status r = pipelined(h, cht::kFind, reinterpret_cast<const u64*>(keys), nullptr,
+                                 reinterpret_cast<u64*>(vals_out), found, n, s, piece_launch, &piped);
+    if (piped) return r;
     Staging stg(s);
     const void* dk;
     void *dv, *dc;
-    cht_status r = stg.in(keys, n * 8, &dk);
+    r = stg.in(keys, n * 8, &dk);
     if (r == CHT_OK) r = stg.out(vals_out, n * 8, &dv);
     if (r == CHT_OK) r = stg.out(found, n, &dc);
     if (r != CHT_OK) return r;
@@ -888,10 +1138,14 @@ cht_status cht_erase(cht_handle h, const uint64_t* keys, uint64_t n, uint8_t* er
     DeviceGuard g(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     h->last = s;
+    bool piped = false;
+    cht_status r = pipelined(h, cht::kErase, reinterpret_cast<const u64*>(keys), nullptr, nullptr, erased, n, s,
+                                 piece_launch, &piped);
+    if (piped) return r;
     Staging stg(s);
     const void* dk;
     void* dc;
-    cht_status r = stg.in(keys, n * 8, &dk);
+    r = stg.in(keys, n * 8, &dk);
     if (r == CHT_OK) r = stg.out(erased, n, &dc);
     if (r != CHT_OK) return r;
     r = launch(h, cht::kErase, static_cast<const u64*>(dk), nullptr, nullptr, static_cast<unsigned char*>(dc),

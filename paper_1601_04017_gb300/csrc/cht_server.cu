@@ -238,6 +238,10 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
         }
     } guard{s, &st};
     if (cudaEventRecord(st.t_begin, s->stream) != cudaSuccess) return CHT_ERR_CUDA;
+    // device memory a growth may still take in this step: asked once per
+    // step that grows a table, then decreased by each growth admitted
+    long long hbm_left = 0;
+    bool hbm_known = false;
     bool enqueued_before_engine = false;  // a migration or staging copy precedes the engine
     std::vector<char> blocked(nt, 0);
     std::vector<u64> step_new(nt, 0);
@@ -269,7 +273,13 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
                 u32 nl = ti.log2c;
                 while (nl < 40 && u64(std::floor(ti.alpha * double(1ull << nl))) < used + m) ++nl;
                 const u64 need = (1ull << nl) * sizeof(cht::Cell);
-                if (s->cfg.memory_cap_bytes && tables_bytes(s) + need + s->cfg.arena_bytes > s->cfg.memory_cap_bytes) {
+                if (!hbm_known) {
+                    hbm_left = (long long)cht::device_free_bytes(s->device) - (long long)s->cfg.hbm_reserve_bytes;
+                    hbm_known = true;
+                }
+                const bool over_cap =
+                    s->cfg.memory_cap_bytes && tables_bytes(s) + need + s->cfg.arena_bytes > s->cfg.memory_cap_bytes;
+                if (over_cap || (long long)need > hbm_left) {
                     if (s->inflight.empty() && parts.empty()) {  // can never fit: reject
                         rq.state = 3;
                         rq.status = CHT_ERR_OOM;
@@ -284,6 +294,7 @@ cht_status admit_and_launch(cht_server* s, u32* admitted) {
                 }
                 cht_status r = cht::table_migrate_to(h, nl, ~0ull, s->stream);
                 if (r != CHT_OK) return r;
+                hbm_left -= (long long)need;
                 enqueued_before_engine = true;
                 ++s->prof.migrations;
                 ++st.rec.migrations;
@@ -523,8 +534,9 @@ cht_status cht_server_create(const cht_handle* tables, uint32_t n_tables, const 
     *out = nullptr;
     cht_server* s = new (std::nothrow) cht_server();
     if (!s) return CHT_ERR_OOM;
-    s->cfg = cfg ? *cfg : cht_server_config{0, 0, 0, 0, 0, 0};
+    s->cfg = cfg ? *cfg : cht_server_config{0, 0, 0, 0, 0, 0, 0};
     if (s->cfg.arena_bytes == 0) s->cfg.arena_bytes = 1ull << 30;
+    if (s->cfg.hbm_reserve_bytes == 0) s->cfg.hbm_reserve_bytes = 1ull << 30;
     if (s->cfg.max_inflight_steps == 0) s->cfg.max_inflight_steps = 2;
     if (s->cfg.max_step_requests == 0) s->cfg.max_step_requests = 8192;
     if (s->cfg.max_step_ops == 0) s->cfg.max_step_ops = 1ull << 26;

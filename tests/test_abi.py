@@ -30,7 +30,7 @@ def lib_path():
 
 def test_header_declares_the_boundary():
     names = set(declared_functions())
-    for want in ["cht_create", "cht_insert", "cht_build", "cht_find", "cht_insert_or_update", "cht_erase",
+    for want in ["cht_create", "cht_insert", "cht_build", "cht_merge", "cht_find", "cht_insert_or_update", "cht_erase",
                  "cht_migrate", "cht_destroy", "cht_size", "cht_export", "cht_status_string"]:
         assert want in names
 

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from gpu_helpers import to_dev, to_np_u64
+from gpu_helpers import codes_buf, to_dev, to_np_u64, to_np_u8, vals_buf
 
 pytestmark = pytest.mark.gpu
 
@@ -179,3 +179,70 @@ def test_build_runs_mixing_keys(cuda_lib, oracle_mod):
     t.find(to_dev(q), got)
     assert to_np_u64(got).tolist() == [last[int(k)] for k in q]
     assert t.size()[0] == len(last)
+
+
+# ---------------------------------------------------------------------------
+# bulk merge into a non-empty table (Sec. 4.5): layout bit-exact vs the oracle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("log2c,n_ins,n_erase,n,growable,full", [
+    (10, 400, 100, 500, False, False),
+    (16, 20_000, 5_000, 30_000, True, False),    # grows to 2^17
+    (16, 30_000, 3_000, 20_000, False, True),    # full key space, keys 0 / ~0 in the batch
+    (18, 100_000, 50_000, 200_000, True, True),  # many tombstones dropped, grows to 2^20
+])
+def test_merge_layout_equals_oracle(cuda_lib, oracle_mod, log2c, n_ins, n_erase, n, growable, full):
+    c = 1 << log2c
+    keys = W.uniform_keys(n_ins, start=log2c * 100_000, seed=25)
+    t = cuda_lib.Table(c, growable=growable)
+    t.set_config(full_key_space=int(full))
+    t.insert(to_dev(keys), to_dev(keys ^ np.uint64(77)))
+    t.erase(to_dev(keys[:n_erase]))
+    o = oracle_mod.OracleTable(c, growable=growable, alpha=0.5, full_key_space=full)
+    o.load_cells(to_np_u64(t.cells()).reshape(-1, 2))
+    if full:
+        z = np.array([0], np.uint64)
+        t.insert(to_dev(z), to_dev(np.array([11], np.uint64)))
+        o.insert(z, np.array([11], np.uint64))
+    rng = np.random.default_rng(log2c)
+    pool = np.concatenate([keys, W.uniform_keys(n, start=9 * 10**8, seed=25)])
+    bk = pool[rng.integers(0, pool.size, n)]
+    bv = rng.integers(1, 1 << 62, n).astype(np.uint64)
+    if full:
+        bk[::1000] = (1 << 64) - 1
+    t.merge(to_dev(bk), to_dev(bv))
+    assert o.merge(bk, bv) == 0
+    got = to_np_u64(t.cells()).reshape(-1, 2)
+    assert got.shape == o.cells().shape
+    assert np.array_equal(got, o.cells())
+    assert t.size(check=True) == (o.live, o.nonempty, o.capacity)
+    if full:
+        q = np.array([0, (1 << 64) - 1], np.uint64)
+        vo, fo = vals_buf(2), codes_buf(2)
+        t.find(to_dev(q), vo, fo)
+        ev, ef = o.find(q)
+        assert np.array_equal(to_np_u8(fo), ef) and np.array_equal(to_np_u64(vo), ev)
+
+
+def test_merge_full_bounded_table_unchanged_and_host_arrays(cuda_lib, oracle_mod):
+    c = 1 << 10
+    keys = W.uniform_keys(900, start=3_000_000, seed=26)
+    t = cuda_lib.Table(c)
+    t.insert(to_dev(keys), to_dev(keys))
+    before = to_np_u64(t.cells())
+    more = W.uniform_keys(200, start=4_000_000, seed=26)
+    with pytest.raises(cuda_lib.ChtError) as ei:
+        t.merge(to_dev(more), to_dev(more))
+    assert ei.value.status == cuda_lib.CHT_ERR_TABLE_FULL
+    assert np.array_equal(to_np_u64(t.cells()), before) and t.size()[0] == 900
+    # host arrays, staged by the library; equals the oracle
+    o = oracle_mod.OracleTable(c)
+    o.load_cells(before.reshape(-1, 2))
+    t.merge(more[:100], more[:100] + np.uint64(1))
+    assert o.merge(more[:100], more[:100] + np.uint64(1)) == 0
+    assert np.array_equal(to_np_u64(t.cells()).reshape(-1, 2), o.cells())
+    # into an empty table the merge is the build
+    k, v = _batch(5000, 3000, seed=8)
+    a, b = cuda_lib.Table(1 << 14), cuda_lib.Table(1 << 14)
+    a.merge(to_dev(k), to_dev(v))
+    b.build(to_dev(k), to_dev(v))
+    assert np.array_equal(to_np_u64(a.cells()), to_np_u64(b.cells()))

@@ -1,12 +1,12 @@
 """GPU parity of the hash-partitioned path (Sec. 4.5 "Bulk Operations") against the oracle.
 
-`partition = 2` forces the path on small tables, so every operation type,
+`partition = 1` runs the path on small tables too, so every operation type,
 table option and a ragged batch (not a multiple of the 2048-operation tile,
 a batch below one tile, one operation) runs through the reorder, the in-order
 operation kernel and the gather of the results.  The bar is the direct path's:
 bit-exact finds, codes and sums; set-valued where equal keys inside one batch
-allow several outcomes.  A final case checks that the automatic rule takes the
-path on a 2^22-cell table and still agrees with the oracle.
+allow several outcomes.  A final case runs a 2^22-cell table at load 0.9 both
+ways.
 """
 import numpy as np
 import pytest
@@ -22,7 +22,7 @@ SIZES = [1, 2047, 2048, 2049, 40_001]
 
 def _pair(cht, oracle_mod, c, growable=False, **cfg):
     t = cht.Table(c, growable=growable)
-    t.set_config(partition=2, **cfg)
+    t.set_config(partition=1, **cfg)
     o = oracle_mod.OracleTable(c, growable=growable, alpha=0.5,
                                reuse_tombstones=bool(cfg.get("reuse_tombstones", 0)),
                                full_key_space=bool(cfg.get("full_key_space", 0)))
@@ -145,30 +145,30 @@ def test_partitioned_growable_insert(cuda_lib, oracle_mod):
     assert_same_live_set(t, o)
 
 
-def test_partition_auto_rule_2p22(cuda_lib, oracle_mod):
-    """2^22 cells, 2^21 operations: the automatic rule partitions (more
-    launches than the direct path); results equal the oracle's."""
+def test_partitioned_2p22_table_load_09(cuda_lib, oracle_mod):
+    """2^22 cells, 2^21 operations per find: the partitioned path takes more
+    launches than the direct one; both agree with the oracle."""
     log2c = 22
     c = 1 << log2c
     wl = W.bounded_workload(log2c, loads=(0.9,), n_find=1 << 21)
     m = wl["counts"][0.9]
     keys, vals = wl["keys"][:m], wl["vals"][:m]
     t = cuda_lib.Table(c)
+    t.set_config(partition=1)
     o = oracle_mod.OracleTable(c)
     l0 = cuda_lib.launch_count()
     codes = codes_buf(m)
     t.insert(to_dev(keys), to_dev(vals), codes)
     assert cuda_lib.launch_count() - l0 >= 5  # histogram, scan (3), scatter, operation, gather
     assert np.array_equal(to_np_u8(codes), o.insert(keys, vals))
-    for q in (wl["hits"][0.9], wl["misses"]):
-        vo, fo = vals_buf(q.size), codes_buf(q.size)
-        t.find(to_dev(q), vo, fo)
-        ev, ef = o.find(q)
-        assert np.array_equal(to_np_u8(fo), ef)
-        assert np.array_equal(to_np_u64(vo), ev)
-    t.set_config(partition=1)
-    l0 = cuda_lib.launch_count()
-    vo = vals_buf(1 << 21)
-    t.find(to_dev(wl["misses"]), vo)
-    assert cuda_lib.launch_count() - l0 == 1
+    for part in (1, 0):
+        t.set_config(partition=part)
+        for q in (wl["hits"][0.9], wl["misses"]):
+            l0 = cuda_lib.launch_count()
+            vo, fo = vals_buf(q.size), codes_buf(q.size)
+            t.find(to_dev(q), vo, fo)
+            assert (cuda_lib.launch_count() - l0 == 1) == (part == 0)
+            ev, ef = o.find(q)
+            assert np.array_equal(to_np_u8(fo), ef)
+            assert np.array_equal(to_np_u64(vo), ev)
     assert_same_live_set(t, o)

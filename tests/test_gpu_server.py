@@ -177,3 +177,27 @@ def test_server_rejects_growth_beyond_memory_cap(cuda_lib):
     done, _, st = srv.result(rid)
     assert done and st == cuda_lib.CHT_ERR_OOM
     srv.destroy()
+
+
+def test_server_admits_growth_by_free_device_memory(cuda_lib):
+    """A growth the device's free memory cannot hold (with the configured
+    reserve left free) is not admitted: with nothing in flight the request is
+    rejected; with a reserve that fits, the same request grows its table."""
+    import torch
+
+    keys = W.uniform_keys(5000, seed=45)
+    free_now = torch.cuda.mem_get_info()[0]
+    for reserve, want in ((free_now * 2, cuda_lib.CHT_ERR_OOM), (1 << 20, cuda_lib.CHT_OK)):
+        codes = np.zeros(5000, np.uint8)
+        t = cuda_lib.Table(64, growable=True)
+        srv = cuda_lib.Server([t], arena_bytes=1 << 20, hbm_reserve_bytes=reserve)
+        rid = srv.submit(0, cuda_lib.OP_INSERT, keys, keys, None, codes)
+        srv.drain()
+        done, _, st = srv.result(rid)
+        assert done and st == want
+        if want == cuda_lib.CHT_OK:
+            assert (codes == 1).all() and t.size()[0] == 5000
+        else:
+            assert t.size()[2] == 64  # never grown
+        srv.destroy()
+        t.destroy()

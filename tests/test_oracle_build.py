@@ -185,3 +185,101 @@ def test_build_keeps_last_in_runs_mixing_keys(oracle_mod):
     got, found = t.find(np.array([a, b], dtype=np.uint64))
     assert found.all() and got.tolist() == [7, 8]
     assert t.live == 2
+
+
+# ---------------------------------------------------------------------------
+# bulk merge of a batch into a non-empty table (Sec. 4.5)
+# ---------------------------------------------------------------------------
+def _filled(oracle_mod, log2c, n_ins, n_erase, seed, growable=False, **kw):
+    keys = W.uniform_keys(n_ins, start=seed * 10_000, seed=33)
+    t = oracle_mod.OracleTable(1 << log2c, growable=growable, **kw)
+    t.insert(keys, keys ^ np.uint64(0xABCDEF))
+    t.erase(keys[:n_erase])
+    return t, keys
+
+
+@pytest.mark.parametrize("log2c,n_ins,n_erase,n,distinct", [(8, 90, 30, 60, 40), (10, 400, 100, 500, 300),
+                                                            (12, 2000, 900, 1500, 1200)])
+def test_merge_is_the_dictionary_update(oracle_mod, log2c, n_ins, n_erase, n, distinct):
+    t, keys = _filled(oracle_mod, log2c, n_ins, n_erase, seed=log2c)
+    d = dict(zip(*(a.tolist() for a in t.export())))
+    # the batch: some keys of the table (live and erased) and new ones, repeated
+    rng = np.random.default_rng(log2c)
+    pool = np.concatenate([keys, W.uniform_keys(distinct, start=10**7, seed=33)])
+    bk = pool[rng.integers(0, pool.size, n)]
+    bv = rng.integers(1, 1 << 62, n).astype(np.uint64)
+    assert t.merge(bk, bv) == 0
+    for k, v in zip(bk.tolist(), bv.tolist()):
+        d[k] = v
+    gk, gv = t.export()
+    assert dict(zip(gk.tolist(), gv.tolist())) == d
+    assert t.live == t.nonempty == len(d)  # the new table has no tombstones
+    t.assert_invariants()
+
+
+@pytest.mark.parametrize("log2c,load", [(8, 0.4), (10, 0.85), (12, 0.95)])
+def test_merge_layout_is_sorted_insertion(oracle_mod, log2c, load):
+    c = 1 << log2c
+    t, keys = _filled(oracle_mod, log2c, int(load * c * 0.6), int(load * c * 0.1), seed=log2c + 3)
+    before = t.cells()
+    table_order = [int(k) for k in before[:, 0] if k != 0 and k != TOMB]  # cell index order
+    live = len(table_order)
+    bk, bv = _dup_batch(int(load * c) - live + 40, int(load * c) - live, seed=log2c + 11)
+    bk[::7] = np.array(table_order[: bk[::7].size], dtype=np.uint64)[: bk[::7].size]  # replace some
+    assert t.merge(bk, bv) == 0
+    cells = t.cells()
+    _check_valid(cells, log2c, oracle_mod)
+    # position of the kept copy in the concatenation (table in cell order, batch)
+    pos = {k: i for i, k in enumerate(table_order)}
+    for j, k in enumerate(bk.tolist()):
+        pos[k] = live + j
+    B = oracle_mod.build_sort_bits(log2c)
+    run = _run_keys(cells)
+    ks = np.array([k for _, k in run], dtype=np.uint64)
+    sk = (oracle_mod.hash64(ks) >> np.uint64(64 - B)).tolist()
+    order = [(s, pos[k]) for s, k in zip(sk, ks.tolist())]
+    descents = sum(1 for a, b in zip(order, order[1:]) if b < a)
+    assert descents <= 1
+    if descents == 1:
+        cut = next(i for i, (a, b) in enumerate(zip(order, order[1:])) if b < a) + 1
+        order = order[cut:] + order[:cut]
+    assert order == sorted(order)
+    homes = oracle_mod.homes(ks, log2c).tolist()
+    for (p, _), h in zip(run, homes):
+        assert p == h or cells[(p - 1) % c, 0] != 0
+    assert len(run) == len(pos)
+
+
+def test_merge_capacity_full_and_empty_table(oracle_mod):
+    # growable: the smallest power of two with live + n <= alpha * c'
+    t, _ = _filled(oracle_mod, 8, 100, 20, seed=1, growable=True)
+    assert t.capacity == 256 and t.live == 80
+    bk = W.uniform_keys(300, start=5 * 10**6, seed=33)
+    assert t.merge(bk, bk) == 0
+    assert t.capacity == 1024 and t.live == 380  # 80 + 300 > 0.5 * 512
+    # bounded: c stays; a merge that leaves no empty cell changes nothing
+    t2, _ = _filled(oracle_mod, 6, 40, 0, seed=2)
+    snap = t2.cells()
+    big = W.uniform_keys(24, start=6 * 10**6, seed=33)
+    assert t2.merge(big, big) == -2
+    assert np.array_equal(t2.cells(), snap) and t2.live == 40
+    assert t2.merge(big[:20], big[:20]) == 0 and t2.live == 60 and t2.capacity == 64
+    # into an empty table the merge is the build
+    k, v = _dup_batch(700, 500, seed=9)
+    a = oracle_mod.OracleTable(1 << 10)
+    b = oracle_mod.OracleTable(1 << 10)
+    assert a.merge(k, v) == 0 and b.build(k, v) == 0
+    assert np.array_equal(a.cells(), b.cells())
+
+
+def test_merge_special_slots(oracle_mod):
+    t, _ = _filled(oracle_mod, 8, 50, 0, seed=3, full_key_space=True)
+    t.insert(np.array([0], np.uint64), np.array([11], np.uint64))
+    bk = np.array([TOMB, 5, TOMB], dtype=np.uint64)
+    bv = np.array([1, 2, 3], dtype=np.uint64)
+    assert t.merge(bk, bv) == 0
+    v, f = t.find(np.array([0, TOMB, 5], dtype=np.uint64))
+    assert f.tolist() == [1, 1, 1] and v.tolist() == [11, 3, 2]  # slot 0 kept, slot 1 = last value
+    assert t.live == 53
+    plain, _ = _filled(oracle_mod, 8, 50, 0, seed=3)
+    assert plain.merge(bk, bv) == 1 and plain.live == 51  # reserved keys skipped
