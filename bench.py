@@ -172,11 +172,12 @@ def make_inputs(device: str):
 class StepRunner:
     """Runs one step; records per-call CUDA events when asked."""
 
-    def __init__(self, cht, inp, host: bool = False, partition: int = 0):
+    def __init__(self, cht, inp, host: bool = False, partition: int = 0, grow_in_kernel: int = 0):
         import torch
 
         self.cht, self.inp, self.host = cht, inp, host
         self.tcfg = {"partition": partition}
+        self.gcfg = dict(self.tcfg, grow_in_kernel=grow_in_kernel)
         self.torch = torch
         wl = inp["wl"]
         n05, n09 = wl["counts"][0.5], wl["counts"][0.9]
@@ -232,7 +233,7 @@ class StepRunner:
         timed("erase", lambda: t.erase(self.keys[:nf], self.codes[:nf]))
         timed("migrate_x2", lambda: t.migrate(2 << LOG2C))
         t.destroy()
-        tg = cht.Table(1 << GROW_LOG2C0, growable=True, config=self.tcfg)
+        tg = cht.Table(1 << GROW_LOG2C0, growable=True, config=self.gcfg)
         timed("grow_insert", lambda: tg.insert(self.keys[:n05], self.vals[:n05], self.codes[:n05]))
         tg.destroy()
 
@@ -488,7 +489,8 @@ def run_gpu(args):
     cht.load_library()
     inp = make_inputs("cuda")
     pmode = {"off": 0, "on": 1}[args.partition]
-    runner = StepRunner(cht, inp, partition=pmode)
+    gk = {"off": 0, "on": 1}[args.grow_in_kernel]
+    runner = StepRunner(cht, inp, partition=pmode, grow_in_kernel=gk)
     for _ in range(args.warmup):
         runner.step()
     torch.cuda.synchronize()
@@ -537,7 +539,7 @@ def run_gpu(args):
     # end-to-end through the same API with pinned host arrays
     e2e = None
     if not args.no_e2e:
-        hrunner = StepRunner(cht, inp, host=True, partition=pmode)
+        hrunner = StepRunner(cht, inp, host=True, partition=pmode, grow_in_kernel=gk)
         hrunner.step()
         torch.cuda.synchronize()
         barrier(pg)
@@ -572,7 +574,7 @@ def run_gpu(args):
                                    "2^26 keys for s in {0.5,1.0,1.25,1.5}, erase 2^27, migrate x2; "
                                    "growable table 2^12 cells taking 2^27 inserts (15 doublings)",
                        "capacity_cells": 1 << LOG2C, "ops_per_step": runner.ops_per_step,
-                       "partition": args.partition,
+                       "partition": args.partition, "grow_in_kernel": args.grow_in_kernel,
                        "l2": "inputs and table far larger than L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "probe_window": "auto by load: finds 2 lanes x 64 B below 0.6, 4 x 64 B above; "
@@ -880,7 +882,8 @@ def run_case(args):
     elif args.case == "grow":
         keys = W.uniform_keys(c // 2, backend="cuda")
         vals = W.values_for(keys, backend="cuda")
-        t = cht.Table(1 << GROW_LOG2C0, growable=True)
+        t = cht.Table(1 << GROW_LOG2C0, growable=True,
+                      config=dict(tcfg, grow_in_kernel={"off": 0, "on": 1}[args.grow_in_kernel]))
         out["grow_insert_ms"] = tm(lambda: t.insert(keys, vals))
         out["capacity"] = t.size()[2]
         t.destroy()
@@ -1311,6 +1314,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--grow-in-kernel", default="off", choices=["off", "on"],
+                    help="table option of the growable table: migrations inside one cooperative launch")
     ap.add_argument("--partition", default="off", choices=["off", "on"],
                     help="table option for every table of the step: hash-partitioned execution of the batches")
     ap.add_argument("--no-e2e", action="store_true")

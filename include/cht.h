@@ -117,7 +117,18 @@ typedef enum {
  * the direct kernel.  Results are the same either way.  Measured on GB300
  * (2^26 cells, 2^25 operations): the reorder and the gather cost about 16 ns
  * per operation, more than the L2 locality saves except for misses at load
- * 0.9 (4.46 vs 4.97 ms), so it is off by default. */
+ * 0.9 (4.46 vs 4.97 ms), so it is off by default.  grow_in_kernel: 1 = an
+ * insert / insert_or_update on a growable table without table options runs as
+ * one cooperative kernel launch that migrates between its operation rounds
+ * (Sec. 4.3.2, the operating threads are recruited for the migration; grid
+ * barriers with bounded waits instead of the host reading the counters back
+ * between chunks); it allocates two tables of the largest capacity the batch
+ * can need for the call and reads the final state back once (one
+ * synchronization of the stream).  A barrier wait longer than grow_spin_us
+ * microseconds (0 = one second) ends the launch with CHT_ERR_TIMEOUT, the
+ * table valid and the batch partly applied.  0 (default) = host-driven chunks.
+ * grow_fault_inject: testing only; 1 = one block of the growth launch never
+ * reaches a barrier, so the others' waits run out. */
 typedef struct {
     int group_width;
     int lane_cells;
@@ -128,6 +139,9 @@ typedef struct {
     int reuse_tombstones;
     int full_key_space;
     int partition;
+    int grow_in_kernel;
+    int grow_spin_us;
+    int grow_fault_inject;
 } cht_config;
 
 /* Create a table of at least `capacity` cells (rounded up to a power of two,

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libcht.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["cht_ops.cu", "cht_migrate.cu", "cht_runtime.cu", "cht_noalloc.cu", "cht_engine.cu", "cht_server.cu",
-           "cht_build.cu", "cht_bulk.cu"]
+           "cht_build.cu", "cht_bulk.cu", "cht_grow.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

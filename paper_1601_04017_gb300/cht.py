@@ -46,7 +46,8 @@ class ChtConfig(ctypes.Structure):
     _fields_ = [("group_width", ctypes.c_int), ("lane_cells", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("migrate_tile", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("iou_aggregate", ctypes.c_int), ("reuse_tombstones", ctypes.c_int),
-                ("full_key_space", ctypes.c_int), ("partition", ctypes.c_int)]
+                ("full_key_space", ctypes.c_int), ("partition", ctypes.c_int), ("grow_in_kernel", ctypes.c_int),
+                ("grow_spin_us", ctypes.c_int), ("grow_fault_inject", ctypes.c_int)]
 
 
 OP_FIND, OP_INSERT, OP_IOU_ADD, OP_IOU_OVERWRITE, OP_ERASE = 0, 1, 2, 3, 4

@@ -122,6 +122,33 @@ u64 compact_scratch_bytes(u32 log2c);
 cudaError_t launch_compact_live(const Cell* cells, u32 log2c, u64* keys_out, u64* vals_out, void* scratch,
                                 cudaStream_t s);
 
+// In-kernel growth (cht_grow.cu, Sec. 4.3.2): one cooperative launch runs an
+// insert / insertOrUpdate batch on a growable table, migrating between
+// operation rounds.  Control words in device memory, zeroed by the host
+// except cur = 0, log2c = the table's, done = 0.
+constexpr unsigned kGrowTimeout = 1u;   // a barrier wait ran out
+constexpr unsigned kGrowMigFail = 2u;   // a migration tile failed: the host redoes that migration
+constexpr unsigned kGrowTooSmall = 4u;  // the targets cannot hold the next capacity
+struct GrowCtl {
+    unsigned int arrived;  // barrier
+    unsigned int gen;
+    unsigned int error;
+    unsigned int cur;      // table buffer: 0 the initial cells, 1 / 2 the targets
+    unsigned int log2c;
+    unsigned int next_log2;
+    unsigned int windows;
+    unsigned int migrations;
+    unsigned int fail_tgt;
+    int action;
+    unsigned long long done;    // operations applied in finished rounds
+    unsigned long long chunk;   // operations of the current round
+    unsigned long long ticket;  // pieces taken in the current round
+};
+u64 grow_border_count(u32 max_log2);
+// group_width 1 (one lane per key, one sector per lane) or 4 (four lanes x one sector).
+cudaError_t launch_grow(const OpArgs& op, Mode mode, Cell* t1, Cell* t2, u32 max_log2, double alpha, GrowCtl* ctl,
+                        u64* border, long long spin_limit, int stall_block, int group_width, cudaStream_t s);
+
 // Compact the live cells into keys_out / vals_out (max_n entries); the count
 // lands in st->export_pos, which must be zero on entry.
 cudaError_t launch_export(const Cell* cells, u32 log2c, u64* keys_out, u64* vals_out, u64 max_n,

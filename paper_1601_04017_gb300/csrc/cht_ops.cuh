@@ -596,9 +596,10 @@ constexpr int kAggSlots = 2048;
 // One operation on the global table by one thread (sector-wise probe).
 template <int MODE, bool kReuse>
 __device__ __forceinline__ unsigned char global_modify(const OpArgs& a, u64 key, u64 d, u64 cap, u32 shift,
-                                                       u64& n_ins, u64& n_reused, u32& sbits) {
+                                                       u64& n_ins, u64& n_reused, u32& sbits,
+                                                       u64 pos = kNoPos, u64 probed = 0) {
     const u64 cmask = cap - 1;
-    u64 pos = home_of(key, shift), probed = 0;
+    if (pos == kNoPos) pos = home_of(key, shift);
     u64 tpos = kNoPos, tprobed = 0;  // tombstone reuse (a.reuse): first one on the path
     for (;;) {
         while (probed < cap) {
@@ -675,8 +676,103 @@ __device__ __forceinline__ unsigned char global_modify(const OpArgs& a, u64 key,
 // operation on a key reports whether the key was present).
 template <int MODE>
 constexpr size_t agg_smem_bytes() {
-    return size_t(kAggSlots) * (8 + 8 + 4) +
+    return size_t(kAggSlots) * (8 + 8 + 4) + size_t(kAggWindow) * 2 +
            ((MODE == kUpdAdd || MODE == kUpdOverwrite) ? size_t(kAggWindow) * 2 + kAggSlots : 0);
+}
+
+// The flush of one window's distinct keys, kAggWindow / kAggBlock at most per
+// thread, with the memory accesses of all of a thread's keys in flight at
+// once: first every key's home sector is loaded, then every key whose sector
+// decides it issues its atomic (the CAS into the empty cell, or the update of
+// its cell), and only the few keys that need more -- a sector without a
+// deciding cell, a CAS lost to another key -- continue one by one with the
+// sector-wise probe from where they stopped.  Same results as probing each key
+// on its own (Algorithm 1 per key; the keys are distinct).
+template <int MODE>
+__device__ __forceinline__ void flush_keys(const OpArgs& a, const u64* fk, const u64* fd, const bool* fv,
+                                           unsigned char* res, u64 cap, u32 shift, u64& n_ins, u64& n_reused,
+                                           u32& sbits) {
+    constexpr int R = kAggWindow / kAggBlock;
+    constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
+    const u64 cmask = cap - 1;
+    u64 pos[R], k0[R], v0[R], k1[R], v1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        k0[r] = v0[r] = k1[r] = v1[r] = 0;
+        pos[r] = 0;
+        if (fv[r]) {
+            pos[r] = home_of(fk[r], shift);
+            ld_pair_cg(a.cells + (pos[r] & ~1ull), k0[r], v0[r], k1[r], v1[r]);
+        }
+    }
+    // 0 done, 1 CAS issued, 2 probe on from pos[r]
+    int st[R];
+    Cell old[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        st[r] = 0;
+        old[r].key = old[r].val = 0;
+        if (!fv[r]) continue;
+        const u64 key = fk[r];
+        const u64 base = pos[r] & ~1ull;
+        int hit = -1;
+        bool match = false;
+        if ((pos[r] & 1ull) == 0 && (k0[r] == key || k0[r] == kEmpty)) {
+            hit = 0;
+            match = k0[r] == key;
+        } else if (k1[r] == key || k1[r] == kEmpty) {
+            hit = 1;
+            match = k1[r] == key;
+        }
+        if (hit < 0) {
+            st[r] = 2;
+            pos[r] = (base + 2) & cmask;
+            continue;
+        }
+        Cell* cp = a.cells + base + hit;
+        if (match) {
+            if (MODE == kIouAdd || MODE == kUpdAdd) atomicAdd(&cp->val, fd[r]);
+            else atomicExch(&cp->val, fd[r]);
+            res[r] = kUpdate ? kYes : kNo;
+        } else if (kUpdate) {
+            res[r] = kNo;  // an empty cell before the key: absent
+        } else {
+            Cell expect;
+            expect.key = kEmpty;
+            expect.val = 0;
+            Cell desired;
+            desired.key = key;
+            desired.val = fd[r];
+            old[r] = cas_cell(cp, expect, desired);
+            st[r] = 1;
+            pos[r] = base + hit;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (st[r] != 1) continue;
+        if (old[r].key == kEmpty && old[r].val == 0) {
+            ++n_ins;
+            res[r] = kYes;
+            st[r] = 0;
+        } else if (old[r].key == fk[r]) {  // another copy of the key won the cell: update it
+            Cell* cp = a.cells + pos[r];
+            if (MODE == kIouAdd) atomicAdd(&cp->val, fd[r]);
+            else atomicExch(&cp->val, fd[r]);
+            res[r] = kNo;
+            st[r] = 0;
+        } else {
+            st[r] = 2;
+            pos[r] = (pos[r] + 1) & cmask;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (st[r] != 2) continue;
+        const u64 probed = (pos[r] - home_of(fk[r], shift)) & cmask;
+        res[r] = global_modify<MODE, false>(a, fk[r], fd[r], cap, shift, n_ins, n_reused, sbits, pos[r],
+                                            probed == 0 ? cap : probed);
+    }
 }
 
 template <int MODE, int DEDUP, bool kReuse>
@@ -688,14 +784,15 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
     u64* const skey = reinterpret_cast<u64*>(agg_smem);
     u64* const sval = skey + kAggSlots;
     u32* const slead = reinterpret_cast<u32*>(sval + kAggSlots);  // window offset of the slot's first op
-    unsigned short* const sslot = reinterpret_cast<unsigned short*>(slead + kAggSlots);  // update: op -> slot
-    unsigned char* const sres = reinterpret_cast<unsigned char*>(sslot + kAggWindow);    // update: slot result
+    unsigned short* const slist = reinterpret_cast<unsigned short*>(slead + kAggSlots);  // the window's claimed slots
+    unsigned short* const sslot = slist + kAggWindow;                                   // update: op -> slot
+    unsigned char* const sres = reinterpret_cast<unsigned char*>(sslot + kAggWindow);   // update: slot result
     const u64 cap = 1ull << a.log2c;
     const u32 shift = 64u - a.log2c;
     const int tid = threadIdx.x;
     u64 n_ins = 0, n_reused = 0;
     u32 sbits = 0;
-    __shared__ u32 s_distinct[2];  // distinct keys of this CTA's window, by window parity
+    __shared__ u32 s_distinct[2];  // distinct keys (claimed slots) of this CTA's window, by window parity
     for (int s = tid; s < kAggSlots; s += kAggBlock) {
         skey[s] = kEmpty;
         sval[s] = 0;
@@ -779,7 +876,7 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
                     else sval[s] = d;
                     slead[s] = off;
                     if (kUpdate) sslot[off] = (unsigned short)s;
-                    if (DEDUP == 1) atomicAdd(&s_distinct[par], 1u);
+                    slist[atomicAdd(&s_distinct[par], 1u)] = (unsigned short)s;
                     break;
                 }
                 if (same) {
@@ -794,20 +891,48 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
         __syncthreads();
         if (DEDUP == 1) {
             // the next window of this CTA combines within warps if this one had
-            // few distinct keys; the other parity's counter is free to reset
+            // few distinct keys
             const u64 ops = a.n - w0 < u64(kAggWindow) ? a.n - w0 : u64(kAggWindow);
             dedup = u64(s_distinct[par]) * 5 < ops;
-            if (tid == 0) s_distinct[par ^ 1] = 0;
         }
-        // flush: one global operation per distinct key of the window
-        for (int s = tid; s < kAggSlots; s += kAggBlock) {
-            const u64 k = skey[s];
-            if (k == kEmpty) continue;
-            const unsigned char r = global_modify<MODE, kReuse>(a, k, sval[s], cap, shift, n_ins, n_reused, sbits);
-            if (kUpdate) sres[s] = r;
-            else if (a.codes) a.codes[w0 + slead[s]] = r;
-            skey[s] = kEmpty;
-            sval[s] = 0;
+        if (tid == 0) s_distinct[par ^ 1] = 0;  // the next window's counter (read by all before it)
+        // flush: one global operation per distinct key of the window (the
+        // dense list of claimed slots; at most kAggWindow / kAggBlock per thread)
+        const u32 nd = s_distinct[par];
+        if (kReuse) {  // tombstone reuse tracks the first tombstone of each path: one key at a time
+            for (u32 j = tid; j < nd; j += kAggBlock) {
+                const u32 sl = slist[j];
+                const unsigned char r =
+                    global_modify<MODE, kReuse>(a, skey[sl], sval[sl], cap, shift, n_ins, n_reused, sbits);
+                if (kUpdate) sres[sl] = r;
+                else if (a.codes) a.codes[w0 + slead[sl]] = r;
+                skey[sl] = kEmpty;
+                sval[sl] = 0;
+            }
+        } else {
+            constexpr int R = kAggWindow / kAggBlock;
+            u64 fk[R], fd[R];
+            bool fv[R];
+            u32 fs[R];
+            unsigned char res[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const u32 j = u32(tid + r * kAggBlock);
+                fv[r] = j < nd;
+                fs[r] = fv[r] ? slist[j] : 0u;
+                fk[r] = fv[r] ? skey[fs[r]] : 0;
+                fd[r] = fv[r] ? sval[fs[r]] : 0;
+                res[r] = kNo;
+            }
+            flush_keys<MODE>(a, fk, fd, fv, res, cap, shift, n_ins, n_reused, sbits);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (!fv[r]) continue;
+                if (kUpdate) sres[fs[r]] = res[r];
+                else if (a.codes) a.codes[w0 + slead[fs[r]]] = res[r];
+                skey[fs[r]] = kEmpty;
+                sval[fs[r]] = 0;
+            }
         }
         __syncthreads();
         if (kUpdate && a.codes) {  // every operation takes its key's result

@@ -171,6 +171,9 @@ cht_config default_config() {
     c.reuse_tombstones = 0;
     c.full_key_space = 0;
     c.partition = 0;
+    c.grow_in_kernel = 0;
+    c.grow_spin_us = 0;
+    c.grow_fault_inject = 0;
     return c;
 }
 
@@ -187,6 +190,9 @@ bool valid_config(const cht_config& c) {
     if (c.reuse_tombstones < 0 || c.reuse_tombstones > 1) return false;
     if (c.full_key_space < 0 || c.full_key_space > 1) return false;
     if (c.partition < 0 || c.partition > 1) return false;
+    if (c.grow_in_kernel < 0 || c.grow_in_kernel > 1 || c.grow_spin_us < 0 || c.grow_fault_inject < 0 ||
+        c.grow_fault_inject > 1)
+        return false;
     return true;
 }
 
@@ -200,6 +206,7 @@ u32 log2_ceil_cap(u64 capacity) {
 
 struct cht_table {
     Cell* cells = nullptr;
+    u64 cells_bytes = 0;  // size of the cells' allocation (at least cap() cells)
     u32 log2c = 0;
     DevState* st = nullptr;
     int growable = 0;
@@ -283,8 +290,9 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
         lib_free(dst, bytes, s);
         return cuda_status(e);
     }
-    lib_free(h->cells, h->cap() * sizeof(Cell), s);
+    lib_free(h->cells, h->cells_bytes, s);
     h->cells = dst;
+    h->cells_bytes = bytes;
     h->log2c = new_log2;
     if (live != ~0ull) {
         h->i_bound = live;
@@ -395,9 +403,102 @@ cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals
     return cuda_status(e);
 }
 
-// insert / insert_or_update with the growth policy of growable tables.
-cht_status run_modify(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals,
-                      unsigned char* codes, u64 n, cudaStream_t s) {
+cht_status run_modify_host(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals,
+                           unsigned char* codes, u64 n, cudaStream_t s);
+
+// In-kernel growth (cht_grow.cu): the whole batch in one cooperative launch
+// that migrates between operation rounds.  The targets take the largest
+// capacity the batch can need (every operation a new key); after the launch
+// the host adopts the final table and frees the rest (one read-back).
+// *handled = false if the batch cannot need a migration (then nothing ran).
+cht_status grow_in_kernel(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals, unsigned char* codes,
+                          u64 n, cudaStream_t s, bool* handled) {
+    *handled = false;
+    const double alpha = h->cfg.alpha;
+    const u64 bound = h->i_bound + n;
+    if (bound <= u64(std::floor(alpha * double(h->cap())))) return CHT_OK;
+    u32 ml = h->log2c;
+    while (ml < kMaxLog2 && u64(std::floor(alpha * double(1ull << ml))) < bound) ++ml;
+    const u64 tbytes = (1ull << ml) * sizeof(Cell);
+    const u64 bbytes = cht::grow_border_count(ml) * sizeof(u64);
+    Cell *t1 = nullptr, *t2 = nullptr;
+    u64* border = nullptr;
+    cht::GrowCtl* ctl = nullptr;
+    cht_status r = lib_alloc(reinterpret_cast<void**>(&t1), tbytes, s);
+    if (r == CHT_OK) r = lib_alloc(reinterpret_cast<void**>(&t2), tbytes, s);
+    if (r == CHT_OK) r = lib_alloc(reinterpret_cast<void**>(&border), bbytes, s);
+    if (r == CHT_OK) r = lib_alloc(reinterpret_cast<void**>(&ctl), sizeof(cht::GrowCtl), s);
+    auto release = [&]() {
+        lib_free(t1, tbytes, s);
+        lib_free(t2, tbytes, s);
+        lib_free(border, bbytes, s);
+        lib_free(ctl, sizeof(cht::GrowCtl), s);
+    };
+    if (r != CHT_OK) {
+        release();
+        return r;
+    }
+    *handled = true;
+    cht::GrowCtl init;
+    std::memset(&init, 0, sizeof(init));
+    init.log2c = h->log2c;
+    cht::OpArgs a;
+    a.cells = h->cells;
+    a.log2c = h->log2c;
+    a.reuse = 0;
+    a.full_keys = 0;
+    a.keys = keys;
+    a.vals = vals;
+    a.vals_out = nullptr;
+    a.codes = codes;
+    a.n = n;
+    a.st = h->st;
+    const Width w = pick_width(h, mode, 0);
+    const long long spin = (h->cfg.grow_spin_us > 0 ? (long long)h->cfg.grow_spin_us : 1000000ll) * 2100;  // ~2.1 GHz
+    cudaError_t e = cudaMemcpyAsync(ctl, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cht::launch_grow(a, mode, t1, t2, ml, alpha, ctl, border, spin, h->cfg.grow_fault_inject ? 1 : -1,
+                             w.g == 1 ? 1 : 4, s);
+    cht::GrowCtl fin;
+    DevState ds;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&fin, ctl, sizeof(fin), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ds, h->st, sizeof(ds), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        release();  // the launch did not run (or its results are unknown): the table is as before
+        return cuda_status(e);
+    }
+    // adopt the table the kernel left (a failed migration's target is dropped)
+    Cell* tabs[3] = {h->cells, t1, t2};
+    const u32 cur = fin.cur > 2 ? 0 : fin.cur;
+    if (cur != 0) {
+        lib_free(h->cells, h->cells_bytes, s);
+        h->cells = tabs[cur];
+        h->cells_bytes = tbytes;
+        h->log2c = fin.log2c;
+        if (cur == 1) t1 = nullptr;
+        else t2 = nullptr;
+    }
+    release();
+    h->i_bound = ds.I;
+    h->i_exact = true;
+    if (fin.error & cht::kGrowTimeout) return CHT_ERR_TIMEOUT;
+    if (fin.error) {
+        // a migration tile could not bound its cluster (or the targets were too
+        // small): the host-driven policy, whose migration has a fallback,
+        // finishes the batch
+        const u64 done = fin.done;
+        return run_modify_host(h, mode, keys + done, vals + done, codes ? codes + done : nullptr, n - done, s);
+    }
+    return CHT_OK;
+}
+
+// insert / insert_or_update with the growth policy of growable tables,
+// driven from the host: read the counters, insert a chunk that fits below
+// the threshold, migrate, repeat.
+cht_status run_modify_host(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals,
+                           unsigned char* codes, u64 n, cudaStream_t s) {
     if (!h->growable) {
         const cht_status r = launch(h, mode, keys, vals, nullptr, codes, n, s);
         h->i_bound += n;  // after the launch: the width choice projects n itself
@@ -452,6 +553,19 @@ cht_status run_modify(cht_table* h, cht::Mode mode, const u64* keys, const u64* 
         done += chunk;
     }
     return CHT_OK;
+}
+
+// insert / insert_or_update on a table: in-kernel growth where configured and
+// possible (a growable table without table options), else host-driven.
+cht_status run_modify(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals, unsigned char* codes, u64 n,
+                      cudaStream_t s) {
+    if (h->growable && h->cfg.grow_in_kernel && !h->cfg.reuse_tombstones && !h->cfg.full_key_space &&
+        cht::mode_fills(mode) && n > 0) {
+        bool handled = false;
+        const cht_status r = grow_in_kernel(h, mode, keys, vals, codes, n, s, &handled);
+        if (handled) return r;
+    }
+    return run_modify_host(h, mode, keys, vals, codes, n, s);
 }
 
 }  // namespace
@@ -715,20 +829,21 @@ cht_status cht_create(uint64_t capacity, int growable, cht_stream_t stream, cht_
     prepare_pool(h->device);
     h->log2c = log2_ceil_cap(capacity < kMinCap ? kMinCap : capacity);
     h->growable = growable ? 1 : 0;
-    cht_status r = lib_alloc(reinterpret_cast<void**>(&h->cells), h->cap() * sizeof(Cell), s);
+    h->cells_bytes = h->cap() * sizeof(Cell);
+    cht_status r = lib_alloc(reinterpret_cast<void**>(&h->cells), h->cells_bytes, s);
     if (r != CHT_OK) {
         delete h;
         return r;
     }
     r = lib_alloc(reinterpret_cast<void**>(&h->st), sizeof(DevState), s);
     if (r != CHT_OK) {
-        lib_free(h->cells, h->cap() * sizeof(Cell), s);
+        lib_free(h->cells, h->cells_bytes, s);
         delete h;
         return r;
     }
     if (cudaMemsetAsync(h->cells, 0, h->cap() * sizeof(Cell), s) != cudaSuccess ||
         cudaMemsetAsync(h->st, 0, sizeof(DevState), s) != cudaSuccess) {
-        lib_free(h->cells, h->cap() * sizeof(Cell), s);
+        lib_free(h->cells, h->cells_bytes, s);
         lib_free(h->st, sizeof(DevState), s);
         delete h;
         return CHT_ERR_CUDA;
@@ -741,7 +856,7 @@ cht_status cht_create(uint64_t capacity, int growable, cht_stream_t stream, cht_
 cht_status cht_destroy(cht_handle h) {
     if (!h) return CHT_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
-    lib_free(h->cells, h->cap() * sizeof(Cell), h->last);
+    lib_free(h->cells, h->cells_bytes, h->last);
     lib_free(h->st, sizeof(DevState), h->last);
     cudaError_t e = cudaStreamSynchronize(h->last);
     delete h;
@@ -996,8 +1111,9 @@ cht_status cht_build(cht_handle h, const uint64_t* keys, const uint64_t* vals, u
                 lib_free(cells, bytes, s);
                 return CHT_ERR_CUDA;
             }
-            lib_free(h->cells, h->cap() * sizeof(Cell), s);
+            lib_free(h->cells, h->cells_bytes, s);
             h->cells = cells;
+            h->cells_bytes = bytes;
             h->log2c = nl;
         }
     }
@@ -1100,8 +1216,9 @@ cht_status cht_merge(cht_handle h, const uint64_t* keys, const uint64_t* vals, u
         lib_free(cells, cbytes, s);
         return cuda_status(e);
     }
-    lib_free(h->cells, h->cap() * sizeof(Cell), s);
+    lib_free(h->cells, h->cells_bytes, s);
     h->cells = cells;
+    h->cells_bytes = cbytes;
     h->log2c = nl;
     h->i_bound = tot;
     h->i_exact = false;
