@@ -518,6 +518,29 @@ uint64_t cht_launch_count(void);
 cht_status cht_find_noalloc(cht_handle h, const uint64_t *keys, uint64_t n, uint64_t *vals_out,
                             uint8_t *found, cht_stream_t stream);
 
+/* Single-call autotuner.  Times one batch of operation `op` (CHT_OP_FIND,
+ * _INSERT, _ERASE, _UPDATE_ADD / _OVERWRITE, _IOU_ADD / _OVERWRITE through the
+ * probe kernel) on this table with every probe window -- group width G in
+ * {1, 2, 4, 8, 16, 32}, cells per lane V in {1, 2, 4} where the kernels exist,
+ * resident CTAs per SM in {occupancy maximum, 4} -- `trials` times each (at
+ * least 3), restoring the table's cells and counters before every trial of a
+ * modifying operation and once more at the end, so the table is unchanged.
+ * results[0 .. *n_results) receive every candidate with the median of its
+ * trials, fastest first (max_results bounds the count).  keys / vals: device
+ * arrays of n entries (vals for operations with values).  Tables with tombstone
+ * reuse or the full key space are not tuned (CHT_ERR_INVALID_ARG).  Scratch of
+ * the table's size is allocated for the call.  The library's automatic window
+ * rule comes from running this over table sizes and loads (the generator is
+ * paper_1601_04017_gb300/tune.py). */
+typedef struct {
+    int group_width;
+    int lane_cells;
+    int ctas_per_sm;  /* 0 = occupancy maximum */
+    double ms;        /* median over the trials */
+} cht_tune_result;
+cht_status cht_tune(cht_handle h, int op, const uint64_t *keys, const uint64_t *vals, uint64_t n, int trials,
+                    cht_tune_result *results, uint32_t max_results, uint32_t *n_results, cht_stream_t stream);
+
 /* Static string for a status code. */
 const char *cht_status_string(cht_status s);
 

@@ -308,7 +308,35 @@ cht_status do_migrate(cht_table* h, u32 new_log2, u64 live, cudaStream_t s) {
 // probes at high load want wider windows so fewer dependent steps are needed.
 struct Width {
     int g, v;
+    int ctas = 0;  // resident CTAs per SM from the measured rule (0 = the configured / maximum)
 };
+
+// The measured rule (cht_tuned.inc, written by tune.py): per operation kind,
+// range of log2 c and load band, the fastest window of the tuning sweep.
+struct TunedWindow {
+    int mode;
+    u32 log2_lo, log2_hi;
+    float load_lo, load_hi;
+    int g, v, ctas;
+};
+const TunedWindow kTuned[] = {
+#include "cht_tuned.inc"
+    {-1, 0, 0, 0.f, 0.f, 0, 0, 0}};
+
+bool tuned_window(cht::Mode mode, u32 log2c, double load, Width* w) {
+    // insertOrUpdate tunes like insert, update (overwrite) like update (add)
+    const int m = (mode == cht::kIouAdd || mode == cht::kIouOverwrite) ? int(cht::kInsert)
+                  : mode == cht::kUpdOverwrite                          ? int(cht::kUpdAdd)
+                                                                        : int(mode);
+    for (const TunedWindow& t : kTuned) {
+        if (t.mode != m || log2c < t.log2_lo || log2c > t.log2_hi || load < t.load_lo || load >= t.load_hi) continue;
+        w->g = t.g;
+        w->v = t.v;
+        w->ctas = t.ctas;
+        return true;
+    }
+    return false;
+}
 
 Width pick_width(const cht_table* h, cht::Mode mode, u64 n) {
     Width w{h->cfg.group_width, h->cfg.lane_cells};
@@ -325,6 +353,7 @@ Width pick_width(const cht_table* h, cht::Mode mode, u64 n) {
         if (mode == cht::kInsert) filled += n;
         if (filled > h->cap()) filled = h->cap();
         const double load = double(filled) / double(h->cap());
+        if (h->cfg.lane_cells == 0 && tuned_window(mode, h->log2c, load, &w)) return w;
         if (load < 0.6) {
             w.g = mode == cht::kFind ? 2 : 1;
             if (w.v == 0) w.v = mode == cht::kFind ? 4 : 2;
@@ -365,7 +394,7 @@ cudaError_t run_kernel(const cht::OpArgs& a, void* ctx, cudaStream_t s) {
     if (aggregated(k->h, k->mode))
         return cht::launch_iou_aggregated(k->mode, a, k->h->cfg.iou_aggregate == 2, k->h->cfg.ctas_per_sm, s);
     const Width w = pick_width(k->h, k->mode, k->n);
-    return cht::launch_op(k->mode, a, w.g, w.v, k->h->cfg.ctas_per_sm, s);
+    return cht::launch_op(k->mode, a, w.g, w.v, k->h->cfg.ctas_per_sm ? k->h->cfg.ctas_per_sm : w.ctas, s);
 }
 
 cudaError_t run_kernel_ordered(const cht::OpArgs& a, void* ctx, cudaStream_t s) {
@@ -1375,6 +1404,102 @@ cht_status cht_clear(cht_handle h, cht_stream_t stream) {
     if (cudaMemsetAsync(h->st, 0, sizeof(DevState), s) != cudaSuccess) return CHT_ERR_CUDA;
     h->i_bound = 0;
     h->i_exact = true;
+    return CHT_OK;
+}
+
+cht_status cht_tune(cht_handle h, int op, const uint64_t* keys, const uint64_t* vals, uint64_t n, int trials,
+                    cht_tune_result* results, uint32_t max_results, uint32_t* n_results, cht_stream_t stream) {
+    if (!h || !keys || n == 0 || !results || !n_results || op < CHT_OP_FIND || op > CHT_OP_UPDATE_OVERWRITE)
+        return CHT_ERR_INVALID_ARG;
+    const cht::Mode mode = cht::Mode(op);
+    if (cht::mode_has_vals(mode) && !vals) return CHT_ERR_INVALID_ARG;
+    if (h->cfg.reuse_tombstones || h->cfg.full_key_space) return CHT_ERR_INVALID_ARG;
+    if (is_host_pointer(keys) || (vals && is_host_pointer(vals))) return CHT_ERR_INVALID_ARG;
+    if (trials < 3) trials = 3;
+    *n_results = 0;
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last = s;
+    const bool modify = mode != cht::kFind;
+    const u64 tbytes = h->cap() * sizeof(Cell);
+    // scratch: the outputs, and a copy of the table for the restores
+    const u64 obytes = ((n * 8 + 255) & ~255ull) + ((n + 255) & ~255ull);
+    const u64 sbytes = obytes + (modify ? tbytes + 256 : 0);
+    unsigned char* scratch = nullptr;
+    cht_status r = lib_alloc(reinterpret_cast<void**>(&scratch), sbytes, s);
+    if (r != CHT_OK) return r;
+    u64* vout = reinterpret_cast<u64*>(scratch);
+    unsigned char* codes = scratch + ((n * 8 + 255) & ~255ull);
+    Cell* save_cells = modify ? reinterpret_cast<Cell*>(scratch + obytes) : nullptr;
+    DevState* save_st = modify ? reinterpret_cast<DevState*>(scratch + obytes + tbytes) : nullptr;
+    auto restore = [&](bool save) -> cudaError_t {
+        if (!modify) return cudaSuccess;
+        cudaError_t e = cudaMemcpyAsync(save ? static_cast<void*>(save_cells) : static_cast<void*>(h->cells),
+                                        save ? static_cast<void*>(h->cells) : static_cast<void*>(save_cells), tbytes,
+                                        cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(save ? static_cast<void*>(save_st) : static_cast<void*>(h->st),
+                                save ? static_cast<void*>(h->st) : static_cast<void*>(save_st), sizeof(DevState),
+                                cudaMemcpyDeviceToDevice, s);
+        return e;
+    };
+    struct Cand {
+        int g, v;
+    };
+    static const Cand cands[] = {{1, 2},  {1, 4}, {2, 1}, {2, 2}, {2, 4},  {4, 1},  {4, 2},
+                                 {4, 4},  {8, 1}, {8, 2}, {8, 4}, {16, 1}, {16, 2}, {32, 1}};
+    static const int ctas[] = {0, 4};
+    cht::OpArgs a;
+    a.cells = h->cells;
+    a.log2c = h->log2c;
+    a.reuse = 0;
+    a.full_keys = 0;
+    a.keys = reinterpret_cast<const u64*>(keys);
+    a.vals = cht::mode_has_vals(mode) ? reinterpret_cast<const u64*>(vals) : nullptr;
+    a.vals_out = mode == cht::kFind ? vout : nullptr;
+    a.codes = codes;
+    a.n = n;
+    a.st = h->st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = restore(true);
+    std::vector<cht_tune_result> all;
+    for (const Cand& c : cands) {
+        for (int ct : ctas) {
+            std::vector<double> t;
+            for (int k = 0; k < trials && e == cudaSuccess; ++k) {
+                if (k > 0 || !all.empty()) e = restore(false);
+                float ms = 0;
+                if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) e = cht::launch_op(mode, a, c.g, c.v, ct, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                t.push_back(ms);
+            }
+            if (e != cudaSuccess) break;
+            std::sort(t.begin(), t.end());
+            cht_tune_result res;
+            res.group_width = c.g;
+            res.lane_cells = c.v;
+            res.ctas_per_sm = ct;
+            res.ms = t[t.size() / 2];
+            all.push_back(res);
+        }
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = restore(false);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    lib_free(scratch, sbytes, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    std::stable_sort(all.begin(), all.end(),
+                     [](const cht_tune_result& x, const cht_tune_result& y) { return x.ms < y.ms; });
+    const u32 m = u32(std::min<size_t>(all.size(), max_results));
+    for (u32 i = 0; i < m; ++i) results[i] = all[i];
+    *n_results = m;
     return CHT_OK;
 }
 
