@@ -676,7 +676,7 @@ __device__ __forceinline__ unsigned char global_modify(const OpArgs& a, u64 key,
 // operation on a key reports whether the key was present).
 template <int MODE>
 constexpr size_t agg_smem_bytes() {
-    return size_t(kAggSlots) * (8 + 8 + 4) + size_t(kAggWindow) * 2 +
+    return size_t(kAggSlots) * (8 + 8 + 2) + size_t(kAggWindow) * 2 +
            ((MODE == kUpdAdd || MODE == kUpdOverwrite) ? size_t(kAggWindow) * 2 + kAggSlots : 0);
 }
 
@@ -776,15 +776,16 @@ __device__ __forceinline__ void flush_keys(const OpArgs& a, const u64* fk, const
 }
 
 template <int MODE, int DEDUP, bool kReuse>
-__global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
+__global__ void __launch_bounds__(kAggBlock, 5) iou_agg_kernel(OpArgs a) {
     pdl_enter();
     constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
     constexpr bool kAdd = MODE == kIouAdd || MODE == kUpdAdd;
     extern __shared__ __align__(16) unsigned char agg_smem[];
     u64* const skey = reinterpret_cast<u64*>(agg_smem);
     u64* const sval = skey + kAggSlots;
-    u32* const slead = reinterpret_cast<u32*>(sval + kAggSlots);  // window offset of the slot's first op
-    unsigned short* const slist = reinterpret_cast<unsigned short*>(slead + kAggSlots);  // the window's claimed slots
+    // window offset of the slot's first op (< kAggWindow: 16 bits)
+    unsigned short* const slead = reinterpret_cast<unsigned short*>(sval + kAggSlots);
+    unsigned short* const slist = slead + kAggSlots;  // the window's claimed slots
     unsigned short* const sslot = slist + kAggWindow;                                   // update: op -> slot
     unsigned char* const sres = reinterpret_cast<unsigned char*>(sslot + kAggWindow);   // update: slot result
     const u64 cap = 1ull << a.log2c;
@@ -874,7 +875,7 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
                 if (mine) {
                     if (kAdd) atomicAdd(reinterpret_cast<unsigned long long*>(sval + s), d);
                     else sval[s] = d;
-                    slead[s] = off;
+                    slead[s] = (unsigned short)off;
                     if (kUpdate) sslot[off] = (unsigned short)s;
                     slist[atomicAdd(&s_distinct[par], 1u)] = (unsigned short)s;
                     break;

@@ -323,3 +323,88 @@ def test_sliding_window_2p24_live(cuda_lib, oracle_mod):
     assert caps == ref["caps"]
     assert size == ref["size"] and size[0] == win
     _assert_same_pairs(gk, gv, *ref["pairs"])
+
+
+# ---------------------------------------------------------------------------
+# batched: 4096 tables (element counts log-uniform 2^8..2^20), every batch in
+# one engine launch; every table checked against the oracle
+# ---------------------------------------------------------------------------
+def _oracle_tables(oracle_mod, wl, tabs, keys, vals, vout, codes):
+    """Run the oracle over the batches of `tabs` in order; return the first
+    mismatch found (or None) and the final contents per table."""
+    bad, contents = None, {}
+    for t in tabs:
+        o = oracle_mod.OracleTable(int(wl["capacity"][t]))
+        for b in wl["by_table"][t]:
+            o0, o1 = int(wl["offsets"][b]), int(wl["offsets"][b + 1])
+            k = keys[o0:o1]
+            op = int(wl["op"][b])
+            if op == W.OP_FIND:
+                ev, ef = o.find(k)
+                if bad is None and not (np.array_equal(ev, vout[o0:o1]) and np.array_equal(ef, codes[o0:o1])):
+                    bad = f"table {t} batch {b}: find results differ"
+            elif op == W.OP_INSERT:
+                oc = o.insert(k, vals[o0:o1])
+                if bad is None and not np.array_equal(oc, codes[o0:o1]):
+                    bad = f"table {t} batch {b}: insert codes differ"
+            else:
+                o.insert_or_update(k, vals[o0:o1], oracle_mod.ADD)
+        ok, ov = o.export()
+        order = np.argsort(ok)
+        contents[t] = (ok[order], ov[order])
+        o.close()
+    return bad, contents
+
+
+def test_batched_4096_tables_one_launch(cuda_lib, oracle_mod):
+    import torch
+
+    wl = W.batched_workload(4096, 8, 20, seed=W.SEED_TABLES)
+    nb = len(wl["n"])
+    total = int(wl["offsets"][-1])
+    keys = torch.empty(total, dtype=torch.int64, device="cuda")
+    vals = torch.empty(total, dtype=torch.int64, device="cuda")
+    b0 = 0
+    while b0 < nb:  # generated in pieces of about 2^27 operations
+        b1 = int(np.searchsorted(wl["offsets"], wl["offsets"][b0] + (1 << 27), side="right")) - 1
+        b1 = min(max(b1, b0 + 1), nb)
+        k, v = W.batched_keys(wl, b0, b1, backend="cuda")
+        keys[wl["offsets"][b0]:wl["offsets"][b1]] = k
+        vals[wl["offsets"][b0]:wl["offsets"][b1]] = v
+        del k, v
+        b0 = b1
+    vout = torch.zeros(total, dtype=torch.int64, device="cuda")
+    codes = torch.full((total,), 255, dtype=torch.uint8, device="cuda")
+    tables = [cuda_lib.Table(int(c)) for c in wl["capacity"]]
+    segs = []
+    for b in range(nb):
+        o0, o1 = int(wl["offsets"][b]), int(wl["offsets"][b + 1])
+        op = int(wl["op"][b])
+        segs.append((tables[int(wl["table"][b])], op, keys[o0:o1], vals[o0:o1] if op != W.OP_FIND else None,
+                     vout[o0:o1] if op == W.OP_FIND else None, codes[o0:o1]))
+    plan = cuda_lib.Plan(segs)
+    l0 = cuda_lib.launch_count()
+    plan.launch()
+    assert plan.status() == 0
+    assert cuda_lib.launch_count() - l0 == 1
+    hk, hv = _host(keys), _host(vals)
+    hvo, hc = _host(vout), codes.cpu().numpy()
+    del keys, vals, vout, codes
+    order = np.argsort(wl["table"], kind="stable")
+    starts = np.searchsorted(wl["table"][order], np.arange(4097))
+    wl["by_table"] = [order[starts[t]:starts[t + 1]] for t in range(4096)]
+    groups = [list(range(i, 4096, 16)) for i in range(16)]
+    with cf.ThreadPoolExecutor(16) as ex:
+        futs = [ex.submit(_oracle_tables, oracle_mod, wl, g, hk, hv, hvo, hc) for g in groups]
+        results = [f.result() for f in futs]
+    for bad, _ in results:
+        assert bad is None, bad
+    for _, contents in results:
+        for t, (ok, ov) in contents.items():
+            gk, gv = tables[t].export()
+            gk, gv = _host(gk), _host(gv)
+            o = np.argsort(gk)
+            assert np.array_equal(gk[o], ok) and np.array_equal(gv[o], ov), f"table {t}: contents differ"
+    plan.destroy()
+    for t in tables:
+        t.destroy()
