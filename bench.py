@@ -548,10 +548,15 @@ def run_gpu(args):
             hrunner.step()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        # one more step with CUDA events around each call (not part of the timing)
+        hev: dict = {}
+        hrunner.step(hev)
+        torch.cuda.synchronize()
+        e2e_calls = {k: round(statistics.mean(a.elapsed_time(b) for a, b in v), 3) for k, v in hev.items()}
         el = max_over_ranks(pg, el, device="cuda")
         e2e = {"value": round(hrunner.ops_per_step * max(1, args.e2e_steps) * world / el / 1e6, 1),
                "unit": UNIT, "h2d_bytes_per_step": hrunner.h2d, "d2h_bytes_per_step": hrunner.d2h,
-               "steps": max(1, args.e2e_steps), "pinned_copy_gbs": pinned_copy_gbs()}
+               "steps": max(1, args.e2e_steps), "pinned_copy_gbs": pinned_copy_gbs(), "calls_ms": e2e_calls}
         del hrunner
 
     lat = latency_percentiles(cht, inp, args.latency_reps) if args.latency_reps > 0 else None

@@ -115,8 +115,8 @@ cudaError_t launch_agg(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
         cudaError_t e = cudaFuncSetAttribute(iou_agg_kernel<MODE, WD, RE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smem));
         if (e != cudaSuccess) return e;
-        // all of the unified L1 / shared memory as shared memory: the CTAs per
-        // SM are limited by it (38 KB each)
+        // as much of the unified L1 / shared memory as shared memory as the
+        // kernel can use (38 KB per CTA)
         e = cudaFuncSetAttribute(iou_agg_kernel<MODE, WD, RE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iou_agg_kernel<MODE, WD, RE>, kAggBlock, smem);

@@ -776,7 +776,7 @@ __device__ __forceinline__ void flush_keys(const OpArgs& a, const u64* fk, const
 }
 
 template <int MODE, int DEDUP, bool kReuse>
-__global__ void __launch_bounds__(kAggBlock, 5) iou_agg_kernel(OpArgs a) {
+__global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
     pdl_enter();
     constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
     constexpr bool kAdd = MODE == kIouAdd || MODE == kUpdAdd;
