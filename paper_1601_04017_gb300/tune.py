@@ -3,7 +3,8 @@
 Runs the single-call autotuner (cht_tune: every probe window -- group width G,
 cells per lane V, resident CTAs per SM -- timed with at least three trials,
 median kept) on tables of 2^20, 2^24 and 2^28 cells at loads 0.25, 0.5, 0.7
-and 0.9, for find (half hits, half misses), insert (the fresh keys that fill
+and 0.9, for find (a batch of hits and a batch of misses, ranked by the sum of
+the two), insert (the fresh keys that fill
 the table from the previous load level to this one), erase and update
 (present keys), and writes
 
@@ -113,7 +114,14 @@ def main():
                 5: (present, vals[: present.numel()]),
             }
             for op, (k, v) in batches.items():
-                res = res_ins if op == 1 else tune_one(lib, t, op, k, v, args.trials)
+                if op == 0:
+                    # finds: a batch of hits and a batch of misses, each window
+                    # ranked by the sum of its two times
+                    rh = {r[:3]: r[3] for r in tune_one(lib, t, 0, present, None, args.trials)}
+                    rm = {r[:3]: r[3] for r in tune_one(lib, t, 0, fresh, None, args.trials)}
+                    res = sorted(((w[0], w[1], w[2], rh[w] + rm[w]) for w in rh), key=lambda r: r[3])
+                else:
+                    res = res_ins if op == 1 else tune_one(lib, t, op, k, v, args.trials)
                 best = res[0]
                 base = next(r for r in res if (r[0], r[1], r[2]) == builtin_window(op, ld))
                 g, vv, ct, ms = best if best[3] < (1.0 - MARGIN) * base[3] else base
