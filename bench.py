@@ -214,10 +214,12 @@ class StepRunner:
                 fn()
                 return
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h0 = time.perf_counter()
             a.record(s)
             fn()
             b.record(s)
             events.setdefault(name, []).append((a, b))
+            events.setdefault("_host_ms", {}).setdefault(name, []).append((time.perf_counter() - h0) * 1e3)
 
         t = cht.Table(1 << LOG2C, config=self.tcfg)
         timed("insert_0.5", lambda: t.insert(self.keys[:n05], self.vals[:n05], self.codes[:n05]))
@@ -530,6 +532,7 @@ def run_gpu(args):
     counts = op_counts(inp)
     bpo = per_op_bytes(inp)
     peak, peak_kind = load_peaks()
+    events.pop("_host_ms", None)
     breakdown = {}
     for name, evs in events.items():
         t_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
@@ -562,11 +565,14 @@ def run_gpu(args):
         hev: dict = {}
         hrunner.step(hev)
         torch.cuda.synchronize()
+        host_ms = hev.pop("_host_ms", {})
         e2e_calls = {k: round(statistics.mean(a.elapsed_time(b) for a, b in v), 3) for k, v in hev.items()}
+        e2e_host = {k: round(statistics.mean(v), 3) for k, v in host_ms.items()}
         el = max_over_ranks(pg, el, device="cuda")
         e2e = {"value": round(hrunner.ops_per_step * max(1, args.e2e_steps) * world / el / 1e6, 1),
                "unit": UNIT, "h2d_bytes_per_step": hrunner.h2d, "d2h_bytes_per_step": hrunner.d2h,
-               "steps": max(1, args.e2e_steps), "pinned_copy_gbs": pinned_copy_gbs(), "calls_ms": e2e_calls}
+               "steps": max(1, args.e2e_steps), "pinned_copy_gbs": pinned_copy_gbs(), "calls_ms": e2e_calls,
+               "calls_host_ms": e2e_host}
         del hrunner
 
     lat = latency_percentiles(cht, inp, args.latency_reps) if args.latency_reps > 0 else None

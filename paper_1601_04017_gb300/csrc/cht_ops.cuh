@@ -776,7 +776,7 @@ __device__ __forceinline__ void flush_keys(const OpArgs& a, const u64* fk, const
 }
 
 template <int MODE, int DEDUP, bool kReuse>
-__global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
+__global__ void __launch_bounds__(kAggBlock, 4) iou_agg_kernel(OpArgs a) {
     pdl_enter();
     constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
     constexpr bool kAdd = MODE == kIouAdd || MODE == kUpdAdd;
@@ -816,17 +816,29 @@ __global__ void __launch_bounds__(kAggBlock) iou_agg_kernel(OpArgs a) {
         const u64 w0 = w * kAggWindow;
         const int par = int(round & 1);
         if (a.ticket && tid == 0) s_next[(round + 1) & 1] = atomicAdd(a.ticket, 1ull);
+        // this thread's operations of the window, all loads issued before any
+        // is used (the loads are volatile asm, which the compiler keeps in
+        // program order: interleaved with the folding below they would cost one
+        // memory round trip each)
+        constexpr int kPer = kAggWindow / kAggBlock;
+        u64 wk[kPer], wv[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const u64 idx = w0 + u32(j * kAggBlock + tid);
+            wk[j] = idx < a.n ? ld_stream(a.keys + idx) : 0;
+            wv[j] = idx < a.n ? ld_stream(a.vals + idx) : 0;
+        }
         // fold the window's operations into the slots
 #pragma unroll
-        for (int j = 0; j < kAggWindow / kAggBlock; ++j) {
+        for (int j = 0; j < kPer; ++j) {
             const u32 off = u32(j * kAggBlock + tid);
             const u64 idx = w0 + off;
             bool valid = idx < a.n;
             u64 key = 0, d = 0;
             if (kUpdate) sslot[off] = 0xffffu;
             if (valid) {
-                key = ld_stream(a.keys + idx);
-                d = ld_stream(a.vals + idx);
+                key = wk[j];
+                d = wv[j];
                 if (is_reserved(key)) {
                     if (a.full_keys) {
                         const unsigned char r = special_op<MODE>(a.st, key, d, nullptr);
