@@ -1321,7 +1321,7 @@ def run_serving(args):
                                             "p50_ms": round(float(np.percentile(blat, 50)) * 1e3, 3),
                                             "p99_ms": round(float(np.percentile(blat, 99)) * 1e3, 3)},
                                "results_equal_served": bool(same)}
-        for frac in args.serving_loads:
+        for frac in (args.serving_loads if args.serving_baseline_loads is None else args.serving_baseline_loads):
             arr = W.poisson_arrivals(nreq, frac * cap_rps)
             blat, bmk, _ = single_calls(arr)
             out["single_calls"][f"load_{frac}"] = {
@@ -1372,6 +1372,8 @@ def main():
                     help="find / insert / insertOrUpdate(add) / erase fractions of the requests")
     ap.add_argument("--no-serving-baseline", action="store_true",
                     help="skip the single-call baseline of the serving workload")
+    ap.add_argument("--serving-baseline-loads", type=float, nargs="*", default=None,
+                    help="Poisson loads for the single-call baseline (default: the served loads)")
     ap.add_argument("--serving-trace", default="",
                     help="save each run's per-step server trace to <prefix>_<run>.npy")
     ap.add_argument("--serving-arrays", default="pinned", choices=["pinned", "device"],

@@ -794,6 +794,8 @@ __global__ void __launch_bounds__(kAggBlock, 4) iou_agg_kernel(OpArgs a) {
     u64 n_ins = 0, n_reused = 0;
     u32 sbits = 0;
     __shared__ u32 s_distinct[2];  // distinct keys (claimed slots) of this CTA's window, by window parity
+    __shared__ unsigned long long s_wsum[kAggBlock];  // warp pre-reduction: per lane, its group's sum
+    s_wsum[tid] = 0;
     for (int s = tid; s < kAggSlots; s += kAggBlock) {
         skey[s] = kEmpty;
         sval[s] = 0;
@@ -857,17 +859,19 @@ __global__ void __launch_bounds__(kAggBlock, 4) iou_agg_kernel(OpArgs a) {
                 const u32 same = __match_any_sync(vm, key);
                 const int lane = tid & 31;
                 if (kAdd) {
-                    u32 rem = same;
-                    u64 total = 0;
-                    while (__any_sync(vm, rem != 0)) {
-                        const int src = rem ? __ffs(rem) - 1 : lane;
-                        const u64 x = __shfl_sync(vm, d, src);
-                        if (rem) {
-                            total += x;
-                            rem &= rem - 1u;
-                        }
+                    // the group's sum: every lane adds its value into its
+                    // leader's word of a warp-private scratch (a few cycles of
+                    // shared-memory atomics instead of a shuffle round per
+                    // member), the leader takes it and clears the word
+                    const int lead = __ffs(same) - 1;
+                    unsigned long long* const ws = s_wsum + (tid & ~31);
+                    atomicAdd(ws + lead, d);
+                    __syncwarp(vm);
+                    if (lane == lead) {
+                        d = ws[lead];
+                        ws[lead] = 0;
                     }
-                    d = total;
+                    __syncwarp(vm);
                 }
                 if (lane != __ffs(same) - 1) {
                     if (a.codes) a.codes[idx] = kNo;
@@ -906,7 +910,7 @@ __global__ void __launch_bounds__(kAggBlock, 4) iou_agg_kernel(OpArgs a) {
             // the next window of this CTA combines within warps if this one had
             // few distinct keys
             const u64 ops = a.n - w0 < u64(kAggWindow) ? a.n - w0 : u64(kAggWindow);
-            dedup = u64(s_distinct[par]) * 5 < ops;
+            dedup = u64(s_distinct[par]) * 2 < ops;
         }
         if (tid == 0) s_distinct[par ^ 1] = 0;  // the next window's counter (read by all before it)
         // flush: one global operation per distinct key of the window (the
