@@ -763,7 +763,7 @@ def run_case(args):
     cht.load_library()
     log2c, load = args.case_log2c, args.case_load
     c = 1 << log2c
-    tcfg = {"partition": {"off": 0, "on": 1}[args.partition]}
+    tcfg = {"partition": {"off": 0, "on": 1}[args.partition], "iou_aggregate": args.case_agg}
     s = torch.cuda.current_stream()
 
     def tm(fn):
@@ -774,7 +774,8 @@ def run_case(args):
         b.synchronize()
         return round(a.elapsed_time(b), 4)
 
-    out = {"case": args.case, "log2c": log2c, "load": load, "partition": args.partition}
+    out = {"case": args.case, "log2c": log2c, "load": load, "partition": args.partition, "agg": args.case_agg,
+           "s": args.case_s}
     if args.case == "shrink":
         # the same shrink once untimed, so the timed one does not include the
         # memory pool's first growth to these sizes
@@ -1254,23 +1255,30 @@ def run_serving(args):
     def same_results(served_vout, served_codes, served_contents, base_contents):
         """Finds bit-exact per operation; insert / insertOrUpdate / erase codes
         summed per (request, key) (which of equal keys in a request reports
-        the change is free); every final table equal."""
-        ops = wl["op"]
-        rid = np.repeat(np.arange(nreq), wl["n"])
-        is_find = ops[rid] == W.OP_FIND
-        sv, sc = served_vout.cpu().numpy(), served_codes.cpu().numpy()
-        bv, bc = base_vout.cpu().numpy(), base_codes.cpu().numpy()
-        if not (np.array_equal(sv[is_find], bv[is_find]) and np.array_equal(sc[is_find], bc[is_find])):
-            return False
-        m = ~is_find
-        kk = keys_h.cpu().numpy().view(np.uint64)[m]
-        rr = rid[m]
-        order = np.lexsort((kk, rr))
-        kk, rr = kk[order], rr[order]
-        starts = np.concatenate([[0], np.nonzero((kk[1:] != kk[:-1]) | (rr[1:] != rr[:-1]))[0] + 1])
-        if not np.array_equal(np.add.reduceat(sc[m][order].astype(np.int64), starts),
-                              np.add.reduceat(bc[m][order].astype(np.int64), starts)):
-            return False
+        the change is free); every final table equal.  Compared in pieces of
+        about 2^26 operations (host memory)."""
+        r0 = 0
+        while r0 < nreq:
+            r1 = int(np.searchsorted(wl["offsets"], wl["offsets"][r0] + (1 << 26), side="right")) - 1
+            r1 = min(max(r1, r0 + 1), nreq)
+            o0, o1 = int(wl["offsets"][r0]), int(wl["offsets"][r1])
+            rid = np.repeat(np.arange(r0, r1), wl["n"][r0:r1])
+            is_find = wl["op"][rid] == W.OP_FIND
+            sv, sc = served_vout[o0:o1].cpu().numpy(), served_codes[o0:o1].cpu().numpy()
+            bv, bc = base_vout[o0:o1].cpu().numpy(), base_codes[o0:o1].cpu().numpy()
+            if not (np.array_equal(sv[is_find], bv[is_find]) and np.array_equal(sc[is_find], bc[is_find])):
+                return False
+            m = ~is_find
+            kk = keys_h[o0:o1].cpu().numpy().view(np.uint64)[m]
+            rr = rid[m]
+            if kk.size:
+                order = np.lexsort((kk, rr))
+                kk, rr = kk[order], rr[order]
+                starts = np.concatenate([[0], np.nonzero((kk[1:] != kk[:-1]) | (rr[1:] != rr[:-1]))[0] + 1])
+                if not np.array_equal(np.add.reduceat(sc[m][order].astype(np.int64), starts),
+                                      np.add.reduceat(bc[m][order].astype(np.int64), starts)):
+                    return False
+            r0 = r1
         return all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
                    for a, b in zip(served_contents, base_contents))
 
@@ -1352,6 +1360,8 @@ def main():
     ap.add_argument("--case-log2c", type=int, default=26)
     ap.add_argument("--case-load", type=float, default=0.9)
     ap.add_argument("--case-s", type=float, default=1.0)
+    ap.add_argument("--case-agg", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="insertOrUpdate aggregation of the case's tables (table option iou_aggregate)")
     ap.add_argument("--probe-random-access", action="store_true",
                     help="measure the HBM random-read ceiling instead of the benchmark")
     ap.add_argument("--workload", default="bounded", choices=["bounded", "batched", "serving"],

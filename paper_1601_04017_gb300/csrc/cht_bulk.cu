@@ -315,6 +315,103 @@ struct PLayout {
 
 u64 partition_scratch_bytes(u64 n, PartitionIO io) { return PLayout(n, io).total; }
 
+namespace {
+
+// Scratch of a two-pass (16-bit) sort of the batch.
+struct SLayout {
+    u64 ntiles, hist_n, parts;
+    u64 o_ha, o_hb, o_pa, o_pb, o_ka, o_va, o_posa, o_kb, o_vb, o_posb, o_ca, o_cb, total;
+    SLayout(u64 n, bool codes) {
+        ntiles = (n + kPTile - 1) / kPTile;
+        hist_n = u64(kPBins) * ntiles + 1;
+        parts = scan_partials(hist_n);
+        u64 o = 0;
+        auto take = [&](u64 bytes) {
+            const u64 at = o;
+            o = align256(o + bytes);
+            return at;
+        };
+        o_ha = take(hist_n * 4);
+        o_hb = take(hist_n * 4);
+        o_pa = take(parts * 4);
+        o_pb = take(parts * 4);
+        o_ka = take(n * 8);
+        o_va = take(n * 8);
+        o_posa = take(n * 2);
+        o_kb = take(n * 8);
+        o_vb = take(n * 8);
+        o_posb = take(n * 2);
+        o_ca = codes ? take(n) : 0;
+        o_cb = codes ? take(n) : 0;
+        total = o;
+    }
+};
+
+// One stable 8-bit pass: histogram, scan, scatter of keys and values.
+cudaError_t sort_pass(const u64* keys, const u64* vals, u64 n, u32 shift, u32* hist, u64 hist_n, u32* part,
+                      u64 ntiles, u64* okeys, u64* ovals, unsigned short* opos, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(hist + hist_n - 1, 0, sizeof(u32), s);
+    if (e != cudaSuccess) return e;
+    part_hist_kernel<<<unsigned(ntiles), kPThreads, 0, s>>>(keys, n, shift, hist, ntiles);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive_u32(hist, hist_n, part, s)) != cudaSuccess) return e;
+    constexpr size_t sm = scatter_smem<true>();
+    static bool attr = false;
+    if (!attr) {
+        if ((e = cudaFuncSetAttribute(part_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(sm))) != cudaSuccess)
+            return e;
+        attr = true;
+    }
+    part_scatter_kernel<true><<<unsigned(ntiles), kPThreads, sm, s>>>(keys, vals, n, shift, hist, ntiles, okeys,
+                                                                      ovals, opos);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+u64 sorted16_scratch_bytes(u64 n, bool codes) { return SLayout(n, codes).total; }
+
+cudaError_t launch_sorted16(const OpArgs& a, void* scratch, PartitionRun run, void* ctx, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    const bool codes = a.codes != nullptr;
+    const SLayout L(a.n, codes);
+    unsigned char* b = static_cast<unsigned char*>(scratch);
+    u32* ha = reinterpret_cast<u32*>(b + L.o_ha);
+    u32* hb = reinterpret_cast<u32*>(b + L.o_hb);
+    u64* ka = reinterpret_cast<u64*>(b + L.o_ka);
+    u64* va = reinterpret_cast<u64*>(b + L.o_va);
+    unsigned short* pa = reinterpret_cast<unsigned short*>(b + L.o_posa);
+    u64* kb = reinterpret_cast<u64*>(b + L.o_kb);
+    u64* vb = reinterpret_cast<u64*>(b + L.o_vb);
+    unsigned short* pb = reinterpret_cast<unsigned short*>(b + L.o_posb);
+    unsigned char* ca = codes ? b + L.o_ca : nullptr;
+    unsigned char* cb = codes ? b + L.o_cb : nullptr;
+    // LSD order: the lower byte of the top 16 hash bits first, then the top byte
+    cudaError_t e = sort_pass(a.keys, a.vals, a.n, 48, ha, L.hist_n, reinterpret_cast<u32*>(b + L.o_pa), L.ntiles,
+                              ka, va, pa, s);
+    if (e == cudaSuccess)
+        e = sort_pass(ka, va, a.n, 56, hb, L.hist_n, reinterpret_cast<u32*>(b + L.o_pb), L.ntiles, kb, vb, pb, s);
+    if (e != cudaSuccess) return e;
+    OpArgs o = a;
+    o.keys = kb;
+    o.vals = vb;
+    o.codes = cb;
+    if ((e = run(o, ctx, s)) != cudaSuccess) return e;
+    if (codes) {
+        const unsigned grid = unsigned(L.ntiles);
+        part_gather_kernel<false, true><<<grid, kPThreads, 0, s>>>(pb, nullptr, cb, hb, L.ntiles, a.n, nullptr, ca);
+        part_gather_kernel<false, true><<<grid, kPThreads, 0, s>>>(pa, nullptr, ca, ha, L.ntiles, a.n, nullptr,
+                                                                   a.codes);
+        count_launch();
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 u64 compact_scratch_bytes(u32 log2c) {
     const u64 nchunks = ((1ull << log2c) + kCompactChunk - 1) / kCompactChunk;
     return align256((nchunks + 1) * 4) + align256(scan_partials(nchunks + 1) * 4);

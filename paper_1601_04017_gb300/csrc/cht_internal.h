@@ -50,6 +50,10 @@ cudaError_t launch_op(Mode mode, const OpArgs& a, int group_width, int lane_cell
 // aggregation of equal keys in shared memory before the table is touched.
 // warp_dedup: first combine equal keys of each warp step (extreme skew).
 cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, bool warp_dedup, int ctas_per_sm, cudaStream_t s);
+// The same with 1024-thread CTAs and windows of 4096 operations (8192
+// shared-memory slots): for batches sorted by hash, where a window holds the
+// whole groups of a key's operations.  insertOrUpdate modes only.
+cudaError_t launch_iou_aggregated_wide(Mode mode, const OpArgs& a, bool warp_dedup, cudaStream_t s);
 
 // Cluster-wise migration of `src` (2^src_log2 cells) into `dst`
 // (2^dst_log2 cells, dst_log2 >= src_log2).  dst needs no initialisation:
@@ -114,6 +118,17 @@ u64 partition_scratch_bytes(u64 n, PartitionIO io);
 typedef cudaError_t (*PartitionRun)(const OpArgs& a, void* ctx, cudaStream_t s);
 cudaError_t launch_partitioned(const OpArgs& a, PartitionIO io, void* scratch, PartitionRun run, void* ctx,
                                cudaStream_t s);
+
+// A batch sorted by the top 16 bits of its keys' hash (two stable 8-bit
+// passes, cht_bulk.cu) before `run` executes the operation on the sorted keys
+// and values; the result codes are put back into the caller's order (two
+// gathers).  All operations of one key then lie in one contiguous run of the
+// sorted batch (the run of their 1/65536 of the hash range), so a window of
+// 4096 consecutive operations holds whole runs of ~4096 / (n / 65536) keys'
+// operations.  Scratch:
+// sorted16_scratch_bytes(n, codes != nullptr), about 38 bytes per operation.
+u64 sorted16_scratch_bytes(u64 n, bool codes);
+cudaError_t launch_sorted16(const OpArgs& a, void* scratch, PartitionRun run, void* ctx, cudaStream_t s);
 
 // The live cells (neither empty nor tombstone) in cell index order into
 // keys_out / vals_out (deterministic; the bulk merge's table side).  Scratch:

@@ -106,30 +106,31 @@ cudaError_t launch_mode(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStre
     }
 }
 
-template <int MODE, int WD, bool RE>
+template <int MODE, int WD, bool RE, int BLOCK = kAggBlock>
 cudaError_t launch_agg(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
-    constexpr size_t smem = agg_smem_bytes<MODE>();
+    constexpr size_t smem = agg_smem_bytes<MODE, BLOCK>();
     static std::atomic<int> occ{0};
     int per_sm = occ.load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(iou_agg_kernel<MODE, WD, RE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
+        cudaError_t e = cudaFuncSetAttribute(iou_agg_kernel<MODE, WD, RE, BLOCK>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         // as much of the unified L1 / shared memory as shared memory as the
-        // kernel can use (38 KB per CTA)
-        e = cudaFuncSetAttribute(iou_agg_kernel<MODE, WD, RE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        // kernel can use (38 KB per 256-thread CTA, 152 KB per 1024-thread CTA)
+        e = cudaFuncSetAttribute(iou_agg_kernel<MODE, WD, RE, BLOCK>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 100);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iou_agg_kernel<MODE, WD, RE>, kAggBlock, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iou_agg_kernel<MODE, WD, RE, BLOCK>, BLOCK, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         occ.store(per_sm, std::memory_order_relaxed);
     }
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     u64 grid = u64(sm_count()) * u64(per_sm);
-    const u64 nwin = (a.n + kAggWindow - 1) / kAggWindow;
+    const u64 nwin = (a.n + 4 * BLOCK - 1) / (4 * BLOCK);
     if (grid > nwin) grid = nwin;
     if (grid < 1) grid = 1;
-    const cudaError_t e = launch_pdl(iou_agg_kernel<MODE, WD, RE>, unsigned(grid), kAggBlock, smem, s, a);
+    const cudaError_t e = launch_pdl(iou_agg_kernel<MODE, WD, RE, BLOCK>, unsigned(grid), BLOCK, smem, s, a);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -157,6 +158,24 @@ cudaError_t launch_iou_aggregated(Mode mode, const OpArgs& a, bool warp_dedup, i
     // warp pre-reduction nor tombstone reuse applies
     if (mode == kUpdAdd) return launch_agg<kUpdAdd, 0, false>(a, ctas_per_sm, s);
     if (mode == kUpdOverwrite) return launch_agg<kUpdOverwrite, 0, false>(a, ctas_per_sm, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_iou_aggregated_wide(Mode mode, const OpArgs& a, bool warp_dedup, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    const bool re = a.reuse != 0;
+    if (mode == kIouAdd) {
+        if (re)
+            return warp_dedup ? launch_agg<kIouAdd, 2, true, 1024>(a, 0, s) : launch_agg<kIouAdd, 1, true, 1024>(a, 0, s);
+        return warp_dedup ? launch_agg<kIouAdd, 2, false, 1024>(a, 0, s) : launch_agg<kIouAdd, 1, false, 1024>(a, 0, s);
+    }
+    if (mode == kIouOverwrite) {
+        if (re)
+            return warp_dedup ? launch_agg<kIouOverwrite, 2, true, 1024>(a, 0, s)
+                              : launch_agg<kIouOverwrite, 1, true, 1024>(a, 0, s);
+        return warp_dedup ? launch_agg<kIouOverwrite, 2, false, 1024>(a, 0, s)
+                          : launch_agg<kIouOverwrite, 1, false, 1024>(a, 0, s);
+    }
     return cudaErrorInvalidValue;
 }
 

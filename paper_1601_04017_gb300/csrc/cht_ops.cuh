@@ -674,10 +674,13 @@ __device__ __forceinline__ unsigned char global_modify(const OpArgs& a, u64 key,
 // Shared memory of the aggregation kernel: slot keys, values and first ops;
 // for update modes also each operation's slot and each slot's result (every
 // operation on a key reports whether the key was present).
-template <int MODE>
+// BLOCK threads per CTA, windows of 4 * BLOCK operations, 8 * BLOCK slots:
+// 256 (the default) or 1024 (hash-sorted batches, whose key groups span whole
+// buckets of the sort).
+template <int MODE, int BLOCK = kAggBlock>
 constexpr size_t agg_smem_bytes() {
-    return size_t(kAggSlots) * (8 + 8 + 2) + size_t(kAggWindow) * 2 +
-           ((MODE == kUpdAdd || MODE == kUpdOverwrite) ? size_t(kAggWindow) * 2 + kAggSlots : 0);
+    return size_t(8 * BLOCK) * (8 + 8 + 2) + size_t(4 * BLOCK) * 2 +
+           ((MODE == kUpdAdd || MODE == kUpdOverwrite) ? size_t(4 * BLOCK) * 2 + 8 * BLOCK : 0);
 }
 
 // The flush of one window's distinct keys, kAggWindow / kAggBlock at most per
@@ -775,35 +778,36 @@ __device__ __forceinline__ void flush_keys(const OpArgs& a, const u64* fk, const
     }
 }
 
-template <int MODE, int DEDUP, bool kReuse>
-__global__ void __launch_bounds__(kAggBlock, 4) iou_agg_kernel(OpArgs a) {
+template <int MODE, int DEDUP, bool kReuse, int BLOCK = kAggBlock>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) iou_agg_kernel(OpArgs a) {
+    constexpr int kB = BLOCK, kW = 4 * BLOCK, kS = 8 * BLOCK;
     pdl_enter();
     constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
     constexpr bool kAdd = MODE == kIouAdd || MODE == kUpdAdd;
     extern __shared__ __align__(16) unsigned char agg_smem[];
     u64* const skey = reinterpret_cast<u64*>(agg_smem);
-    u64* const sval = skey + kAggSlots;
-    // window offset of the slot's first op (< kAggWindow: 16 bits)
-    unsigned short* const slead = reinterpret_cast<unsigned short*>(sval + kAggSlots);
-    unsigned short* const slist = slead + kAggSlots;  // the window's claimed slots
-    unsigned short* const sslot = slist + kAggWindow;                                   // update: op -> slot
-    unsigned char* const sres = reinterpret_cast<unsigned char*>(sslot + kAggWindow);   // update: slot result
+    u64* const sval = skey + kS;
+    // window offset of the slot's first op (< kW: 16 bits)
+    unsigned short* const slead = reinterpret_cast<unsigned short*>(sval + kS);
+    unsigned short* const slist = slead + kS;  // the window's claimed slots
+    unsigned short* const sslot = slist + kW;                                   // update: op -> slot
+    unsigned char* const sres = reinterpret_cast<unsigned char*>(sslot + kW);   // update: slot result
     const u64 cap = 1ull << a.log2c;
     const u32 shift = 64u - a.log2c;
     const int tid = threadIdx.x;
     u64 n_ins = 0, n_reused = 0;
     u32 sbits = 0;
     __shared__ u32 s_distinct[2];  // distinct keys (claimed slots) of this CTA's window, by window parity
-    __shared__ unsigned long long s_wsum[kAggBlock];  // warp pre-reduction: per lane, its group's sum
+    __shared__ unsigned long long s_wsum[kB];  // warp pre-reduction: per lane, its group's sum
     s_wsum[tid] = 0;
-    for (int s = tid; s < kAggSlots; s += kAggBlock) {
+    for (int s = tid; s < kS; s += kB) {
         skey[s] = kEmpty;
         sval[s] = 0;
     }
     if (tid < 2) s_distinct[tid] = 0;
     __syncthreads();
     bool dedup = DEDUP == 2;
-    const u64 nwin = (a.n + kAggWindow - 1) / kAggWindow;
+    const u64 nwin = (a.n + kW - 1) / kW;
     // windows: blockIdx.x, + gridDim.x, ... or, with a ticket counter, the
     // next window in batch order (every window already ends in a barrier,
     // which publishes the next ticket to the block)
@@ -815,25 +819,25 @@ __global__ void __launch_bounds__(kAggBlock, 4) iou_agg_kernel(OpArgs a) {
         w = s_next[0];
     }
     for (u32 round = 0; w < nwin; ++round) {
-        const u64 w0 = w * kAggWindow;
+        const u64 w0 = w * kW;
         const int par = int(round & 1);
         if (a.ticket && tid == 0) s_next[(round + 1) & 1] = atomicAdd(a.ticket, 1ull);
         // this thread's operations of the window, all loads issued before any
         // is used (the loads are volatile asm, which the compiler keeps in
         // program order: interleaved with the folding below they would cost one
         // memory round trip each)
-        constexpr int kPer = kAggWindow / kAggBlock;
+        constexpr int kPer = kW / kB;
         u64 wk[kPer], wv[kPer];
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            const u64 idx = w0 + u32(j * kAggBlock + tid);
+            const u64 idx = w0 + u32(j * kB + tid);
             wk[j] = idx < a.n ? ld_stream(a.keys + idx) : 0;
             wv[j] = idx < a.n ? ld_stream(a.vals + idx) : 0;
         }
         // fold the window's operations into the slots
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            const u32 off = u32(j * kAggBlock + tid);
+            const u32 off = u32(j * kB + tid);
             const u64 idx = w0 + off;
             bool valid = idx < a.n;
             u64 key = 0, d = 0;
@@ -879,7 +883,7 @@ __global__ void __launch_bounds__(kAggBlock, 4) iou_agg_kernel(OpArgs a) {
                 }
             }
             if (!valid) continue;
-            u32 s = u32(fmix64(key)) & (kAggSlots - 1);
+            u32 s = u32(fmix64(key)) & (kS - 1);
             for (;;) {
                 const u64 k0 = *reinterpret_cast<volatile u64*>(skey + s);
                 bool mine = false, same = k0 == key;
@@ -902,22 +906,22 @@ __global__ void __launch_bounds__(kAggBlock, 4) iou_agg_kernel(OpArgs a) {
                     else if (a.codes) a.codes[idx] = kNo;
                     break;
                 }
-                s = (s + 1) & (kAggSlots - 1);
+                s = (s + 1) & (kS - 1);
             }
         }
         __syncthreads();
         if (DEDUP == 1) {
             // the next window of this CTA combines within warps if this one had
             // few distinct keys
-            const u64 ops = a.n - w0 < u64(kAggWindow) ? a.n - w0 : u64(kAggWindow);
+            const u64 ops = a.n - w0 < u64(kW) ? a.n - w0 : u64(kW);
             dedup = u64(s_distinct[par]) * 2 < ops;
         }
         if (tid == 0) s_distinct[par ^ 1] = 0;  // the next window's counter (read by all before it)
         // flush: one global operation per distinct key of the window (the
-        // dense list of claimed slots; at most kAggWindow / kAggBlock per thread)
+        // dense list of claimed slots; at most kW / kB per thread)
         const u32 nd = s_distinct[par];
         if (kReuse) {  // tombstone reuse tracks the first tombstone of each path: one key at a time
-            for (u32 j = tid; j < nd; j += kAggBlock) {
+            for (u32 j = tid; j < nd; j += kB) {
                 const u32 sl = slist[j];
                 const unsigned char r =
                     global_modify<MODE, kReuse>(a, skey[sl], sval[sl], cap, shift, n_ins, n_reused, sbits);
@@ -927,14 +931,14 @@ __global__ void __launch_bounds__(kAggBlock, 4) iou_agg_kernel(OpArgs a) {
                 sval[sl] = 0;
             }
         } else {
-            constexpr int R = kAggWindow / kAggBlock;
+            constexpr int R = kW / kB;
             u64 fk[R], fd[R];
             bool fv[R];
             u32 fs[R];
             unsigned char res[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const u32 j = u32(tid + r * kAggBlock);
+                const u32 j = u32(tid + r * kB);
                 fv[r] = j < nd;
                 fs[r] = fv[r] ? slist[j] : 0u;
                 fk[r] = fv[r] ? skey[fs[r]] : 0;
@@ -953,7 +957,7 @@ __global__ void __launch_bounds__(kAggBlock, 4) iou_agg_kernel(OpArgs a) {
         }
         __syncthreads();
         if (kUpdate && a.codes) {  // every operation takes its key's result
-            for (int off = tid; off < kAggWindow; off += kAggBlock) {
+            for (int off = tid; off < kW; off += kB) {
                 const unsigned short sl = sslot[off];
                 if (sl != 0xffffu) a.codes[w0 + off] = sres[sl];
             }

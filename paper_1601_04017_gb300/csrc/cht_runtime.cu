@@ -186,7 +186,7 @@ bool valid_config(const cht_config& c) {
     const int t = c.migrate_tile;
     if (t != 0 && (t < 64 || t > 8192 || (t & (t - 1)) != 0)) return false;
     if (!(c.alpha > 0.0 && c.alpha < 1.0)) return false;
-    if (c.iou_aggregate < 0 || c.iou_aggregate > 2) return false;
+    if (c.iou_aggregate < 0 || c.iou_aggregate > 3) return false;
     if (c.reuse_tombstones < 0 || c.reuse_tombstones > 1) return false;
     if (c.full_key_space < 0 || c.full_key_space > 1) return false;
     if (c.partition < 0 || c.partition > 1) return false;
@@ -383,6 +383,13 @@ bool use_partition(const cht_table* h, u64 n) {
     return h->cfg.partition == 1 && n < (1ull << 32) && h->log2c >= 8;
 }
 
+// insertOrUpdate on a hash-sorted batch (iou_aggregate = 3): the batch is
+// sorted by the top 16 hash bits first, so one aggregation window holds all
+// operations of the keys it sees.
+bool use_sorted_agg(const cht_table* h, cht::Mode mode, u64 n) {
+    return (mode == cht::kIouAdd || mode == cht::kIouOverwrite) && h->cfg.iou_aggregate == 3 && n < (1ull << 32);
+}
+
 struct KernelCtx {
     const cht_table* h;
     cht::Mode mode;
@@ -395,6 +402,13 @@ cudaError_t run_kernel(const cht::OpArgs& a, void* ctx, cudaStream_t s) {
         return cht::launch_iou_aggregated(k->mode, a, k->h->cfg.iou_aggregate == 2, k->h->cfg.ctas_per_sm, s);
     const Width w = pick_width(k->h, k->mode, k->n);
     return cht::launch_op(k->mode, a, w.g, w.v, k->h->cfg.ctas_per_sm ? k->h->cfg.ctas_per_sm : w.ctas, s);
+}
+
+// insertOrUpdate on a batch sorted by hash: 1024-thread CTAs, 4096-operation
+// windows
+cudaError_t run_sorted_agg(const cht::OpArgs& a, void* ctx, cudaStream_t s) {
+    const KernelCtx* k = static_cast<const KernelCtx*>(ctx);
+    return cht::launch_iou_aggregated_wide(k->mode, a, false, s);
 }
 
 cudaError_t run_kernel_ordered(const cht::OpArgs& a, void* ctx, cudaStream_t s) {
@@ -418,6 +432,15 @@ cht_status launch(cht_table* h, cht::Mode mode, const u64* keys, const u64* vals
     a.st = h->st;
     KernelCtx ctx{h, mode, n};
     if (n == 0) return CHT_OK;
+    if (!use_partition(h, n) && use_sorted_agg(h, mode, n)) {
+        const u64 bytes = cht::sorted16_scratch_bytes(n, codes != nullptr);
+        void* scratch = nullptr;
+        cht_status r = lib_alloc(&scratch, bytes, s);
+        if (r != CHT_OK) return r;
+        const cudaError_t e = cht::launch_sorted16(a, scratch, run_sorted_agg, &ctx, s);
+        lib_free(scratch, bytes, s);
+        return cuda_status(e);
+    }
     if (!use_partition(h, n)) return cuda_status(run_kernel(a, &ctx, s));
     cht::PartitionIO io;
     io.vals = cht::mode_has_vals(mode);

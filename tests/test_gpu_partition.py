@@ -172,3 +172,37 @@ def test_partitioned_2p22_table_load_09(cuda_lib, oracle_mod):
             assert np.array_equal(to_np_u8(fo), ef)
             assert np.array_equal(to_np_u64(vo), ev)
     assert_same_live_set(t, o)
+
+
+@pytest.mark.parametrize("s", [0.5, 1.0, 1.5])
+@pytest.mark.parametrize("n", [1, 4097, 300_001])
+def test_hash_sorted_insert_or_update(cuda_lib, oracle_mod, s, n):
+    """iou_aggregate = 3: the batch is sorted by the top 16 hash bits (two stable
+    passes), aggregated in 4096-operation windows, codes gathered back."""
+    c = 1 << 18
+    keys = W.zipf_keys(n, s, n_ranks=1 << 16, seed=65)
+    vals = (np.arange(n, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)) | np.uint64(1)
+    keys[::997] = 0
+    pre = np.unique(keys[keys != 0])[::5]
+    t = cuda_lib.Table(c)
+    t.set_config(iou_aggregate=3)
+    o = oracle_mod.OracleTable(c)
+    t.insert(to_dev(pre), to_dev(pre))
+    o.insert(pre, pre)
+    codes = codes_buf(n)
+    t.insert_or_update(to_dev(keys), to_dev(vals), cuda_lib.ADD, codes)
+    o.insert_or_update(keys, vals, oracle_mod.ADD)
+    cs = to_np_u8(codes)
+    assert (cs[keys == 0] == 3).all()
+    pre_set = set(pre.tolist())
+    live_ops = keys != 0
+    assert_one_winner(keys[live_ops], cs[live_ops], lambda k: k not in pre_set)
+    assert_same_live_set(t, o)
+    # overwrite through the same path: every stored value is one of its key's
+    t.insert_or_update(to_dev(keys), to_dev(vals), cuda_lib.OVERWRITE)
+    gk, gv = t.export()
+    got = dict(zip(to_np_u64(gk).tolist(), to_np_u64(gv).tolist()))
+    allowed = {}
+    for k, v in zip(keys.tolist(), vals.tolist()):
+        allowed.setdefault(k, set()).add(v)
+    assert all(got[k] in allowed[k] for k in allowed if k != 0)
