@@ -94,7 +94,13 @@ typedef enum {
  * operation per distinct key and window), and for insertOrUpdate also combines
  * equal keys within each warp step in a window that follows a window with
  * fewer distinct keys than a fifth of its operations; 2 always combines them
- * (insertOrUpdate); 0 probes every operation with the group kernel.  reuse_tombstones: 0 (default) = the paper's rule,
+ * (insertOrUpdate); 3 first sorts an insertOrUpdate batch by the top 16 bits
+ * of the hash (two stable 8-bit passes, Sec. 4.5 integer sorting) so that the
+ * windows -- 4096 operations per 1024-thread CTA -- hold every operation of
+ * the keys they see, and puts the result codes back into the caller's order
+ * (about 38 bytes of scratch per operation; measured slower than 1 on GB300 at
+ * every skew: the sort passes cost more than the aggregation saves); 0 probes
+ * every operation with the group kernel.  reuse_tombstones: 0 (default) = the paper's rule,
  * an erased cell is never used again until a migration drops it (Sec. 3
  * "Deletions"); 1 = an insert / insert-or-update that finds its key absent
  * puts it into the first tombstone on its probe path (safe under phase
