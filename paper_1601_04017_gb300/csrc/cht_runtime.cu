@@ -937,11 +937,11 @@ cht_status cht_get_config(cht_handle h, cht_config* cfg) {
 // second copy stream.  Pieces of one batch run one after another on the
 // caller's stream, which is one linearization of the batch (phase semantics
 // hold per piece and across them).  Device arrays are used in place.  The
-// slots (about 100 MB per slot) are allocated on a device's first pipelined
+// slots (about 420 MB per slot) are allocated on a device's first pipelined
 // call and kept until the process exits; calls on one device take the slots
 // one after another (a host lock around the enqueueing, events on the GPU).
 // ---------------------------------------------------------------------------
-constexpr u64 kPipeChunk = 1ull << 22;
+constexpr u64 kPipeChunk = 1ull << 24;
 constexpr int kPipeSlots = 3;
 
 struct PipeSlot {

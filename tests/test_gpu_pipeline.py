@@ -1,4 +1,4 @@
-"""Host arrays larger than one pipeline piece (2^22 operations): the library
+"""Host arrays larger than one pipeline piece (2^24 operations): the library
 copies piece i+1 in while piece i runs and piece i-1's results go back.  The
 results must equal the same call on device arrays: finds, erase and update
 codes bit-exact; inserts of distinct keys all 1; insertOrUpdate(add) sums and
@@ -13,7 +13,7 @@ from gpu_helpers import assert_same_live_set, to_dev, to_np_u64, to_np_u8
 
 pytestmark = pytest.mark.gpu
 
-PIECE = 1 << 22
+PIECE = 1 << 24
 
 
 def _pinned(a):
@@ -27,7 +27,7 @@ def _pinned(a):
 def test_pipelined_host_arrays_match_device_arrays(cuda_lib, oracle_mod, n, growable):
     import torch
 
-    c = 1 << 25
+    c = 1 << 27
     keys = W.uniform_keys(n, seed=71)
     vals = W.values_for(keys)
     th = cuda_lib.Table(1 << 12 if growable else c, growable=growable)  # host arrays
