@@ -1127,6 +1127,8 @@ def main():
     ap.add_argument("--case-s", type=float, default=1.0)
     ap.add_argument("--case-agg", type=int, default=1, choices=[0, 1, 2, 3],
                     help="insertOrUpdate aggregation of the case's tables (table option iou_aggregate)")
+    ap.add_argument("--case-group-width", type=int, default=0, choices=[-1, 0, 1, 2, 4, 8, 16, 32],
+                    help="--case: probe window group width (0 = the automatic rule, -1 = one thread per operation)")
     ap.add_argument("--probe-random-access", action="store_true",
                     help="measure the HBM random-read ceiling instead of the benchmark")
     ap.add_argument("--workload", default="bounded", choices=["bounded", "batched", "serving"],

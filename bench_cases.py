@@ -26,7 +26,8 @@ def run_case(args):
     cht.load_library()
     log2c, load = args.case_log2c, args.case_load
     c = 1 << log2c
-    tcfg = {"partition": {"off": 0, "on": 1}[args.partition], "iou_aggregate": args.case_agg}
+    tcfg = {"partition": {"off": 0, "on": 1}[args.partition], "iou_aggregate": args.case_agg,
+            "group_width": args.case_group_width}
     s = torch.cuda.current_stream()
 
     def tm(fn):
@@ -38,6 +39,7 @@ def run_case(args):
         return round(a.elapsed_time(b), 4)
 
     out = {"case": args.case, "log2c": log2c, "load": load, "partition": args.partition, "agg": args.case_agg,
+           "group_width": args.case_group_width,
            "s": args.case_s}
     if args.case == "shrink":
         # the same shrink once untimed, so the timed one does not include the
@@ -194,6 +196,33 @@ template <int W> __global__ void rr(const unsigned char* buf, u64 mask, u64 n, u
   }
   out[u64(blockIdx.x) * blockDim.x + threadIdx.x] = acc;
 }
+// Random modifications of 16-byte cells (the table's cell layout) at random
+// cell indices: K = 0 a fetch-and-add on the cell's second word whose result is
+// unused (a reduction); K = 1 a load of the cell, then that add (an update of a
+// present key: the add follows the load); K = 2 the 16-byte CAS of an empty
+// cell to a filled one (an insert's claim; the buffer starts zeroed).
+struct alignas(16) Cell16 { u64 k, v; };
+template <int K> __global__ void rm(Cell16* buf, u64 mask, u64 n, u64* out) {
+  u64 acc = 0; const u64 stride = u64(gridDim.x) * blockDim.x;
+  for (u64 i = u64(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    Cell16* p = buf + (mix(i + 1) & mask);
+    if (K == 0) atomicAdd(&p->v, 1ull);
+    if (K == 1) { u64 a, b; asm volatile("ld.global.cg.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+      atomicAdd(&p->v, (a & 1ull) | 1ull); acc ^= b; }
+    if (K == 2) { Cell16 e{0, 0}, d{i + 1, i}; Cell16 o = atomicCAS(p, e, d); acc ^= o.k; }
+  }
+  out[u64(blockIdx.x) * blockDim.x + threadIdx.x] = acc;
+}
+extern "C" float run_rm(void* buf, u64 bytes, u64 n, int kind, u64* out, int grid) {
+  cudaEvent_t a, b; cudaEventCreate(&a); cudaEventCreate(&b);
+  const u64 mask = bytes / 16 - 1; cudaEventRecord(a);
+  if (kind == 0) rm<0><<<grid, 256>>>((Cell16*)buf, mask, n, out);
+  if (kind == 1) rm<1><<<grid, 256>>>((Cell16*)buf, mask, n, out);
+  if (kind == 2) rm<2><<<grid, 256>>>((Cell16*)buf, mask, n, out);
+  cudaEventRecord(b); cudaEventSynchronize(b); float ms = 0; cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a); cudaEventDestroy(b);
+  return cudaGetLastError() == cudaSuccess ? ms : -1.0f;
+}
 extern "C" float run_rr(const void* buf, u64 bytes, u64 n, int width, u64* out, int grid) {
   cudaEvent_t a, b; cudaEventCreate(&a); cudaEventCreate(&b);
   const u64 mask = bytes / width - 1; cudaEventRecord(a);
@@ -213,7 +242,10 @@ extern "C" float run_rr(const void* buf, u64 bytes, u64 n, int width, u64* out, 
 def probe_random_access():
     """Random-read bandwidth of the HBM: n reads of W bytes at uniformly random
     W-aligned offsets of a 4 GiB buffer (and of a 16 MiB, L2-resident one).
-    This is the practical ceiling of a probe that touches one sector per step."""
+    This is the practical ceiling of a probe that touches one sector per step.
+    Then the rate of random modifications of 16-byte cells (an atomic add, a
+    load followed by the add, a 16-byte CAS claim): the ceiling of the
+    modifying operations, which dirty a random line each."""
     import ctypes
     import tempfile
 
@@ -245,4 +277,25 @@ def probe_random_access():
             res.append({"buffer_bytes": nbytes, "width_bytes": width, "ms": round(ms, 4),
                         "gbs": round(n * width / ms / 1e6, 1), "greads_per_s": round(n / ms / 1e6, 2)})
         del buf
-    print(json.dumps({"probe": "random_read", "results": res}), flush=True)
+    # random modifications of 16-byte cells: 2^27 per run, on a 4 GiB buffer
+    # (HBM) and a 16 MiB one (L2); the CAS runs on a zeroed buffer each time
+    lib.run_rm.restype = ctypes.c_float
+    lib.run_rm.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
+                           ctypes.c_int]
+    mod = []
+    names = {0: "fetch_add", 1: "load_then_add", 2: "cas16_claim"}
+    for log2b in (24, 32):
+        nbytes = 1 << log2b
+        buf = torch.zeros(nbytes // 8, dtype=torch.int64, device="cuda")
+        n = 1 << 27
+        for kind in (0, 1, 2):
+            times = []
+            for _ in range(2):  # warm, then timed
+                if kind == 2:
+                    buf.zero_()
+                times.append(lib.run_rm(buf.data_ptr(), nbytes, n, kind, out.data_ptr(), grid))
+            ms = times[-1]
+            mod.append({"buffer_bytes": nbytes, "kind": names[kind], "ms": round(ms, 4),
+                        "gops_per_s": round(n / ms / 1e6, 2)})
+        del buf
+    print(json.dumps({"probe": "random_read", "results": res, "random_modify": mod}), flush=True)

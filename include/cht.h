@@ -79,13 +79,19 @@ typedef enum {
 #define CHT_STATUS_RESERVED 0x2u
 
 /* Tunables.  group_width G: lanes that probe one key together, each loading
- * lane_cells cells per probe step (G in {1,2,4,8,16,32}); 0 (default) picks
- * the window per batch from the table's load (for insert: the load after the
- * batch): below 0.6, finds 2 lanes x 4 cells (one 128-byte line) and the
- * other operations 1 lane x 2 cells; above it, finds and inserts 4 lanes x 4
- * cells and the others 4 lanes x 2 cells.  lane_cells V: 1 (16 bytes), 2 (one
- * 32-byte sector) or 4 (two sectors, loaded together); 0 = default (2 for
- * G = 1, else 1); G = 32 allows only 1, G = 16 at most 2.  ctas_per_sm: resident CTAs per
+ * lane_cells cells per probe step (G in {1,2,4,8,16,32}; a warp refills a
+ * group with its next operation when the group's key is decided); -1: one
+ * thread per operation, the paper's own form (each thread runs its operations
+ * one at a time from a grid-stride sequence, V = 2 or 4 cells per step;
+ * tables with reuse_tombstones or full_key_space run it as G = 1).  0
+ * (default) picks the window per batch from the table's size and load (for
+ * insert: the load after the batch) by the measured rule the library was
+ * built with (the single-call autotuner's output; where it has no entry:
+ * below load 0.6, finds 2 lanes x 4 cells and the others 1 lane x 2 cells;
+ * above it, finds and inserts 4 lanes x 4 cells and the others 4 lanes x 2
+ * cells).  lane_cells V: 1 (16 bytes), 2 (one 32-byte sector) or 4 (two
+ * sectors, loaded together); 0 = default (2 for G = 1, 4 for G = -1, else 1);
+ * G = 32 allows only 1, G = 16 at most 2, G = -1 not 1.  ctas_per_sm: resident CTAs per
  * SM for the operation kernels (0 = occupancy maximum).  migrate_tile:
  * source cells per migration warp task (power of two, 64..8192; 0 = by load:
  * 512 below load 0.6, else 1024).  alpha: growth threshold in (0, 1) (Sec. 4.3.2; default 0.5).
@@ -527,7 +533,8 @@ cht_status cht_find_noalloc(cht_handle h, const uint64_t *keys, uint64_t n, uint
 /* Single-call autotuner.  Times one batch of operation `op` (CHT_OP_FIND,
  * _INSERT, _ERASE, _UPDATE_ADD / _OVERWRITE, _IOU_ADD / _OVERWRITE through the
  * probe kernel) on this table with every probe window -- group width G in
- * {1, 2, 4, 8, 16, 32}, cells per lane V in {1, 2, 4} where the kernels exist,
+ * {-1 (one thread per operation), 1, 2, 4, 8, 16, 32}, cells per lane V in
+ * {1, 2, 4} where the kernels exist,
  * resident CTAs per SM in {occupancy maximum, 4} -- `trials` times each (at
  * least 3), restoring the table's cells and counters before every trial of a
  * modifying operation and once more at the end, so the table is unchanged.

@@ -44,6 +44,33 @@ cudaError_t launch_one(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// Per-thread operations (group_width = -1), V = 2 or 4 cells per step.
+template <int V, int MODE>
+cudaError_t launch_thread_v(const OpArgs& a, int ctas_per_sm, cudaStream_t s) {
+    static std::atomic<int> occ{0};
+    int per_sm = occ.load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thread_kernel<V, MODE>, kThreadBlock, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        occ.store(per_sm, std::memory_order_relaxed);
+    }
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    u64 grid = u64(sm_count()) * u64(per_sm);
+    const u64 need = (a.n + kThreadBlock - 1) / kThreadBlock;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    const cudaError_t e = launch_pdl(thread_kernel<V, MODE>, unsigned(grid), kThreadBlock, 0, s, a);
+    count_launch();
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_thread(const OpArgs& a, int v, int ctas_per_sm, cudaStream_t s) {
+    return v == 2 ? launch_thread_v<2, MODE>(a, ctas_per_sm, s) : launch_thread_v<4, MODE>(a, ctas_per_sm, s);
+}
+
 // Tables with tombstone reuse or the full key space: kernels exist for the
 // automatic windows only -- 1 lane x 1 sector, 2 lanes x 2 sectors, 4 lanes x
 // 1 or 2 sectors; any other configured window takes the nearest of these.
@@ -75,6 +102,13 @@ cudaError_t launch_flagged(const OpArgs& a, int g, int v, int flags, int ctas_pe
 template <int MODE>
 cudaError_t launch_mode(const OpArgs& a, int g, int v, int ctas_per_sm, cudaStream_t s) {
     const int flags = ((mode_fills(MODE) && a.reuse) ? kFlagReuse : 0) | (a.full_keys ? kFlagFullKeys : 0);
+    if (g < 0) {
+        // the per-thread kernels: plain tables, the whole batch in one
+        // grid-stride pass (in-order pieces take the 1-lane group loop)
+        if (!flags && a.chunk == 0) return launch_thread<MODE>(a, v, ctas_per_sm, s);
+        g = 1;
+        if (v != 4) v = 2;
+    }
     if (flags) return launch_flagged<MODE>(a, g, v, flags, ctas_per_sm, s);
     if (v == 4) {
         switch (g) {

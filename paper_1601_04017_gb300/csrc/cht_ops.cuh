@@ -202,6 +202,13 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
     // (not in the engine, kCoherent: over its many small, mostly L2-resident
     // tables the CAS-first step made the 4096-table workload 45 % slower)
     constexpr bool kCasFirst = MODE == kInsert && G == 1 && kFlags == 0 && !kCoherent;
+    // Finds whose window spans more than one 128-byte line skip the sectors
+    // that lie wholly before `first` (cells before it are never examined): on
+    // the first step this saves the line in front of the home cell's.
+    // (Inserts keep whole windows: with the extra predicates the 5-CTA bound
+    // spilled more registers and the load-0.9 inserts took 10.2 -> 14.4 ms;
+    // one-line windows gain nothing, the line is fetched whole anyway.)
+    constexpr bool kSkipBeforeFirst = MODE == kFind && W * sizeof(Cell) > 128;
 
     const u64 cap = 1ull << a.log2c;
     const u64 cmask = cap - 1;
@@ -373,17 +380,21 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
         u64 hv = 0;
         if (active) {
             const Cell* p = a.cells + base + u32(gl) * V;
+            const u32 o0 = u32(gl) * V;
             if (V == 1) {
-                if (kModify || kCoherent) ld_cell_cg(p, kk[0], vv[0]);
-                else ld_cell_nc(p, kk[0], vv[0]);
+                if (!kSkipBeforeFirst || o0 >= first) {
+                    if (kModify || kCoherent) ld_cell_cg(p, kk[0], vv[0]);
+                    else ld_cell_nc(p, kk[0], vv[0]);
+                }
             } else {
 #pragma unroll
                 for (int j = 0; j < V; j += 2) {
-                    if (kModify || kCoherent) ld_pair_cg(p + j, kk[j], vv[j], kk[j + 1], vv[j + 1]);
-                    else ld_pair_nc(p + j, kk[j], vv[j], kk[j + 1], vv[j + 1]);
+                    if (!kSkipBeforeFirst || o0 + j + 1 >= first) {
+                        if (kModify || kCoherent) ld_pair_cg(p + j, kk[j], vv[j], kk[j + 1], vv[j + 1]);
+                        else ld_pair_nc(p + j, kk[j], vv[j], kk[j + 1], vv[j + 1]);
+                    }
                 }
             }
-            const u32 o0 = u32(gl) * V;
 #pragma unroll
             for (int j = V - 1; j >= 0; --j) {  // the lowest qualifying cell wins
                 if (o0 + j >= first && (kk[j] == key || kk[j] == kEmpty)) {
@@ -564,6 +575,138 @@ __global__ void __launch_bounds__(kOpBlock, op_min_blocks<G, V>()) op_kernel(OpA
             const u64 end = begin + a.chunk < a.n ? begin + a.chunk : a.n;
             warp_ops<G, V, MODE, false, false, kFlags>(a, begin, end, n_ins, n_del, sbits);
         }
+    }
+    warp_flush_counters(a.st, n_ins, n_del, sbits);
+}
+
+// ---------------------------------------------------------------------------
+// Per-thread operations (group_width = -1): the paper's own form, one thread
+// per operation (Algorithm 1 and the find / erase / update probes of Sec. 3):
+// each thread runs one operation at a time over a grid-stride sequence of the
+// batch and probes V cells (one or two 32-byte sectors, aligned) per step;
+// inserts claim the home cell with the 16-byte CAS first.  No group shuffles
+// and no refill bookkeeping, so few instructions and registers per operation
+// and more resident warps per SM -- for short probes (low load), where the
+// lanes of a warp finish in about the same number of steps.  Tables without
+// table options only (reuse_tombstones and full_key_space take the group
+// loop); the next operation's key and value are loaded before the current
+// one probes, and results are stored after the warp reconverges (coalesced).
+// ---------------------------------------------------------------------------
+constexpr int kThreadBlock = 256;
+
+// One operation; returns its code and (find) the value found.
+template <int V, int MODE>
+__device__ __forceinline__ unsigned char thread_op(const OpArgs& a, u64 key, u64 d, u64 cap, u32 shift,
+                                                   u64& n_ins, u64& n_del, u32& sbits, u64& vout) {
+    constexpr bool kInsLike = mode_fills(MODE);
+    constexpr bool kUpdate = MODE == kUpdAdd || MODE == kUpdOverwrite;
+    const u64 cmask = cap - 1;
+    vout = 0;
+    if (is_reserved(key)) {
+        sbits |= kReserved;
+        return kCodeReserved;
+    }
+    u64 pos = home_of(key, shift);
+    u64 probed = 0;
+    if (MODE == kInsert) {
+        Cell expect;
+        expect.key = kEmpty;
+        expect.val = 0;
+        Cell desired;
+        desired.key = key;
+        desired.val = d;
+        const Cell old = cas_cell(a.cells + pos, expect, desired);
+        if (old.key == kEmpty && old.val == 0) {
+            ++n_ins;
+            return kYes;
+        }
+        if (old.key == key) return kNo;
+        probed = 1;
+        pos = (pos + 1) & cmask;
+    }
+    while (probed < cap) {
+        const u64 base = pos & ~u64(V - 1);
+        const u32 first = u32(pos - base);
+        u64 kk[V], vv[V];
+        const Cell* p = a.cells + base;
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            if (MODE == kFind) ld_pair_nc(p + j, kk[j], vv[j], kk[j + 1], vv[j + 1]);
+            else ld_pair_cg(p + j, kk[j], vv[j], kk[j + 1], vv[j + 1]);
+        }
+        int hit = -1;
+        bool match = false;
+        u64 hv = 0;
+#pragma unroll
+        for (int j = V - 1; j >= 0; --j) {  // the lowest qualifying cell wins
+            if (u32(j) >= first && (kk[j] == key || kk[j] == kEmpty)) {
+                hit = j;
+                match = kk[j] == key;
+                hv = vv[j];
+            }
+        }
+        if (hit < 0) {
+            probed += V - first;
+            pos = (base + V) & cmask;
+            continue;
+        }
+        if (MODE == kFind) {
+            vout = match ? hv : 0;
+            return match ? kYes : kNo;
+        }
+        const int out = modify_at<MODE>(a.cells + base + u32(hit), match, key, d);
+        if (out != kStepContinue) {
+            if (out == kStepDoneYes) {
+                if (MODE == kErase) ++n_del;
+                else if (kInsLike) ++n_ins;
+            }
+            return (unsigned char)out;
+        }
+        probed += u32(hit) - first + 1;
+        pos = (base + u32(hit) + 1) & cmask;
+    }
+    // every cell was examined without a decision
+    if (MODE == kFind || MODE == kErase || kUpdate) return kNo;
+    sbits |= kFull;
+    return kCodeFull;
+}
+
+template <int V, int MODE>
+__global__ void __launch_bounds__(kThreadBlock) thread_kernel(OpArgs a) {
+    constexpr bool kHasVals = mode_has_vals(MODE);
+    pdl_enter();
+    const u64 cap = 1ull << a.log2c;
+    const u32 shift = 64u - a.log2c;
+    u64 n_ins = 0, n_del = 0;
+    u32 sbits = 0;
+    const u64 stride = u64(gridDim.x) * kThreadBlock;
+    u64 i = u64(blockIdx.x) * kThreadBlock + threadIdx.x;
+    u64 key = 0, d = 0;
+    if (i < a.n) {
+        key = ld_stream(a.keys + i);
+        if (kHasVals) d = ld_stream(a.vals + i);
+    }
+    // the lanes of a warp hold consecutive operations and step together (a
+    // warp-uniform loop), so they meet at the stores
+    for (;; i += stride) {
+        const bool live = i < a.n;
+        if (!__any_sync(0xffffffffu, live)) break;
+        const u64 j = i + stride;
+        u64 nk = 0, nd = 0;
+        if (j < a.n) {
+            nk = ld_stream(a.keys + j);
+            if (kHasVals) nd = ld_stream(a.vals + j);
+        }
+        u64 v = 0;
+        unsigned char c = 0;
+        if (live) c = thread_op<V, MODE>(a, key, d, cap, shift, n_ins, n_del, sbits, v);
+        __syncwarp();
+        if (live) {
+            if (MODE == kFind) a.vals_out[i] = v;
+            if (a.codes) a.codes[i] = c;
+        }
+        key = nk;
+        d = nd;
     }
     warp_flush_counters(a.st, n_ins, n_del, sbits);
 }

@@ -179,8 +179,9 @@ cht_config default_config() {
 
 bool valid_config(const cht_config& c) {
     const int g = c.group_width;
-    if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32)) return false;
+    if (!(g == -1 || g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32)) return false;
     if (!(c.lane_cells == 0 || c.lane_cells == 1 || c.lane_cells == 2 || c.lane_cells == 4)) return false;
+    if (g == -1 && c.lane_cells == 1) return false;
     if ((g == 32 && c.lane_cells >= 2) || (g == 16 && c.lane_cells == 4)) return false;
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 64) return false;
     const int t = c.migrate_tile;
@@ -362,7 +363,8 @@ Width pick_width(const cht_table* h, cht::Mode mode, u64 n) {
             if (w.v == 0) w.v = (mode == cht::kFind || mode == cht::kInsert) ? 4 : 2;
         }
     }
-    if (w.g == 1 && w.v != 4) w.v = 2;
+    if (w.g == -1) w.v = w.v == 2 ? 2 : 4;
+    else if (w.g == 1 && w.v != 4) w.v = 2;
     else if (w.v == 0 || w.g == 32) w.v = 1;
     return w;
 }
@@ -1469,8 +1471,8 @@ cht_status cht_tune(cht_handle h, int op, const uint64_t* keys, const uint64_t* 
     struct Cand {
         int g, v;
     };
-    static const Cand cands[] = {{1, 2},  {1, 4}, {2, 1}, {2, 2}, {2, 4},  {4, 1},  {4, 2},
-                                 {4, 4},  {8, 1}, {8, 2}, {8, 4}, {16, 1}, {16, 2}, {32, 1}};
+    static const Cand cands[] = {{-1, 2}, {-1, 4}, {1, 2},  {1, 4},  {2, 1},  {2, 2}, {2, 4}, {4, 1},
+                                 {4, 2},  {4, 4},  {8, 1},  {8, 2},  {8, 4},  {16, 1}, {16, 2}, {32, 1}};
     static const int ctas[] = {0, 4};
     cht::OpArgs a;
     a.cells = h->cells;

@@ -4,8 +4,9 @@ Runs the single-call autotuner (cht_tune: every probe window -- group width G,
 cells per lane V, resident CTAs per SM -- timed with at least three trials,
 median kept) on tables of 2^20, 2^24 and 2^28 cells at loads 0.25, 0.5, 0.7
 and 0.9, for find (a batch of hits and a batch of misses, ranked by the sum of
-the two), insert (the fresh keys that fill
-the table from the previous load level to this one), erase and update
+the two), insert (two batches that end at the load: the fresh keys that fill
+the table from the previous load level to this one, and the keys up to this
+load into an empty table; ranked by the sum of the two), erase and update
 (present keys), and writes
 
   csrc/cht_tuned.inc   the rule the runtime's automatic window choice reads:
@@ -95,13 +96,17 @@ def main():
         keys = W.uniform_keys(n_max + c // 2, backend="cuda")
         vals = W.values_for(keys, backend="cuda")
         t = cht.Table(c)
+        t_empty = cht.Table(c)  # stays empty: the tuner restores it after every trial
         filled = 0
         for ld in LOADS:
             n_ld = W.load_count(c, ld)
-            # the insert batch fills the table from the previous level to this
-            # one (its load after the batch is `ld`); tuned before it is applied
+            # the insert batches end at load `ld`: one fills the table from the
+            # previous level (tuned before it is applied), one fills an empty
+            # table; each window is ranked by the sum of its two times
             ins_k, ins_v = keys[filled:n_ld], vals[filled:n_ld]
-            res_ins = tune_one(lib, t, 1, ins_k, ins_v, args.trials)
+            ra = {r[:3]: r[3] for r in tune_one(lib, t, 1, ins_k, ins_v, args.trials)}
+            rb = {r[:3]: r[3] for r in tune_one(lib, t_empty, 1, keys[:n_ld], vals[:n_ld], args.trials)}
+            res_ins = sorted(((w[0], w[1], w[2], ra[w] + rb[w]) for w in ra), key=lambda r: r[3])
             t.insert(ins_k, ins_v)
             filled = n_ld
             nq = min(c // 2, 1 << 26)
@@ -127,11 +132,13 @@ def main():
                 g, vv, ct, ms = best if best[3] < (1.0 - MARGIN) * base[3] else base
                 lo, hi = SIZE_RANGES[log2c]
                 blo, bhi = BANDS[ld]
-                rows.append((MODE_NAMES[op], lo, hi, blo, bhi, g, vv, ct, ms, k.numel()))
+                nops = k.numel() if op != 1 else ins_k.numel() + n_ld  # (the ranked times cover both batches)
+                rows.append((MODE_NAMES[op], lo, hi, blo, bhi, g, vv, ct, ms, nops))
                 second = res[1] if len(res) > 1 else None
-                summary.append((log2c, ld, MODE_NAMES[op], k.numel(), res[0], second, base, (g, vv, ct)))
+                summary.append((log2c, ld, MODE_NAMES[op], nops, res[0], second, base, (g, vv, ct)))
                 torch.cuda.synchronize()
         t.destroy()
+        t_empty.destroy()
         del keys, vals
         torch.cuda.empty_cache()
     with open(args.out, "w") as f:

@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 
 GROUPS = [0, 1, 2, 4, 8, 16, 32]  # 0 = chosen by load
 # (group width, cells per lane): every probe window shape the kernels support
-WIDTHS = [(g, 0) for g in GROUPS] + [(2, 2), (4, 2), (8, 2), (16, 2), (1, 4), (2, 4), (4, 4), (8, 4)]
+WIDTHS = [(g, 0) for g in GROUPS] + [(2, 2), (4, 2), (8, 2), (16, 2), (1, 4), (2, 4), (4, 4), (8, 4),
+                                     (-1, 0), (-1, 2), (-1, 4)]  # -1: one thread per operation
 
 
 def _table(cht, cap, g=1, growable=False, v=0, **cfg):
@@ -53,7 +54,7 @@ def test_insert_find_uniform(cuda_lib, oracle_mod, g, v, load):
     assert_same_live_set(t, o)
 
 
-@pytest.mark.parametrize("g,v", [(1, 0), (8, 0), (8, 2)])
+@pytest.mark.parametrize("g,v", [(1, 0), (8, 0), (8, 2), (-1, 2), (-1, 4)])
 def test_insert_duplicates_one_winner(cuda_lib, oracle_mod, g, v):
     c = 1 << 14
     base = W.uniform_keys(3000, seed=51)
@@ -84,7 +85,7 @@ def test_insert_duplicates_one_winner(cuda_lib, oracle_mod, g, v):
     assert live == len(pre_set | set(keys.tolist()))
 
 
-IOU_PATHS = [(0, 1), (0, 2)] + [(g, 0) for g in GROUPS]  # (group width, shared-memory aggregation)
+IOU_PATHS = [(0, 1), (0, 2)] + [(g, 0) for g in GROUPS + [-1]]  # (group width, shared-memory aggregation)
 
 
 @pytest.mark.parametrize("g,agg", IOU_PATHS)
@@ -132,7 +133,7 @@ def test_insert_or_update_overwrite(cuda_lib, oracle_mod, g, agg):
         assert v in {r[0] for r in by[k]}
 
 
-@pytest.mark.parametrize("g,v", [(1, 0), (2, 0), (8, 0), (32, 0), (4, 2), (8, 2)])
+@pytest.mark.parametrize("g,v", [(1, 0), (2, 0), (8, 0), (32, 0), (4, 2), (8, 2), (-1, 2), (-1, 4)])
 def test_erase_and_tombstones(cuda_lib, oracle_mod, g, v):
     c = 1 << 15
     keys = W.uniform_keys(20_000, seed=54)
@@ -163,10 +164,11 @@ def test_erase_and_tombstones(cuda_lib, oracle_mod, g, v):
     assert t.size()[1] == o.nonempty
 
 
-def test_reserved_keys(cuda_lib):
+@pytest.mark.parametrize("g", [1, -1])
+def test_reserved_keys(cuda_lib, g):
     import torch
 
-    t = _table(cuda_lib, 1024)
+    t = _table(cuda_lib, 1024, g)
     keys = np.array([5, 0, (1 << 64) - 1, 9], dtype=np.uint64)
     codes = codes_buf(4)
     t.insert(to_dev(keys), to_dev(keys), codes)
@@ -184,7 +186,7 @@ def test_reserved_keys(cuda_lib):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("g,v", [(1, 0), (8, 0), (32, 0), (16, 2)])
+@pytest.mark.parametrize("g,v", [(1, 0), (8, 0), (32, 0), (16, 2), (-1, 2), (-1, 4)])
 def test_full_bounded_table(cuda_lib, g, v):
     t = _table(cuda_lib, 64, g, v=v)
     keys = W.uniform_keys(100, seed=55)
@@ -295,7 +297,8 @@ def _tombstones(t):
 
 
 @pytest.mark.parametrize("g,agg,mode", [(1, 0, "insert"), (4, 0, "insert"), (8, 0, "insert"), (1, 0, "iou_add"),
-                                        (4, 0, "iou_ow"), (0, 1, "iou_add"), (0, 2, "iou_ow"), (16, 0, "insert")])
+                                        (4, 0, "iou_ow"), (0, 1, "iou_add"), (0, 2, "iou_ow"), (16, 0, "insert"),
+                                        (-1, 0, "insert")])
 def test_reuse_tombstones_matches_oracle(cuda_lib, oracle_mod, g, agg, mode):
     """Tombstone reuse: erase, then insert / insertOrUpdate a mix of erased,
     live and fresh keys with duplicates, several rounds; results and contents
@@ -345,7 +348,8 @@ def test_reuse_tombstones_matches_oracle(cuda_lib, oracle_mod, g, agg, mode):
     assert t.size()[1] <= universe.size
 
 
-@pytest.mark.parametrize("g,v,agg", [(0, 0, 1), (0, 0, 0), (1, 0, 0), (4, 2, 0), (8, 2, 0), (2, 1, 0), (32, 1, 0)])
+@pytest.mark.parametrize("g,v,agg", [(0, 0, 1), (0, 0, 0), (1, 0, 0), (4, 2, 0), (8, 2, 0), (2, 1, 0), (32, 1, 0),
+                                     (-1, 2, 0), (-1, 4, 0)])
 @pytest.mark.parametrize("mode", ["add", "overwrite"])
 def test_update_matches_oracle(cuda_lib, oracle_mod, g, v, agg, mode):
     """update (Sec. 3): present keys change, absent and erased ones do not; the
@@ -382,7 +386,7 @@ def test_update_matches_oracle(cuda_lib, oracle_mod, g, v, agg, mode):
             assert gv in set(vs[ks == k].tolist())
 
 
-@pytest.mark.parametrize("g,v,agg", [(0, 0, 1), (1, 0, 0), (4, 4, 0), (8, 2, 0), (32, 1, 0), (0, 0, 2)])
+@pytest.mark.parametrize("g,v,agg", [(0, 0, 1), (1, 0, 0), (4, 4, 0), (8, 2, 0), (32, 1, 0), (0, 0, 2), (-1, 4, 0)])
 def test_full_key_space_matches_oracle(cuda_lib, oracle_mod, g, v, agg):
     """Keys 0 and ~0 mixed into every operation type (many copies per batch):
     codes, found values and the exported contents equal the oracle's special
@@ -435,3 +439,52 @@ def test_full_key_space_matches_oracle(cuda_lib, oracle_mod, g, v, agg):
     g_ = oracle_mod.OracleTable(64)
     g_.load_cells(cells)
     g_.assert_invariants()
+
+
+@pytest.mark.parametrize("mode", ["add", "overwrite"])
+@pytest.mark.parametrize("full_keys", [0, 1])
+def test_insert_or_update_low_skew_windows(cuda_lib, oracle_mod, mode, full_keys):
+    """Enough windows per CTA (2^23 operations) that low-skew stretches run
+    without the shared-memory fold and skewed ones with it, in both orders:
+    a segment of nearly distinct keys, a Zipf(1.5) segment, nearly distinct
+    keys again (with repeats of earlier ones), reserved keys throughout.  Add
+    sums bit-exact; overwrite stores a value that depends only on the key, so
+    it is exact whichever copy lands last; one insertion code per new key."""
+    n_seg = 1 << 21
+    rng = np.random.default_rng(61)
+    uni = W.uniform_keys(1 << 22, seed=62)
+    seg_a = uni[rng.integers(0, uni.size, n_seg)]
+    seg_b = W.zipf_keys(n_seg, 1.5, n_ranks=1 << 16, seed=63)
+    seg_c = uni[rng.integers(0, uni.size, 2 * n_seg)]
+    keys = np.concatenate([seg_a, seg_b, seg_c])
+    keys[rng.integers(0, keys.size, 4000)] = 0
+    keys[rng.integers(0, keys.size, 4000)] = np.uint64((1 << 64) - 1)
+    if mode == "add":
+        vals = (np.arange(keys.size, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)) | np.uint64(1)
+        op, oop = cuda_lib.ADD, oracle_mod.ADD
+    else:
+        vals = keys ^ np.uint64(0x5DEECE66D)
+        op, oop = cuda_lib.OVERWRITE, oracle_mod.OVERWRITE
+    pre = uni[::7]
+    c = 1 << 24
+    t = _table(cuda_lib, c, 0, iou_aggregate=1, full_key_space=full_keys)
+    o = oracle_mod.OracleTable(c, full_key_space=bool(full_keys))
+    t.insert(to_dev(pre), to_dev(pre))
+    o.insert(pre, pre)
+    codes = codes_buf(keys.size)
+    t.insert_or_update(to_dev(keys), to_dev(vals), op, codes)
+    oc = o.insert_or_update(keys, vals, oop)
+    cs = to_np_u8(codes)
+    reserved = (keys == 0) | (keys == np.uint64((1 << 64) - 1))
+    if not full_keys:
+        assert (cs[reserved] == 3).all()
+    # per key: the number of insertion codes (one for a new key, none for a
+    # present one) equals the oracle's
+    order = np.argsort(keys, kind="stable")
+    ks, gsum, osum = keys[order], cs[order].astype(np.int64), oc[order].astype(np.int64)
+    starts = np.flatnonzero(np.r_[True, ks[1:] != ks[:-1]])
+    assert np.array_equal(np.add.reduceat(gsum, starts), np.add.reduceat(osum, starts))
+    assert set(np.unique(cs[~reserved]).tolist()) <= {0, 1}
+    assert_same_live_set(t, o)
+    live, ne, _ = t.size()  # (the sticky status holds the reserved-key bit when full_keys is off)
+    assert live == o.live and ne == o.nonempty

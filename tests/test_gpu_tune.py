@@ -57,7 +57,7 @@ def test_tune_leaves_table_unchanged(cuda_lib, oracle_mod, op):
         k = wl["hits"][0.7]
     st, res = _tune(lib, t, op, to_dev(k), to_dev(W.values_for(k)))
     assert st == cuda_lib.CHT_OK
-    assert len(res) == 28  # 14 windows x 2 CTA counts
+    assert len(res) == 32  # 16 windows x 2 CTA counts
     assert [r[3] for r in res] == sorted(r[3] for r in res) and res[0][3] > 0
     assert np.array_equal(to_np_u64(t.cells()), before)
     assert t.size(check=True) == size0
