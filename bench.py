@@ -458,6 +458,31 @@ def kernel_rooflines(breakdown, counts, bpo, peak, peak_kind):
     return dom, rows[1:]
 
 
+# The ceiling of random modifications of 16-byte cells on this GPU (a random
+# line read and a dirty sector written back per operation), measured by
+# `python bench.py --probe-random-access --probe-out profiles/ceilings.json`:
+# the modifying calls whose operations nearly all reach the table, against it.
+MODIFY_CEILING = {"insert_0.5": "random_cas16_g_per_s", "erase": "random_fetch_add_g_per_s",
+                  "iou_add_s0.5": "random_fetch_add_g_per_s"}
+
+
+def random_modify_context(breakdown, counts):
+    try:
+        with open(os.path.join(ROOT, "profiles", "ceilings.json")) as f:
+            ceil = json.load(f)
+    except (OSError, ValueError):
+        return None
+    out = {"source": "profiles/ceilings.json (" + ceil.get("how", "") + ")"}
+    for name, key in MODIFY_CEILING.items():
+        row = breakdown.get(name)
+        c = ceil.get(key)
+        if not row or not c:
+            continue
+        g = counts[name] / (row["ms"] * 1e-3) / 1e9
+        out[name] = {"g_ops_per_s": round(g, 2), "ceiling_g_per_s": c, "ceiling": key, "frac": round(g / c, 3)}
+    return out
+
+
 def load_half_fractions(breakdown, peak):
     """The load-0.5 figures the project aims at (>= 0.5 of the random-access
     roofline for find and insert): the 2^28-cell step's calls and, when
@@ -547,6 +572,10 @@ def run_gpu(args):
                         "frac_of_" + peak_kind: round(gbs / peak, 4)})
         breakdown[name] = row
     roofline, roofline_others = kernel_rooflines(breakdown, counts, bpo, peak, peak_kind)
+    modify_ctx = random_modify_context(breakdown, counts)
+    if modify_ctx and "iou_add_s0.5" in modify_ctx and roofline["kernel"].startswith("iou_agg"):
+        # the dominant kernel's low-skew call against the random-modify ceiling
+        roofline["random_modify"] = dict(modify_ctx["iou_add_s0.5"], call="iou_add_s0.5")
     target = load_half_fractions(breakdown, peak)
 
     # end-to-end through the same API with pinned host arrays
@@ -601,6 +630,7 @@ def run_gpu(args):
                        "probe_window": "auto by load: finds 2 lanes x 64 B below 0.6, 4 x 64 B above; "
                                        "inserts 1 x 32 B below 0.6, 4 x 64 B above"},
             "roofline": roofline, "roofline_other_kernels": roofline_others, "target": target,
+            "random_modify_ceiling": modify_ctx,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "breakdown": breakdown, "latency_config1": lat,
         }
@@ -1130,7 +1160,9 @@ def main():
     ap.add_argument("--case-group-width", type=int, default=0, choices=[-1, 0, 1, 2, 4, 8, 16, 32],
                     help="--case: probe window group width (0 = the automatic rule, -1 = one thread per operation)")
     ap.add_argument("--probe-random-access", action="store_true",
-                    help="measure the HBM random-read ceiling instead of the benchmark")
+                    help="measure the HBM random-read and random-modify ceilings instead of the benchmark")
+    ap.add_argument("--probe-out", default="",
+                    help="--probe-random-access: also write the 4 GiB ceilings as JSON to this path")
     ap.add_argument("--workload", default="bounded", choices=["bounded", "batched", "serving"],
                     help="bounded: the 2^28-cell table step (the bench line); batched: many tables, "
                          "one engine launch vs one launch per batch")
@@ -1172,7 +1204,7 @@ def main():
     if args.probe_random_access:
         import bench_cases
 
-        bench_cases.probe_random_access()
+        bench_cases.probe_random_access(args.probe_out)
         return
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

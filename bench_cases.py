@@ -239,7 +239,7 @@ extern "C" float run_rr(const void* buf, u64 bytes, u64 n, int width, u64* out, 
 """
 
 
-def probe_random_access():
+def probe_random_access(out_path: str = ""):
     """Random-read bandwidth of the HBM: n reads of W bytes at uniformly random
     W-aligned offsets of a 4 GiB buffer (and of a 16 MiB, L2-resident one).
     This is the practical ceiling of a probe that touches one sector per step.
@@ -298,4 +298,15 @@ def probe_random_access():
             mod.append({"buffer_bytes": nbytes, "kind": names[kind], "ms": round(ms, 4),
                         "gops_per_s": round(n / ms / 1e6, 2)})
         del buf
-    print(json.dumps({"probe": "random_read", "results": res, "random_modify": mod}), flush=True)
+    line = {"probe": "random_read", "results": res, "random_modify": mod}
+    print(json.dumps(line), flush=True)
+    if out_path:
+        # the ceilings the benchmark quotes beside its byte roofline
+        hbm = {m["kind"]: m["gops_per_s"] for m in mod if m["buffer_bytes"] == 1 << 32}
+        rd = {r["width_bytes"]: r["greads_per_s"] for r in res if r["buffer_bytes"] == 1 << 32}
+        with open(out_path, "w") as f:
+            json.dump({"how": "python bench.py --probe-random-access --probe-out " + out_path +
+                       " (4 GiB buffer, uniformly random 16-byte cells / W-byte reads, CUDA events)",
+                       "random_read_32B_g_per_s": rd.get(32), "random_fetch_add_g_per_s": hbm.get("fetch_add"),
+                       "random_load_then_add_g_per_s": hbm.get("load_then_add"),
+                       "random_cas16_g_per_s": hbm.get("cas16_claim")}, f, indent=1)
