@@ -512,6 +512,23 @@ def pinned_copy_gbs(nbytes: int = 1 << 32) -> dict:
         b.record(s)
         b.synchronize()
         out[name] = round(nbytes / (a.elapsed_time(b) * 1e-3) / 1e9, 1)
+    # both directions at once (half of the buffers each way, two streams): the
+    # link's shared ceiling, which the pipelined calls' copies run against
+    half = nbytes // 2
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    s_in.wait_event(a)
+    s_out.wait_event(a)
+    with torch.cuda.stream(s_in):
+        d[:half].copy_(h[:half], non_blocking=True)
+    with torch.cuda.stream(s_out):
+        h[half:].copy_(d[half:], non_blocking=True)
+    s.wait_stream(s_in)
+    s.wait_stream(s_out)
+    b.record(s)
+    b.synchronize()
+    out["both_total"] = round(nbytes / (a.elapsed_time(b) * 1e-3) / 1e9, 1)
     del h, d
     return out
 
