@@ -1,0 +1,105 @@
+"""Host-side arithmetic of bench.py: the algorithmic byte model behind every
+roofline fraction, the choice of the dominant kernel, and the random-modify
+context.  No GPU: the functions are pure arithmetic on a breakdown.
+
+Pins: Knuth's expected probe lengths for linear probing (successful search
+(1 + 1/(1-a))/2, unsuccessful (1 + 1/(1-a)^2)/2) at the loads the bench uses,
+the insert fill average checked against a numerical integral of the
+unsuccessful-search length (not the closed form it uses), and the per-operation
+byte counts the design table quotes.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def test_knuth_probe_lengths():
+    assert bench.knuth_hit(0.5) == pytest.approx(1.5)
+    assert bench.knuth_miss(0.5) == pytest.approx(2.5)
+    assert bench.knuth_hit(0.9) == pytest.approx(5.5)
+    assert bench.knuth_miss(0.9) == pytest.approx(50.5)
+    assert bench.sectors(1.0) == 1.0 and bench.sectors(3.0) == 2.0
+
+
+@pytest.mark.parametrize("a0,a1", [(0.0, 0.5), (0.5, 0.9), (0.25, 0.5), (0.7, 0.9)])
+def test_insert_fill_average_is_the_integral(a0, a1):
+    # an insert into a table at load a is an unsuccessful search; averaged over
+    # a fill from a0 to a1 (midpoint rule, 10^6 intervals)
+    m = 1_000_000
+    a = a0 + (np.arange(m) + 0.5) * (a1 - a0) / m
+    mean = float(np.mean(0.5 * (1.0 + 1.0 / (1.0 - a) ** 2)))
+    if a0 == 0.0:
+        # from an empty table the bench counts the first probe of every insert
+        # as the successful-search length of the final table (the same number
+        # of occupied cells probed, Knuth's relation)
+        assert bench.insert_probe_cells(a0, a1) == pytest.approx(bench.knuth_hit(a1))
+        assert mean == pytest.approx(bench.knuth_hit(a1), rel=1e-6)
+    else:
+        assert bench.insert_probe_cells(a0, a1) == pytest.approx(mean, rel=1e-6)
+
+
+def test_algorithmic_bytes_table():
+    ab = bench.algorithmic_bytes
+    assert ab("find_hit", load=0.5) == pytest.approx(57.0)
+    assert ab("find_miss", load=0.5) == pytest.approx(73.0)
+    assert ab("find_hit", load=0.9) == pytest.approx(121.0)
+    assert ab("find_miss", load=0.9) == pytest.approx(841.0)
+    assert ab("insert", a0=0.0, a1=0.5) == pytest.approx(89.0)
+    assert ab("insert", a0=0.5, a1=0.9) == pytest.approx(233.0)
+    assert ab("erase", load=0.9) == pytest.approx(145.0)
+    assert ab("iou", distinct=1 << 26, ops=1 << 28) == pytest.approx(17.0 + 16.0)
+    assert ab("migrate", gamma=2) == 48
+    with pytest.raises(ValueError):
+        ab("nonsense")
+
+
+def _breakdown():
+    # ms per call of a made-up step; the four insertOrUpdate calls sum to the most
+    return {"insert_0.5": {"ms": 7.0}, "find_hit_0.5": {"ms": 4.5}, "find_miss_0.5": {"ms": 5.0},
+            "insert_0.9": {"ms": 10.0}, "find_hit_0.9": {"ms": 6.5}, "find_miss_0.9": {"ms": 21.0},
+            "iou_add_s0.5": {"ms": 14.0}, "iou_add_s1.0": {"ms": 11.0}, "iou_add_s1.25": {"ms": 6.0},
+            "iou_add_s1.5": {"ms": 5.0}, "erase": {"ms": 7.5}, "migrate_x2": {"ms": 4.0}}
+
+
+def test_dominant_kernel_is_the_largest_summed_time():
+    bd = _breakdown()
+    counts = {k: 1 << 27 for k in bd}
+    counts.update({k: 1 << 28 for k in bd if k.startswith("iou")})
+    counts["migrate_x2"] = 1 << 28
+    bpo = {k: 100.0 for k in bd}
+    dom, others = bench.kernel_rooflines(bd, counts, bpo, 6766.0, "measured")
+    assert dom["kernel"].startswith("iou_agg_kernel")
+    assert dom["ms_per_step"] == pytest.approx(36.0)
+    assert dom["launches_per_step"] == 4
+    gbs = 4 * 100.0 * (1 << 28) / (36.0e-3) / 1e9
+    assert dom["achieved"] == pytest.approx(gbs, rel=1e-3)
+    assert dom["frac"] == pytest.approx(gbs / 6766.0, rel=1e-3)
+    # the find kernel at load 0.9 covers both of its calls and comes next
+    assert others[0]["kernel"] == bench.CALL_KERNEL["find_hit_0.9"]
+    assert others[0]["ms_per_step"] == pytest.approx(27.5)
+    assert [o["ms_per_step"] for o in others] == sorted((o["ms_per_step"] for o in others), reverse=True)
+
+
+def test_random_modify_context_uses_the_committed_ceilings():
+    with open(os.path.join(bench.ROOT, "profiles", "ceilings.json")) as f:
+        ceil = json.load(f)
+    bd = _breakdown()
+    counts = {"insert_0.5": 1 << 27, "erase": 1 << 27, "iou_add_s0.5": 1 << 28}
+    ctx = bench.random_modify_context(bd, counts)
+    for name, key in bench.MODIFY_CEILING.items():
+        g = counts[name] / (bd[name]["ms"] * 1e-3) / 1e9
+        assert ctx[name]["g_ops_per_s"] == pytest.approx(g, abs=0.01)
+        assert ctx[name]["ceiling_g_per_s"] == ceil[key]
+        assert ctx[name]["frac"] == pytest.approx(g / ceil[key], abs=1e-3)
+
+
+def test_load_half_fractions():
+    bd = {"insert_0.5": {"gbs": 1700.0}, "find_hit_0.5": {"gbs": 1720.0}, "find_miss_0.5": {"gbs": 1960.0}}
+    t = bench.load_half_fractions(bd, 6800.0)
+    assert t["goal_frac"] == 0.5
+    assert t["2p28_insert_0.5"] == pytest.approx(0.25)
+    assert t["2p28_find_miss_0.5"] == pytest.approx(1960.0 / 6800.0, abs=1e-4)
