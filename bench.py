@@ -533,6 +533,43 @@ def pinned_copy_gbs(nbytes: int = 1 << 32) -> dict:
     return out
 
 
+def side_workloads(args) -> dict:
+    """Small runs of the batched and serving workloads beside the step, so one
+    bench line carries their evidence: 256 tables in one engine launch against
+    one launch per batch (sampled tables checked against the oracle), and 10^4
+    served requests with p50 / p99 at Poisson arrivals of half the capacity,
+    against the same requests as single calls (results compared).  Outside
+    the timed region; the full-size runs are `--workload batched|serving`."""
+    import copy
+
+    out = {}
+    b = copy.copy(args)
+    b.batched_tables, b.batched_log2_min, b.batched_log2_max = 256, 8, 20
+    b.steps, b.warmup, b.batched_verify = 2, 1, 4
+    b.batched_engine_only, b.no_graph_baseline = False, True
+    r = run_batched(b)
+    out["batched_256_tables"] = {
+        "tables": r["tables"], "batches": r["batches"], "ops": r["ops"],
+        "engine_ms": r["engine"]["ms"], "engine_mops": r["engine"]["mops"],
+        "per_call_ms": r["per_call"]["ms"], "per_call_mops": r["per_call"]["mops"],
+        "engine_over_per_call": round(r["per_call"]["ms"] / r["engine"]["ms"], 1),
+        "verified_tables": r["verified_tables"]}
+    v = copy.copy(args)
+    v.serving_requests, v.serving_arrays, v.serving_loads, v.serving_baseline_loads = 10_000, "device", [0.5], [0.5]
+    v.no_serving_baseline, v.serving_trace = False, ""
+    r = run_serving(v)
+    sc = r["single_calls"]
+    out["serving_1e4_requests"] = {
+        "requests": r["requests"], "ops": r["ops"],
+        "served": {"capacity_mops": r["capacity"]["mops"], "capacity_requests_per_s": r["capacity"]["requests_per_s"],
+                   "p50_ms_at_0.5": r["load_0.5"]["p50_ms"], "p99_ms_at_0.5": r["load_0.5"]["p99_ms"]},
+        "single_calls": {"capacity_mops": sc["capacity"]["mops"],
+                         "capacity_requests_per_s": sc["capacity"]["requests_per_s"],
+                         "p50_ms_at_0.5": sc["load_0.5"]["p50_ms"], "p99_ms_at_0.5": sc["load_0.5"]["p99_ms"]},
+        "results_equal": sc["results_equal_served"]}
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -630,6 +667,12 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_once()
+    side = None
+    ops_step = runner.ops_per_step
+    if rank == 0 and world == 1 and not args.no_side_workloads:
+        del runner, inp
+        torch.cuda.empty_cache()
+        side = side_workloads(args)
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -640,16 +683,17 @@ def run_gpu(args):
                                    "2^27 misses at each load, insertOrUpdate(add 1) 2^28 Zipf ops over "
                                    "2^26 keys for s in {0.5,1.0,1.25,1.5}, erase 2^27, migrate x2; "
                                    "growable table 2^12 cells taking 2^27 inserts (15 doublings)",
-                       "capacity_cells": 1 << LOG2C, "ops_per_step": runner.ops_per_step,
+                       "capacity_cells": 1 << LOG2C, "ops_per_step": ops_step,
                        "partition": args.partition, "grow_in_kernel": args.grow_in_kernel,
                        "l2": "inputs and table far larger than L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "probe_window": "auto by load: finds 2 lanes x 64 B below 0.6, 4 x 64 B above; "
-                                       "inserts 1 x 32 B below 0.6, 4 x 64 B above"},
+                       "probe_window": "auto (the autotuned rule): at 2^28 cells finds 2 lanes x 64 B at "
+                                       "load 0.5 and 4 x 64 B at 0.9, inserts 1 x 32 B below 0.6 and "
+                                       "4 x 64 B at 0.9"},
             "roofline": roofline, "roofline_other_kernels": roofline_others, "target": target,
             "random_modify_ceiling": modify_ctx,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "breakdown": breakdown, "latency_config1": lat,
+            "clocks": clk, "breakdown": breakdown, "latency_config1": lat, "side_workloads": side,
         }
         print(json.dumps(line), flush=True)
     if pg is not None:
@@ -905,7 +949,7 @@ def run_batched(args):
                            {"ms": round(graph_ms, 3), "mops": round(total / (graph_ms * 1e-3) / 1e6, 1)}),
         "verified_tables": verified, "steps": args.steps, "warmup": args.warmup,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def verify_batched_sample(wl, tables, keys, vout, codes, n_sample):
@@ -1148,7 +1192,7 @@ def run_serving(args):
                 "offered_requests_per_s": round(frac * cap_rps, 1), "makespan_s": round(bmk, 4),
                 "mops": round(total / bmk / 1e6, 1), "p50_ms": round(float(np.percentile(blat, 50)) * 1e3, 3),
                 "p99_ms": round(float(np.percentile(blat, 99)) * 1e3, 3)}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def main():
@@ -1164,6 +1208,8 @@ def main():
                     help="table option for every table of the step: hash-partitioned execution of the batches")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side-workloads", action="store_true",
+                    help="skip the small batched and serving runs reported beside the step")
     ap.add_argument("--latency-reps", type=int, default=100)
     ap.add_argument("--window-rounds", type=int, default=128,
                     help="sliding-window case: rounds of 2^20 inserts + 2^20 erases (128 = 2^27 of each)")
@@ -1208,10 +1254,10 @@ def main():
                     help="1: copy every request through the device arena instead of reading it in place")
     args = ap.parse_args()
     if args.workload == "batched":
-        run_batched(args)
+        print(json.dumps(run_batched(args)), flush=True)
         return
     if args.workload == "serving":
-        run_serving(args)
+        print(json.dumps(run_serving(args)), flush=True)
         return
     if args.case:
         import bench_cases
