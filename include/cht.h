@@ -369,10 +369,11 @@ cht_status cht_plan_launch(cht_plan_handle p, cht_stream_t stream);
 /* Synchronize `stream` and return the status bits of the last launch. */
 cht_status cht_plan_status(cht_plan_handle p, uint32_t *bits, cht_stream_t stream);
 /* Try the engine's probe windows and CTAs/SM on this plan and keep the
- * fastest: each trial runs on a copy of the plan's tables, which are restored
- * afterwards (their contents are unchanged on return; the plan's output
- * arrays hold the results of the last trial).  *best_ms (nullable) receives
- * the best time.  Needs device memory for one copy of every table. */
+ * fastest by the median of three runs each: every run works on the plan's
+ * tables, which are restored from a copy afterwards (their contents are
+ * unchanged on return; the plan's output arrays hold the results of the last
+ * run).  *best_ms (nullable) receives the best median.  Needs device memory
+ * for one copy of every table. */
 cht_status cht_plan_autotune(cht_plan_handle p, cht_stream_t stream, double *best_ms);
 cht_status cht_plan_destroy(cht_plan_handle p);
 

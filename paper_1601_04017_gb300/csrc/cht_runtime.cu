@@ -1854,26 +1854,34 @@ cht_status cht_plan_autotune(cht_plan_handle p, cht_stream_t stream, double* bes
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = CHT_ERR_CUDA;
     if (r == CHT_OK) r = copy_tables(true);
+    constexpr int kTrials = 3;  // the median of three runs per candidate
     for (const Cand& c : cands) {
         if (r != CHT_OK) break;
         p->cfg.group_width = c.g;
         p->cfg.lane_cells = c.v;
         p->cfg.ctas_per_sm = c.ctas;
         p->cfg.direct_io = c.direct;
-        float ms = 0;
-        if (cudaEventRecord(e0, s) != cudaSuccess) r = CHT_ERR_CUDA;
-        if (r == CHT_OK) r = plan_run(p, s);
-        if (r == CHT_OK && cudaEventRecord(e1, s) != cudaSuccess) r = CHT_ERR_CUDA;
-        if (r == CHT_OK && cudaEventSynchronize(e1) != cudaSuccess) r = CHT_ERR_CUDA;
-        if (r == CHT_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = CHT_ERR_CUDA;
-        u32 st = 0;
-        if (r == CHT_OK && cudaMemcpy(&st, p->d_status, sizeof(u32), cudaMemcpyDeviceToHost) != cudaSuccess)
-            r = CHT_ERR_CUDA;
-        if (r == CHT_OK && st == 0 && ms < best) {
+        float t[kTrials] = {};
+        bool ok = true;
+        for (int k = 0; k < kTrials && r == CHT_OK; ++k) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) r = CHT_ERR_CUDA;
+            if (r == CHT_OK) r = plan_run(p, s);
+            if (r == CHT_OK && cudaEventRecord(e1, s) != cudaSuccess) r = CHT_ERR_CUDA;
+            if (r == CHT_OK && cudaEventSynchronize(e1) != cudaSuccess) r = CHT_ERR_CUDA;
+            if (r == CHT_OK && cudaEventElapsedTime(&t[k], e0, e1) != cudaSuccess) r = CHT_ERR_CUDA;
+            u32 st = 0;
+            if (r == CHT_OK && cudaMemcpy(&st, p->d_status, sizeof(u32), cudaMemcpyDeviceToHost) != cudaSuccess)
+                r = CHT_ERR_CUDA;
+            if (st != 0) ok = false;
+            if (r == CHT_OK) r = copy_tables(false);
+        }
+        if (r != CHT_OK) break;
+        std::sort(t, t + kTrials);
+        const double ms = t[kTrials / 2];
+        if (ok && ms < best) {
             best = ms;
             best_cfg = p->cfg;
         }
-        if (r == CHT_OK) r = copy_tables(false);
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
