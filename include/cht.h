@@ -537,8 +537,9 @@ cht_status cht_find_noalloc(cht_handle h, const uint64_t *keys, uint64_t n, uint
  * {-1 (one thread per operation), 1, 2, 4, 8, 16, 32}, cells per lane V in
  * {1, 2, 4} where the kernels exist,
  * resident CTAs per SM in {occupancy maximum, 4} -- `trials` times each (at
- * least 3), restoring the table's cells and counters before every trial of a
- * modifying operation and once more at the end, so the table is unchanged.
+ * least 3; a find trial is the mean of 8 launches back to back), restoring the
+ * table's cells and counters before every trial of a modifying operation and
+ * once more at the end, so the table is unchanged.
  * results[0 .. *n_results) receive every candidate with the median of its
  * trials, fastest first (max_results bounds the count).  keys / vals: device
  * arrays of n entries (vals for operations with values).  Tables with tombstone

@@ -1490,6 +1490,11 @@ cht_status cht_tune(cht_handle h, int op, const uint64_t* keys, const uint64_t* 
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = restore(true);
     std::vector<cht_tune_result> all;
+    // finds leave the table as it is: a trial times kFindReps launches back to
+    // back (as calls are issued) and keeps their mean, which also averages out
+    // the launch-to-launch noise of short calls
+    constexpr int kFindReps = 8;
+    const int reps = mode == cht::kFind ? kFindReps : 1;
     for (const Cand& c : cands) {
         for (int ct : ctas) {
             std::vector<double> t;
@@ -1497,11 +1502,11 @@ cht_status cht_tune(cht_handle h, int op, const uint64_t* keys, const uint64_t* 
                 if (k > 0 || !all.empty()) e = restore(false);
                 float ms = 0;
                 if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-                if (e == cudaSuccess) e = cht::launch_op(mode, a, c.g, c.v, ct, s);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cht::launch_op(mode, a, c.g, c.v, ct, s);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                t.push_back(ms);
+                t.push_back(ms / reps);
             }
             if (e != cudaSuccess) break;
             std::sort(t.begin(), t.end());

@@ -2,9 +2,9 @@
 
 Runs the single-call autotuner (cht_tune: every probe window -- group width G,
 cells per lane V, resident CTAs per SM -- timed with at least three trials,
-median kept) on tables of 2^20, 2^24 and 2^28 cells at loads 0.25, 0.5, 0.7
-and 0.9, for find (a batch of hits and a batch of misses, ranked by the sum of
-the two), insert (two batches that end at the load: the fresh keys that fill
+median kept) on tables of 2^20, 2^24, 2^26 and 2^28 cells at loads 0.25, 0.5, 0.7
+and 0.9, for find (a batch of hits and a batch of misses of c/2 operations each, at
+most 2^26, ranked by the sum of the two), insert (two batches that end at the load: the fresh keys that fill
 the table from the previous load level to this one, and the keys up to this
 load into an empty table; ranked by the sum of the two), erase and update
 (present keys), and writes
@@ -45,8 +45,11 @@ def builtin_window(op: int, load: float):
     return (4, 4, 0) if op in (0, 1) else (4, 2, 0)
 
 
-SIZES = (20, 24, 28)                # tuned sizes: log2 of the capacity
-SIZE_RANGES = {20: (0, 22), 24: (23, 26), 28: (27, 40)}  # the sizes each one stands for
+# tuned sizes (log2 of the capacity) and the sizes each one stands for: 2^20
+# cells fit the 129 MB L2, 2^24 cells (256 MB) half fit, 2^26 and 2^28 are
+# HBM-resident
+SIZES = (20, 24, 26, 28)
+SIZE_RANGES = {20: (0, 22), 24: (23, 24), 26: (25, 26), 28: (27, 40)}
 LOADS = (0.25, 0.5, 0.7, 0.9)       # tuned loads
 BANDS = {0.25: (0.0, 0.375), 0.5: (0.375, 0.6), 0.7: (0.6, 0.8), 0.9: (0.8, 1.01)}
 MODE_NAMES = {0: "cht::kFind", 1: "cht::kInsert", 4: "cht::kErase", 5: "cht::kUpdAdd"}
@@ -109,9 +112,12 @@ def main():
             res_ins = sorted(((w[0], w[1], w[2], ra[w] + rb[w]) for w in ra), key=lambda r: r[3])
             t.insert(ins_k, ins_v)
             filled = n_ld
+            # find / erase / update batches of c/2 operations (at most 2^26):
+            # present keys (as many as the table holds, up to that) and as
+            # many absent ones -- the batch sizes the workloads use
             nq = min(c // 2, 1 << 26)
-            present = keys[:filled][torch.randperm(filled, device="cuda")[: nq // 2]]
-            fresh = keys[n_max: n_max + nq - nq // 2]
+            present = keys[:filled][torch.randperm(filled, device="cuda")[:nq]]
+            fresh = keys[n_max: n_max + nq]
             batches = {
                 0: (torch.cat([present, fresh]), None),
                 1: (ins_k, ins_v),
