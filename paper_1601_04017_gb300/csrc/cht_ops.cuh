@@ -514,6 +514,38 @@ __device__ __forceinline__ void warp_ops(const OpArgs& a, u64 next, const u64 en
 
 }
 
+// Sum the CTA's counters and status bits into the table's device state with
+// one atomic per counter and CTA (a warp each would put thousands of atomics
+// on the same two words at the end of a launch).  Every thread of the CTA
+// calls it once, at the end of the kernel.
+__device__ __forceinline__ void block_flush_counters(DevState* st, u64 n_ins, u64 n_del, u32 sbits) {
+    constexpr u32 FULL = 0xffffffffu;
+    __shared__ unsigned long long s_ins, s_del;
+    __shared__ u32 s_bits;
+    if (threadIdx.x == 0) {
+        s_ins = 0;
+        s_del = 0;
+        s_bits = 0;
+    }
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        n_ins += __shfl_xor_sync(FULL, n_ins, o);
+        n_del += __shfl_xor_sync(FULL, n_del, o);
+    }
+    const u32 any_status = __reduce_or_sync(FULL, sbits);
+    if ((threadIdx.x & 31) == 0) {
+        if (n_ins) atomicAdd(&s_ins, n_ins);
+        if (n_del) atomicAdd(&s_del, n_del);
+        if (any_status) atomicOr(&s_bits, any_status);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_ins) atomicAdd(&st->I, s_ins);
+        if (s_del) atomicAdd(&st->D, s_del);
+        if (s_bits) atomicOr(&st->status, s_bits);
+    }
+}
+
 // Sum the warp's counters and status bits into the table's device state.
 __device__ __forceinline__ void warp_flush_counters(DevState* st, u64 n_ins, u64 n_del, u32 sbits) {
     constexpr u32 FULL = 0xffffffffu;
@@ -576,6 +608,8 @@ __global__ void __launch_bounds__(kOpBlock, op_min_blocks<G, V>()) op_kernel(OpA
             warp_ops<G, V, MODE, false, false, kFlags>(a, begin, end, n_ins, n_del, sbits);
         }
     }
+    // (one atomic per warp: the CTA-level flush costs the 5-CTA window kernels
+    // register spills, and these kernels serve the large batches)
     warp_flush_counters(a.st, n_ins, n_del, sbits);
 }
 
@@ -708,7 +742,7 @@ __global__ void __launch_bounds__(kThreadBlock) thread_kernel(OpArgs a) {
         key = nk;
         d = nd;
     }
-    warp_flush_counters(a.st, n_ins, n_del, sbits);
+    block_flush_counters(a.st, n_ins, n_del, sbits);
 }
 
 }  // namespace cht
