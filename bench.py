@@ -1213,7 +1213,8 @@ def main():
     ap.add_argument("--latency-reps", type=int, default=100)
     ap.add_argument("--window-rounds", type=int, default=128,
                     help="sliding-window case: rounds of 2^20 inserts + 2^20 erases (128 = 2^27 of each)")
-    ap.add_argument("--case", choices=["find", "insert", "migrate", "shrink", "iou", "grow", "contention", "window", "build"],
+    ap.add_argument("--case", choices=["find", "insert", "migrate", "shrink", "iou", "grow", "contention", "window", "build",
+                                       "smallcalls"],
                     help="run one small single-operation case (for profiling) instead of the benchmark")
     ap.add_argument("--case-log2c", type=int, default=26)
     ap.add_argument("--case-load", type=float, default=0.9)

@@ -169,6 +169,61 @@ def run_case(args):
                     "pairs_per_s_M": round(batch * rounds / (ms * 1e-3) / 1e6, 1),
                     "capacity_before": mig0, "capacity_after": cap, "nonempty_after": ne})
         t.destroy()
+    elif args.case == "smallcalls":
+        # Per-call cost of calls of 2^10 .. 2^20 operations on a 2^20-cell table
+        # at load 0.5 (L2-resident), device time per call from 32 calls replayed
+        # in one CUDA graph: finds of present keys, and inserts of fresh keys
+        # into a table just cleared (the clear's own replay time subtracted).
+        # A least-squares line over the sizes gives the fixed cost per call and
+        # the time per operation.
+        import numpy as np
+
+        c = 1 << 20
+        wl = W.bounded_workload(20, loads=(0.5,), n_find=c // 2, backend="cuda")
+        n05 = wl["counts"][0.5]
+        t1 = cht.Table(c)
+        t1.insert(wl["keys"][:n05], wl["vals"][:n05])
+        t2 = cht.Table(c)
+        vout = torch.empty(c, dtype=torch.int64, device="cuda")
+        codes = torch.empty(c, dtype=torch.uint8, device="cuda")
+        fresh = W.uniform_keys(c, start=1 << 40, backend="cuda")
+        R = 32
+
+        def graph_ms(fn):
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                for _ in range(R):
+                    fn()
+            g.replay()
+            ms = tm(g.replay) / R
+            del g
+            return ms
+
+        sizes = [1 << k for k in range(10, 21)]
+        rows = []
+        clear_ms = graph_ms(t2.clear)
+        for n in sizes:
+            q = wl["hits"][0.5][:n] if n <= n05 else torch.cat([wl["hits"][0.5], wl["hits"][0.5]])[:n]
+            f_ms = graph_ms(lambda: t1.find(q, vout[:n], codes[:n]))
+
+            def ins():
+                t2.clear()
+                t2.insert(fresh[:n], fresh[:n], codes[:n])
+
+            i_ms = graph_ms(ins) - clear_ms if n <= n05 else None
+            rows.append({"n": n, "find_us": round(f_ms * 1e3, 3), "insert_us": None if i_ms is None else
+                         round(i_ms * 1e3, 3)})
+        ns = np.array([r["n"] for r in rows], dtype=np.float64)
+        fu = np.array([r["find_us"] for r in rows])
+        slope, icpt = np.polyfit(ns, fu, 1)
+        ok = [r for r in rows if r["insert_us"] is not None]
+        islope, iicpt = np.polyfit(np.array([r["n"] for r in ok], np.float64), np.array([r["insert_us"] for r in ok]), 1)
+        out.update({"log2c": 20, "load": 0.5, "rows": rows, "clear_us": round(clear_ms * 1e3, 3),
+                    "find_fit": {"fixed_us": round(float(icpt), 3), "ns_per_op": round(float(slope) * 1e3, 4)},
+                    "insert_fit": {"fixed_us": round(float(iicpt), 3), "ns_per_op": round(float(islope) * 1e3, 4)}})
+        t1.destroy()
+        t2.destroy()
     elif args.case == "grow":
         keys = W.uniform_keys(c // 2, backend="cuda")
         vals = W.values_for(keys, backend="cuda")
