@@ -5,8 +5,9 @@ context.  No GPU: the functions are pure arithmetic on a breakdown.
 Pins: Knuth's expected probe lengths for linear probing (successful search
 (1 + 1/(1-a))/2, unsuccessful (1 + 1/(1-a)^2)/2) at the loads the bench uses,
 the insert fill average checked against a numerical integral of the
-unsuccessful-search length (not the closed form it uses), and the per-operation
-byte counts the design table quotes.
+unsuccessful-search length (not the closed form it uses), the per-operation
+byte counts the design table quotes, and the sector model against the sectors
+the probes of an actual oracle table touch.
 """
 import json
 import os
@@ -103,3 +104,49 @@ def test_load_half_fractions():
     assert t["goal_frac"] == 0.5
     assert t["2p28_insert_0.5"] == pytest.approx(0.25)
     assert t["2p28_find_miss_0.5"] == pytest.approx(1960.0 / 6800.0, abs=1e-4)
+
+
+@pytest.mark.parametrize("alpha", [0.5, 0.9])
+def test_sector_model_on_an_actual_table(oracle_mod, alpha):
+    """The bench's algorithmic sectors (1 + (L - 1)/2 for a probe of L cells
+    from a random home) against the distinct 32-byte sectors each probe of an
+    actual oracle table touches: cells [home, end] with end the key's cell
+    (hit) or the first empty cell (miss), sectors = end//2 - home//2 + 1 on the
+    unwrapped index.  Within 5 % of the Knuth-based figure the roofline uses
+    (8 % for misses at 0.9, whose mean has a heavy tail)."""
+    import workloads as W
+
+    log2c = 18
+    c = 1 << log2c
+    n = int(alpha * c)
+    ks = W.uniform_keys(n, seed=91)
+    t = oracle_mod.OracleTable(c)
+    t.insert(ks, ks)
+    cells = t.cells()
+    keys_at = cells[:, 0]
+    occupied = keys_at != 0
+    pos_of = {int(k): i for i, k in enumerate(keys_at.tolist()) if k != 0}
+
+    def sectors(home, end):
+        end = np.where(end < home, end + c, end)  # unwrap a probe that wrapped
+        return end // 2 - home // 2 + 1
+
+    h_hit = oracle_mod.homes(ks, log2c).astype(np.int64)
+    e_hit = np.array([pos_of[int(k)] for k in ks.tolist()], dtype=np.int64)
+    s_hit = float(np.mean(sectors(h_hit, e_hit)))
+    # first empty cell at or after every index (two passes for the wrap)
+    nxt = np.empty(2 * c, dtype=np.int64)
+    occ2 = np.concatenate([occupied, occupied])
+    last = -1
+    for i in range(2 * c - 1, -1, -1):
+        if not occ2[i]:
+            last = i
+        nxt[i] = last
+    misses = W.uniform_keys(1 << 15, start=n, seed=91)
+    h_miss = oracle_mod.homes(misses, log2c).astype(np.int64)
+    e_miss = nxt[h_miss] % c
+    s_miss = float(np.mean(sectors(h_miss, e_miss)))
+    model_hit = bench.sectors(bench.knuth_hit(alpha))
+    model_miss = bench.sectors(bench.knuth_miss(alpha))
+    assert abs(s_hit - model_hit) / model_hit < 0.05, (s_hit, model_hit)
+    assert abs(s_miss - model_miss) / model_miss < (0.08 if alpha >= 0.9 else 0.05), (s_miss, model_miss)
