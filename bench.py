@@ -345,8 +345,8 @@ def latency_percentiles(cht, inp, reps: int):
         v = sorted(v)
         p50 = v[len(v) // 2]
         p99 = v[min(len(v) - 1, int(math.ceil(0.99 * len(v))) - 1)]
-        out[k] = {"p50_ms": round(p50, 5), "p99_ms": round(p99, 5),
-                  "mops_at_p50": round(n / (p50 * 1e-3) / 1e6, 1)}
+        out[k] = {"p50_ms": round(p50, 5), "p99_ms": round(p99, 5), "mean_ms": round(statistics.mean(v), 5),
+                  "reps": len(v), "mops_at_p50": round(n / (p50 * 1e-3) / 1e6, 1)}
     # The same calls back to back (the host enqueues ahead of the GPU, so the
     # host-side cost of a call is hidden) and replayed from a CUDA graph (no
     # host work at all: the device time of a call).  As in the single calls,
