@@ -26,7 +26,11 @@
  *   (pageable or pinned) are staged through library-owned device buffers:
  *   inputs are copied in on the stream before the kernel, outputs are copied
  *   back on the stream after it; results in a host output array are valid
- *   once the stream has been synchronized.  The caller owns every array and
+ *   once the stream has been synchronized.  Batches of more than 2^24
+ *   operations with host arrays run in pieces of 2^24 through three device
+ *   slots kept by the library (about 420 MB each, allocated on a device's
+ *   first such call), so the copies of one piece overlap the kernel of
+ *   another; the pieces run in order, one linearization of the batch.  The caller owns every array and
  *   keeps it alive until the work on the stream has completed.  The library
  *   owns the table memory.  `stream` may be NULL (the legacy default stream).
  *
