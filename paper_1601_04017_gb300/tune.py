@@ -55,6 +55,27 @@ BANDS = {0.25: (0.0, 0.375), 0.5: (0.375, 0.6), 0.7: (0.6, 0.8), 0.9: (0.8, 1.01
 MODE_NAMES = {0: "cht::kFind", 1: "cht::kInsert", 4: "cht::kErase", 5: "cht::kUpdAdd"}
 
 
+def rank_by_sum(a: dict, b: dict) -> list:
+    """Windows ranked by the sum of their times on two batches (a, b: window
+    (G, V, CTAs/SM) -> ms), fastest first, as (G, V, CTAs/SM, ms) rows."""
+    return sorted(((w[0], w[1], w[2], a[w] + b[w]) for w in a if w in b), key=lambda r: r[3])
+
+
+def choose(res: list, builtin: tuple, margin: float = MARGIN) -> tuple:
+    """The rule's window: the fastest measured one if it beats the built-in
+    window by more than `margin`, else the built-in one (timing noise of short
+    calls would otherwise pick windows at random).  res: ranked rows."""
+    best = res[0]
+    base = next(r for r in res if (r[0], r[1], r[2]) == builtin)
+    return best if best[3] < (1.0 - margin) * base[3] else base
+
+
+def rule_line(mode_name: str, lo: int, hi: int, blo: float, bhi: float, g: int, v: int, ct: int,
+              ms: float, nops: int) -> str:
+    """One entry of cht_tuned.inc."""
+    return f"{{{mode_name}, {lo}, {hi}, {blo:.3f}f, {bhi:.3f}f, {g}, {v}, {ct}}},  // {ms:.4f} ms for {nops} ops\n"
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("group_width", ctypes.c_int), ("lane_cells", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("ms", ctypes.c_double)]
@@ -109,7 +130,7 @@ def main():
             ins_k, ins_v = keys[filled:n_ld], vals[filled:n_ld]
             ra = {r[:3]: r[3] for r in tune_one(lib, t, 1, ins_k, ins_v, args.trials)}
             rb = {r[:3]: r[3] for r in tune_one(lib, t_empty, 1, keys[:n_ld], vals[:n_ld], args.trials)}
-            res_ins = sorted(((w[0], w[1], w[2], ra[w] + rb[w]) for w in ra), key=lambda r: r[3])
+            res_ins = rank_by_sum(ra, rb)
             t.insert(ins_k, ins_v)
             filled = n_ld
             # find / erase / update batches of c/2 operations (at most 2^26):
@@ -130,12 +151,11 @@ def main():
                     # ranked by the sum of its two times
                     rh = {r[:3]: r[3] for r in tune_one(lib, t, 0, present, None, args.trials)}
                     rm = {r[:3]: r[3] for r in tune_one(lib, t, 0, fresh, None, args.trials)}
-                    res = sorted(((w[0], w[1], w[2], rh[w] + rm[w]) for w in rh), key=lambda r: r[3])
+                    res = rank_by_sum(rh, rm)
                 else:
                     res = res_ins if op == 1 else tune_one(lib, t, op, k, v, args.trials)
-                best = res[0]
                 base = next(r for r in res if (r[0], r[1], r[2]) == builtin_window(op, ld))
-                g, vv, ct, ms = best if best[3] < (1.0 - MARGIN) * base[3] else base
+                g, vv, ct, ms = choose(res, builtin_window(op, ld))
                 lo, hi = SIZE_RANGES[log2c]
                 blo, bhi = BANDS[ld]
                 nops = k.numel() if op != 1 else ins_k.numel() + n_ld  # (the ranked times cover both batches)
@@ -152,9 +172,8 @@ def main():
                 "// (median of >= 3 trials per window).  Per operation, table size range (log2 of\n"
                 "// the capacity) and load band: the fastest window (G lanes, V cells per lane,\n"
                 "// resident CTAs per SM, 0 = occupancy maximum) and its time for the tuning batch.\n")
-        for (m, lo, hi, blo, bhi, g, vv, ct, ms, nops) in rows:
-            f.write(f"{{{m}, {lo}, {hi}, {blo:.3f}f, {bhi:.3f}f, {g}, {vv}, {ct}}},"
-                    f"  // {ms:.4f} ms for {nops} ops\n")
+        for row in rows:
+            f.write(rule_line(*row))
     if args.summary:
         with open(args.summary, "w") as f:
             f.write("# Probe-window autotuning (cht_tune) on this GPU\n\n")
